@@ -1,0 +1,34 @@
+"""The seeded workloads (stand-ins for the paper's DYAMOND fields, Sec. IV-A).
+
+* ``config1_field``: 64 lon x 32 Gaussian lat x 8 levels, T21 spectrum with
+  complex N(0,1) (l+1)^-1.5 amplitudes, one draw per level, seed 0.
+* ``config2_field``: 1280 x 640 x 137, T639 (l+1)^-1.5 spectrum, one draw per
+  level, each level scaled to unit RMS, plus N(0, 0.01^2) white noise, seed 1.
+* ``temperature_like``: 250 + 20 * field -- the paper's temperature has a
+  large mean offset, which is what makes its relative error small.
+"""
+import numpy as np
+
+from .sht import sht_field
+
+
+def config1_field():
+    return sht_field(64, 32, 8, T=21, slope=-1.5, seed=0)
+
+
+def unit_rms_plus_noise(f, noise, seed):
+    f = f.astype(np.float64)
+    rms = np.sqrt(np.mean(f * f, axis=(1, 2), keepdims=True))
+    f = f / np.where(rms > 0, rms, 1.0)
+    rng = np.random.default_rng([int(seed), 0x5eed])
+    f = f + noise * rng.standard_normal(f.shape)
+    return f.astype(np.float32)
+
+
+def config2_field(nlon=1280, nlat=640, nlev=137, T=639, seed=1, noise=0.01):
+    f = sht_field(nlon, nlat, nlev, T=T, slope=-1.5, seed=seed)
+    return unit_rms_plus_noise(f, noise, seed)
+
+
+def temperature_like(f):
+    return (250.0 + 20.0 * f.astype(np.float64)).astype(np.float32)
