@@ -1,0 +1,443 @@
+"""Benchmark of the fused pencil-transposition pack + ZFP fixed-rate path.
+
+Workload (one GPU): a 1280 x 640 x 137 float32 field (T639 power-law
+spectrum, unit RMS per level plus 0.01 white noise, seed 1) held in HBM,
+planned over an 8 x 8 grid of simulated ranks for the z -> lambda
+transposition (512 messages of 160 x 80 x 17/18 values).  One step =
+for rate in (8, 16): fused pack+compress -> device-local all-to-all ->
+fused decompress+unpack.  The metric is GB/s of float32 through the codec
+passes: 4 passes x 449 MB per step (compress reads the field, decompress
+writes it, at each rate), divided by the step time.  The comparators (plain
+float32 and float16-cast pack -> all-to-all -> unpack) are timed the same
+way on the same field and reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl zfpx|reference]
+Under torchrun every rank runs its own field (weak scaling, no data-path
+collective); rank 0 prints one JSON line.
+"""
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import threading
+import time
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fused pack+ZFP rate-8/16 GB/s (fp32 in) vs HBM roofline & fp16-cast pack"
+SHAPE = (137, 640, 1280)                    # [lev][lat][lon]
+PR = PC = 8
+RATES = (8, 16)
+WORKLOAD = ("config2: 1280x640x137 float32 T639 (l+1)^-1.5 field + 0.01 noise (seed 1), "
+            "z->lambda over 8x8 simulated ranks (512 messages), ZFP 3-D rates 8 and 16: "
+            "pack+compress, device-local all-to-all, decompress+unpack")
+FALLBACK_HBM = 6800.0
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2609_24294_gb300", "csrc", "*"))):
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key, sha):
+    """DRAM bytes per launch from a committed ncu summary of the same sources."""
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(f):
+            m = re.match(r"^traffic:\s*kernel=(\S+)\s+bytes_per_launch=(\d+)\s+source_sha=(\w+)", line.strip())
+            if m and m.group(1) == kernel_key and m.group(3) == sha:
+                return int(m.group(2))
+    return None
+
+
+# ------------------------------------------------------------------ CPU oracle leg
+def oracle_sample(x, max_seconds, max_messages=None):
+    """Runs the oracle over messages of the same plan (both rates, compress and
+    decompress) on all host cores until max_seconds or the whole field is
+    done.  Returns (f32 bytes processed, seconds, threads, messages)."""
+    from oracle import codec as oc
+    from oracle import plan as opl
+    nz, ny, nx = x.shape
+    plan = opl.Plan(nx, ny, nz, PR, PC, 0, 3)
+    msgs = plan.messages[: max_messages or len(plan.messages)]
+    threads = os.cpu_count() or 1
+
+    def one(m):
+        box = x[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx]
+        out = np.empty(box.shape, dtype=np.float32)
+        for r in RATES:
+            s = oc.encode_array(3, r, box)
+            oc.decode_array(3, r, s, out)
+        return 4 * 4 * m.nvals          # f32 bytes through 4 codec passes
+
+    done_bytes, done = 0, 0
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        it = iter(msgs)
+        pending = set()
+        for _ in range(2 * threads):
+            m = next(it, None)
+            if m is not None:
+                pending.add(ex.submit(one, m))
+        while pending:
+            f = next(iter(pending))
+            done_bytes += f.result()
+            done += 1
+            pending.discard(f)
+            if time.perf_counter() - t0 < max_seconds:
+                m = next(it, None)
+                if m is not None:
+                    pending.add(ex.submit(one, m))
+    return done_bytes, time.perf_counter() - t0, threads, done
+
+
+def make_field():
+    import fieldgen
+    return fieldgen.config2_field()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    x = make_field()
+    nbytes, secs = [], []
+    for i in range(args.warmup + args.steps):
+        b, s, threads, done = oracle_sample(x, args.ref_seconds)
+        if i >= args.warmup:
+            nbytes.append(b)
+            secs.append(s)
+    value = sum(nbytes) / sum(secs) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * sum(secs) / len(secs), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": threads, "kind": "oracle",
+                         "sample": "per step: messages of the same plan for ~%.0f s (4 codec passes each)"
+                                   % args.ref_seconds},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2609_24294_gb300 import build, zfpx as z
+    build.build()
+    z.lib()
+
+    x = make_field()
+    nz, ny, nx = x.shape
+    nvals = x.size
+    field_bytes = 4 * nvals
+    xd = torch.from_numpy(x).cuda()
+    plan = z.Plan.for_fields(xd, PR, PC, 0, 3)
+    for r in RATES + (z.RATE_F32, z.RATE_F16):
+        plan.prepare(r)
+    send = {r: torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda") for r in RATES}
+    recv = {r: torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda") for r in RATES}
+    outs = {r: torch.empty_like(xd) for r in RATES}
+    stream = torch.cuda.current_stream()
+
+    names = []
+    for r in RATES:
+        names += ["compress_r%d" % r, "permute_r%d" % r, "decompress_r%d" % r]
+
+    def step(ev=None):
+        k = 0
+        for r in RATES:
+            if ev is not None:
+                ev[k].record(stream)
+            z.zfpx_pack_compress(plan, r, xd, send[r])
+            if ev is not None:
+                ev[k + 1].record(stream)
+            z.zfpx_permute(plan, r, send[r], recv[r])
+            if ev is not None:
+                ev[k + 2].record(stream)
+            z.zfpx_decompress_unpack(plan, r, recv[r], outs[r])
+            k += 3
+        if ev is not None:
+            ev[k].record(stream)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    launches0 = z.zfpx_launch_count()
+    per_kernel = {n: 0.0 for n in names}
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(names) + 1)] for _ in range(args.steps)]
+    t_start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = z.zfpx_launch_count() - launches0
+    clk = clocks.stop()
+    total_ms = t_start.elapsed_time(t_end)
+    for i in range(args.steps):
+        for j, n in enumerate(names):
+            per_kernel[n] += evs[i][j].elapsed_time(evs[i][j + 1])
+    elapsed = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        barrier()
+        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
+    total_ms = float(elapsed.item())
+    ms_per_step = total_ms / args.steps
+    pass_bytes = 2 * len(RATES) * field_bytes            # f32 bytes through the codec passes
+    value = ws * pass_bytes * args.steps / (total_ms / 1e3) / 1e9
+
+    # per-kernel figures (algorithmic bytes = f32 side + compressed stream actually written/read)
+    peak, peak_kind = measured_peak()
+    kern = {}
+    for r in RATES:
+        cbytes = plan.buffer_bytes(r)
+        for n, moved in (("compress_r%d" % r, field_bytes + cbytes), ("permute_r%d" % r, 2 * cbytes),
+                         ("decompress_r%d" % r, cbytes + field_bytes)):
+            ms = per_kernel[n] / args.steps
+            kern[n] = {"ms": ms, "algorithmic_bytes": moved, "GBps": moved / (ms / 1e3) / 1e9,
+                       "f32_GBps": (field_bytes / (ms / 1e3) / 1e9) if "permute" not in n else None,
+                       "frac_of_measured_hbm": moved / (ms / 1e3) / 1e9 / peak}
+    dom = max((n for n in names if "permute" not in n), key=lambda n: kern[n]["ms"])
+    sha = kernel_source_sha()
+    kkey = {"compress_r8": "encode3_r8", "compress_r16": "encode3_r16", "decompress_r8": "decode3_r8",
+            "decompress_r16": "decode3_r16"}[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
+                "traffic": recorded_traffic(kkey, sha), "source_sha": sha}
+
+    # comparators on the same field: float32 and float16 (RN) pack -> all-to-all -> unpack
+    comp = {}
+    for label, rate in (("float32", z.RATE_F32), ("float16_rn", z.RATE_F16)):
+        sb = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        o = torch.empty_like(xd)
+
+        def cstep():
+            if rate == z.RATE_F32:
+                z.zfpx_pack(plan, xd, sb)
+                z.zfpx_permute(plan, rate, sb, rb)
+                z.zfpx_unpack(plan, rb, o)
+            else:
+                z.zfpx_cast_fp16_pack(plan, z.ROUND_NEAREST, xd, sb)
+                z.zfpx_permute(plan, rate, sb, rb)
+                z.zfpx_fp16_unpack(plan, rb, o)
+        for _ in range(args.warmup):
+            cstep()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ms = [0.0, 0.0, 0.0]
+        for _ in range(args.steps):
+            e[0].record(stream)
+            if rate == z.RATE_F32:
+                z.zfpx_pack(plan, xd, sb)
+            else:
+                z.zfpx_cast_fp16_pack(plan, z.ROUND_NEAREST, xd, sb)
+            e[1].record(stream)
+            z.zfpx_permute(plan, rate, sb, rb)
+            e[2].record(stream)
+            if rate == z.RATE_F32:
+                z.zfpx_unpack(plan, rb, o)
+            else:
+                z.zfpx_fp16_unpack(plan, rb, o)
+            e[3].record(stream)
+            torch.cuda.synchronize()
+            for j in range(3):
+                ms[j] += e[j].elapsed_time(e[j + 1])
+        bb = plan.buffer_bytes(rate)
+        comp[label] = {"pack_f32_GBps": field_bytes / (ms[0] / args.steps / 1e3) / 1e9,
+                       "unpack_f32_GBps": field_bytes / (ms[2] / args.steps / 1e3) / 1e9,
+                       "pack_frac_of_measured_hbm": (field_bytes + bb) / (ms[0] / args.steps / 1e3) / 1e9 / peak,
+                       "roundtrip_ms": sum(ms) / args.steps, "message_bytes_total": bb}
+        del sb, rb, o
+
+    # reconstruction error of the timed outputs (FP64, off the timed path)
+    x64 = x.astype(np.float64)
+    err = {}
+    for r in RATES:
+        d = outs[r].cpu().numpy().astype(np.float64)
+        err["r%d" % r] = {"rel_l2": float(np.linalg.norm(d - x64) / np.linalg.norm(x64)),
+                          "max_abs": float(np.max(np.abs(d - x64)))}
+
+    # end to end through the public API: pinned host field in, decoded fields out
+    hx = torch.from_numpy(x).pin_memory()
+    hout = {r: torch.empty(SHAPE, dtype=torch.float32).pin_memory() for r in RATES}
+    xin = torch.empty_like(xd)
+
+    def e2e_step():
+        xin.copy_(hx, non_blocking=True)
+        for r in RATES:
+            z.zfpx_pack_compress(plan, r, xin, send[r])
+            z.zfpx_permute(plan, r, send[r], recv[r])
+            z.zfpx_decompress_unpack(plan, r, recv[r], outs[r])
+            hout[r].copy_(outs[r], non_blocking=True)
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
+    e2e_value = ws * pass_bytes * args.steps / (float(e2e_ms.item()) / 1e3) / 1e9
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        b_, s_, threads, done = oracle_sample(x, args.cpu_seconds)
+        cpu = {"value": b_ / s_ / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
+               "sample": "%d of 512 messages of this plan, each through r8 and r16 compress+decompress "
+                         "(%.1f s on %d threads)" % (done, s_, threads)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "inputs larger than L2 (449 MB field, 0.9 GB moved per pass)",
+                       "ranks": "8x8", "rates": list(RATES), "parallelism": "independent field per GPU"},
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "GB/s", "h2d_bytes_per_step": field_bytes,
+                    "d2h_bytes_per_step": len(RATES) * field_bytes},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "kernels": kern,
+            "comparators": comp,
+            "error": err,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="zfpx", choices=["zfpx", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

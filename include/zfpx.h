@@ -1,0 +1,167 @@
+/*
+ * zfpx.h -- C ABI of the GB300 (sm_103a) library for the fused pencil-
+ * transposition pack + ZFP fixed-rate compression path.
+ *
+ * The method (paper Sec. I and Sec. IV-C/D): before each all-to-all of the
+ * Spherical Harmonic Transform's pencil transpositions (Sec. II-B), every
+ * rank compresses its outgoing buffer on the GPU with ZFP in fixed-rate mode
+ * (Sec. II-C, Sec. IV-B: rate 8 or 16 bits per value, a fixed and
+ * predictable message size), sends the streams, and decompresses on receipt.
+ * Comparators: the plain float32 buffer and a float16 cast (Sec. I,
+ * Sec. IV-D).  On one device every rank is simulated: the all-to-all is a
+ * device-local permutation of fixed-size messages.
+ *
+ * Conventions (all entry points):
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *    never frees them.  Pointers without the prefix are host pointers.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every d_* call only enqueues work on that stream and returns;
+ *    the caller synchronises.
+ *  - Return value 0 on success, a negative ZFPX_E* code otherwise; nothing
+ *    is enqueued when an argument check fails.  zfpx_strerror() names codes.
+ *  - Fields are float32 arrays indexed by (x, y, z) = (longitude, latitude,
+ *    level); a view gives extents n[] and element strides stride[] (axis 0 =
+ *    longitude, normally stride 1).  Strides are non-negative.
+ *  - rate: ZFPX_RATE_F32 (0) plain float32, ZFPX_RATE_F16 (-16) float16
+ *    cast, or a ZFP rate in bits per value; the GPU codec supports 8 and 16.
+ *  - ZFP streams: every 4^d block takes exactly 4^d * rate bits, blocks back
+ *    to back in raster order of block index (axis 0 fastest); bit p of a
+ *    stream is bit (p % 8) of byte p / 8.  Partial blocks are completed by
+ *    repeating the last value along each short axis; the repeated values are
+ *    coded and dropped again on decode.
+ */
+#ifndef ZFPX_H
+#define ZFPX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define ZFPX_API __attribute__((visibility("default")))
+#else
+#define ZFPX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes ------------------------------------------------------- */
+#define ZFPX_OK 0
+#define ZFPX_EINVAL (-1)          /* bad argument: view, rate, dims, rank grid, NULL */
+#define ZFPX_ESIZE (-2)           /* caller's buffer smaller than required */
+#define ZFPX_ECUDA (-3)           /* a CUDA call or kernel launch failed */
+#define ZFPX_ETIMEOUT (-4)        /* a bounded device-side wait gave up */
+#define ZFPX_ENOMEM_BUDGET (-5)   /* request larger than the admission budget */
+#define ZFPX_ENOMEM (-6)          /* host or device allocation failed */
+
+#define ZFPX_RATE_F32 0
+#define ZFPX_RATE_F16 (-16)
+
+/* buffer layouts a call reads or writes */
+#define ZFPX_LAYOUT_SEND 0        /* per source rank, messages in destination-peer order */
+#define ZFPX_LAYOUT_RECV 1        /* per destination rank, in source-peer order */
+
+/* float16 rounding of the comparator */
+#define ZFPX_ROUND_NEAREST 0      /* IEEE round to nearest even; overflow to +-inf */
+#define ZFPX_ROUND_ZERO 1         /* toward zero; overflow to +-65504 */
+
+/* plan split modes */
+#define ZFPX_SPLIT_BALANCED 0     /* the first (extent mod parts) parts get one more */
+#define ZFPX_SPLIT_TABLE1 1       /* floor(extent / parts) each, remainder dropped (Table 1) */
+
+typedef struct {
+    int64_t n[3];       /* extents: longitude, latitude, level */
+    int64_t stride[3];  /* element strides of the same axes */
+} zfpx_view3;
+
+typedef struct zfpx_plan_s *zfpx_plan;
+
+ZFPX_API const char *zfpx_strerror(int code);
+
+/* Number of kernels this library has launched since load (all devices). */
+ZFPX_API uint64_t zfpx_launch_count(void);
+
+/* ---- plan (Sec. II-B, pencil transpositions; Table 1) --------------------
+ * Builds the message list of one transposition over a p_r x p_c rank grid,
+ * rank id = row * p_c + col.
+ *   transposition 0, z -> lambda (the all-to-all by rows): source (row j, col i)
+ *     holds lon part i of p_c x lat part j of p_r x all levels; message
+ *     (j,i) -> (j,k) is the box lon_i x lat_j x lev_k (levels split in p_c).
+ *   transposition 1, lambda -> theta (the all-to-all by columns): source
+ *     (row j, col k) holds all lon x lat_j x lev_k; message (j,k) -> (l,k) is
+ *     lon_l (lon split in p_r) x lat_j x lev_k.
+ * `src` describes the field the packs read (all simulated ranks' pencils
+ * together, as one array); `dst` the field the unpacks write; their
+ * extents must be equal, strides may differ.  dims = 3 (4x4x4 blocks) or 1
+ * (4 values along longitude).  Every message starts at a multiple of 256
+ * bytes in both layouts.  The plan is host-side; device tables are built on
+ * first use per rate (or by zfpx_plan_prepare, which should precede any
+ * stream capture).  *out receives a plan owned by the caller, freed with
+ * zfpx_plan_destroy.  Errors: ZFPX_EINVAL, ZFPX_ENOMEM. */
+ZFPX_API int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *dst,
+                     int pr, int pc, int transposition, int dims, int split_mode);
+ZFPX_API void zfpx_plan_destroy(zfpx_plan plan);
+/* Uploads the device tables for `rate` on the current device (synchronous). */
+ZFPX_API int zfpx_plan_prepare(zfpx_plan plan, int rate);
+
+ZFPX_API int zfpx_plan_num_messages(zfpx_plan plan);
+/* Geometry of message i (send order): ranks, peers, and the box x0,nx,y0,ny,z0,nz. */
+ZFPX_API int zfpx_plan_message(zfpx_plan plan, int i, int32_t ranks[4], int64_t box[6]);
+/* Bytes of message (src, dst) at `rate`; 0 if the pair exchanges nothing. */
+ZFPX_API size_t zfpx_message_bytes(zfpx_plan plan, int rate, int src, int dst);
+/* Byte offset of message (src, dst) in the given layout; -1 if none. */
+ZFPX_API int64_t zfpx_message_offset(zfpx_plan plan, int rate, int layout, int src, int dst);
+/* Total bytes of a send (= receive) buffer at `rate`. */
+ZFPX_API size_t zfpx_buffer_bytes(zfpx_plan plan, int rate);
+
+/* ---- the fused codec path -------------------------------------------------
+ * zfpx_pack_compress (Sec. I: the send buffer is compressed on the device
+ * right ahead of the exchange; Sec. II-C fixed-rate ZFP):
+ * gathers every message's box from d_src (the plan's src view), codes it at
+ * `rate` (8 or 16) and writes it at its fixed offset of the chosen layout in
+ * d_out (cap bytes).  ZFPX_LAYOUT_RECV writes each message straight into the
+ * receiver's slot (the permutation folded into the addressing).
+ * Errors: ZFPX_EINVAL, ZFPX_ESIZE (cap < zfpx_buffer_bytes), ZFPX_ECUDA. */
+ZFPX_API int zfpx_pack_compress(zfpx_plan plan, int rate, const float *d_src, uint8_t *d_out,
+                       size_t cap, int layout, void *stream);
+
+/* zfpx_decompress_unpack (Sec. I: the receiver expands the streams before it
+ * computes on them): decodes every message of d_in (len bytes, the
+ * chosen layout) and scatters the values into d_dst through the plan's dst
+ * view; padding values are dropped.  Errors as above. */
+ZFPX_API int zfpx_decompress_unpack(zfpx_plan plan, int rate, const uint8_t *d_in, size_t len,
+                           float *d_dst, int layout, void *stream);
+
+/* ---- comparators (Sec. I; Sec. IV-D, Table 1 columns Float32/Float16) ----- */
+/* float32 -> float16 cast of every message (round_mode ZFPX_ROUND_*). */
+ZFPX_API int zfpx_cast_fp16_pack(zfpx_plan plan, int round_mode, const float *d_src, uint16_t *d_out,
+                        size_t cap_bytes, int layout, void *stream);
+ZFPX_API int zfpx_fp16_unpack(zfpx_plan plan, const uint16_t *d_in, size_t len_bytes, float *d_dst,
+                     int layout, void *stream);
+/* plain float32 copy-pack and unpack */
+ZFPX_API int zfpx_pack(zfpx_plan plan, const float *d_src, float *d_out, size_t cap_bytes, int layout,
+              void *stream);
+ZFPX_API int zfpx_unpack(zfpx_plan plan, const float *d_in, size_t len_bytes, float *d_dst, int layout,
+                void *stream);
+
+/* ---- the all-to-all on one device (Sec. II-B; Sec. IV-D) ------------------
+ * recv[dst][src] <- send[src][dst] for every message of the plan at `rate`.
+ * d_send and d_recv must not overlap; len = zfpx_buffer_bytes(plan, rate). */
+ZFPX_API int zfpx_permute(zfpx_plan plan, int rate, const void *d_send, void *d_recv, size_t len,
+                 void *stream);
+
+/* ---- raw codec on one array (Sec. II-C) ------------------------------------
+ * Encodes the array of extents n[] read through element strides stride[]
+ * into d_out (cap bytes, at least zfpx_stream_bytes).  dims 1 or 3,
+ * rate 8 or 16.  Errors: ZFPX_EINVAL, ZFPX_ESIZE, ZFPX_ECUDA. */
+ZFPX_API size_t zfpx_stream_bytes(int dims, int rate, const int64_t n[3]);
+ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3],
+                const int64_t stride[3], uint8_t *d_out, size_t cap, void *stream);
+ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
+                const int64_t stride[3], float *d_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ZFPX_H */

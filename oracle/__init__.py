@@ -15,8 +15,8 @@ Contents (each module cites the passage of the paper it restates):
                  buffer permutation, and pack+compress / decompress+unpack over
                  a whole plan (Sec. I; Sec. IV-C/D).
 * ``fp16``    -- float32 -> float16 casts, round-to-nearest-even and
-                 round-toward-zero (Sec. I, "casting exchanged buffers to
-                 half-precision").
+                 round-toward-zero (Sec. I: the exchanged buffer cast to
+                 half precision).
 
 Parity status: see the header of each module.
 """

@@ -1,14 +1,14 @@
 """float32 -> float16 casts for the comparator (test infrastructure; oracle side).
 
 The paper's comparator casts the exchanged buffer to half precision and back
-(Sec. I, Sec. IV-D "Float16 truncation is modeled with negligible cast
-overhead", Sec. IV-F "casting the float32 values to float16 and back").
+(Sec. I; Sec. IV-D treats the cast as costing nothing; Sec. IV-F measures
+its error by a round trip float32 -> float16 -> float32).
 
 * ``to_f16_rn``: IEEE 754 round-to-nearest-even, overflow to +-inf, subnormal
   halves kept -- this is numpy's float32 -> float16 conversion, used as is
   (a library routine; pinned against the definition in
   tests/test_oracle_fp16.py).
-* ``to_f16_rz``: round toward zero (the paper says "truncation"): the
+* ``to_f16_rz``: round toward zero (the paper calls the cast a truncation): the
   float16 of largest magnitude not above |x|, same sign; finite values beyond
   the float16 range give +-65504 (IEEE round-toward-zero overflow), inf stays
   inf, NaN stays NaN.  Pinned by brute force over neighbouring float16 values.

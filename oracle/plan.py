@@ -3,7 +3,7 @@
 Restates Sec. II-B of the paper: a 3-D field (N_lambda x N_theta x N_z, held
 [lev][lat][lon], lon fastest) is split over a p_r x p_c rank grid; each
 transposition is an all-to-all inside one row (z->lambda) or one column
-(lambda->theta) of the grid (Sec. II-B, "all-to-all by rows / by columns").
+(lambda->theta) of the grid (Sec. II-B: all-to-all by rows, then by columns).
 
 Rank (row, col) has id row * p_c + col.
 

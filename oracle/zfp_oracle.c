@@ -3,9 +3,9 @@
  *
  * A plain, slow, scalar CPU statement of ZFP fixed-rate coding of float32
  * blocks, written step by step from the method the paper uses (Sec. II-C:
- * "non-overlapping 4^d blocks ... reversible lifting transform followed by a
- * precision reduction"; fixed-rate mode = exactly r bits per value, Sec. II-C
- * and Sec. IV-B, ZFP 1.0.1 fixed-rate) and from the cited published method
+ * the array is cut into disjoint 4^d blocks, each decorrelated by a lifting
+ * transform and then reduced in precision; fixed-rate mode spends exactly r
+ * bits per value, Sec. II-C and Sec. IV-B, ZFP 1.0.1) and from the cited published method
  * (Lindstrom 2014, the paper's reference for ZFP).  Where both are silent the
  * readings used are listed in the design doc and repeated at the step below.
  *
@@ -351,7 +351,7 @@ static void encode_block(bitw *w, int dims, int rate, const float *v)
     int zero = 1;
     if (M > 0.0 && isfinite(M)) {
         (void)frexp(M, &emax);                     /* M = f 2^emax, f in [0.5,1) */
-        zero = (emax + 127 <= 0);                  /* reading: subnormal max -> zero block */
+        zero = (emax + 127 <= 0);                  /* reading: max below 2^-127 -> zero block */
     }
     if (zero) {
         /* reading: non-finite maxima are coded as a zero block too */

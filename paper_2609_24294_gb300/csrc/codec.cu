@@ -1,0 +1,485 @@
+// Fused pack + ZFP fixed-rate encode, and fused decode + unpack, for sm_103a.
+//
+// The codec is ZFP's fixed-rate mode as the paper uses it (Sec. II-C: 4^d
+// blocks coded independently by a lifting transform and precision
+// reduction; Sec. IV-B: rate 8 and 16, fixed message size), in the readings
+// stated in include/zfpx.h and the design doc:
+//   e_max = frexp exponent of max|x|; zero block if max|x| is 0, subnormal or
+//   non-finite; q = trunc(x 2^(30-e_max)); five-step integer lifting along
+//   x, y, z; coefficients in total-sequency order; negabinary; group-tested
+//   bit planes from 31 down, cut at exactly 4^d r bits.
+//
+// Mapping to the GPU: one lane owns one block.  A warp takes 32 consecutive
+// blocks of one message, so its compressed output (or input) is one
+// contiguous run of 32 * 8r bytes, staged through shared memory in a
+// [word][lane] layout (XOR-swizzled) and moved with coalesced 8-byte
+// accesses.  The 64 coefficients of a block live in registers; their 32 bit
+// planes are formed with two in-register 32x32 bit-matrix transposes
+// (byte permutes for the 16- and 8-bit stages, masked shifts below), after
+// which each plane is one 64-bit word and group testing is a find-first-set
+// per newly significant coefficient.  Each warp processes a contiguous range
+// of 32-block chunks, so the message lookup is a forward scan.
+#include <climits>
+#include <cuda_runtime.h>
+
+#include "zfpx_internal.h"
+#include "zfpx_block.cuh"
+
+namespace zfpx {
+namespace {
+
+using namespace blk;
+
+constexpr int kWarps = 4;
+constexpr int kThreads = 32 * kWarps;
+
+// ----------------------------------------------------------------- stream I/O
+// Writer into this lane's column of a [word][lane] shared-memory tile of
+// RATE 64-bit words (XOR-swizzled so a warp's stores spread over banks).
+template <int RATE>
+struct SmemWriter {
+    uint64_t *sm;
+    uint64_t acc;
+    int nb, w, lane;
+    __device__ __forceinline__ void put(uint64_t bits, int len)   // 1 <= len <= 64
+    {
+        acc |= bits << nb;
+        int t = nb + len;
+        if (t >= 64) {
+            sm[w * 32 + (lane ^ w)] = acc;
+            w++;
+            acc = nb ? (bits >> (64 - nb)) : 0ull;
+            t -= 64;
+        }
+        nb = t;
+    }
+    __device__ __forceinline__ void finish()
+    {
+        if (nb > 0) { sm[w * 32 + (lane ^ w)] = acc; w++; }
+        for (; w < RATE; w++) sm[w * 32 + (lane ^ w)] = 0ull;
+    }
+};
+
+// Reader over this lane's column; two zero rows follow the stream.
+struct SmemReader {
+    const uint64_t *sm;
+    uint64_t w0, w1;
+    int off, widx, lane;
+    __device__ __forceinline__ void init(const uint64_t *s, int l)
+    {
+        sm = s; lane = l; off = 0; widx = 0;
+        w0 = sm[0 * 32 + (l ^ 0)];
+        w1 = sm[1 * 32 + (l ^ 1)];
+    }
+    __device__ __forceinline__ uint64_t peek() const { return off ? ((w0 >> off) | (w1 << (64 - off))) : w0; }
+    __device__ __forceinline__ void skip(int k)    // 0 <= k <= 64
+    {
+        off += k;
+        if (off >= 64) {
+            off -= 64;
+            widx++;
+            w0 = w1;
+            const int r = widx + 1;
+            w1 = sm[r * 32 + (lane ^ r)];
+        }
+    }
+};
+
+// ----------------------------------------------------------------- message walk
+__device__ __forceinline__ int find_msg(const MsgDev *msgs, int nmsg, int64_t u)
+{
+    int lo = 0, hi = nmsg - 1;               // last message with unit0 <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (msgs[mid].unit0 <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+struct MsgWalk {
+    const MsgDev *msgs;
+    int nmsg, mi;
+    int64_t next0;
+    __device__ __forceinline__ void start(const MsgDev *m, int n, int64_t u)
+    {
+        msgs = m; nmsg = n;
+        mi = find_msg(m, n, u);
+        next0 = mi + 1 < n ? m[mi + 1].unit0 : LLONG_MAX;
+    }
+    __device__ __forceinline__ void advance(int64_t u)
+    {
+        while (u >= next0) {
+            mi++;
+            next0 = mi + 1 < nmsg ? msgs[mi + 1].unit0 : LLONG_MAX;
+        }
+    }
+};
+
+// ================================================================= 3-D kernels
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
+{
+    __shared__ uint64_t smem[kWarps][RATE * 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t *wsm = smem[wid];
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t unit0 = m.unit0, nblocks = m.nblocks, src_off = m.src_off;
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
+        const int64_t b0 = (c - unit0) * 32;
+        const int nact = (int)min((int64_t)32, nblocks - b0);
+        if (lane < nact) {
+            const int b = (int)b0 + lane;
+            const int bxi = b % bxn, t = b / bxn;
+            const int byi = t % byn, bzi = t / byn;
+            const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
+            const float *base = src + src_off;
+            float x[64];
+            const bool full = vec && (x0 + 4 <= nx);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int64_t zo = (int64_t)min(z0 + k, nz - 1) * g.ss[2];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float *row = base + zo + (int64_t)min(y0 + j, ny - 1) * g.ss[1];
+                    if (full) {
+                        const float4 f = __ldg(reinterpret_cast<const float4 *>(row + x0));
+                        x[16 * k + 4 * j] = f.x; x[16 * k + 4 * j + 1] = f.y;
+                        x[16 * k + 4 * j + 2] = f.z; x[16 * k + 4 * j + 3] = f.w;
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            x[16 * k + 4 * j + i] = __ldg(row + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
+                    }
+                }
+            }
+            SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
+            encode_block3<RATE>(x, wr);
+        }
+        __syncwarp();
+        uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * RATE;
+        for (int idx = lane; idx < nact * RATE; idx += 32) {
+            const int l = idx / RATE, w = idx % RATE;
+            dst[idx] = wsm[w * 32 + (l ^ w)];
+        }
+        __syncwarp();
+    }
+}
+
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
+{
+    __shared__ uint64_t smem[kWarps][(RATE + 2) * 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t *wsm = smem[wid];
+    wsm[RATE * 32 + lane] = 0ull;
+    wsm[(RATE + 1) * 32 + lane] = 0ull;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t unit0 = m.unit0, nblocks = m.nblocks, dst_off = m.dst_off;
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
+        const int64_t b0 = (c - unit0) * 32;
+        const int nact = (int)min((int64_t)32, nblocks - b0);
+        const uint64_t *srcw = reinterpret_cast<const uint64_t *>(in + boff) + b0 * RATE;
+        __syncwarp();
+        for (int idx = lane; idx < nact * RATE; idx += 32) {
+            const int l = idx / RATE, w = idx % RATE;
+            wsm[w * 32 + (l ^ w)] = __ldg(srcw + idx);
+        }
+        __syncwarp();
+        if (lane < nact) {
+            const int b = (int)b0 + lane;
+            const int bxi = b % bxn, t = b / bxn;
+            const int byi = t % byn, bzi = t / byn;
+            const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
+            float v[64];
+            SmemReader rd;
+            rd.init(wsm, lane);
+            decode_block3<RATE>(rd, v);
+            float *base = dstf + dst_off;
+            const bool full = vec && (x0 + 4 <= nx);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (z0 + k >= nz) continue;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    if (y0 + j >= ny) continue;
+                    float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1];
+                    if (full) {
+                        *reinterpret_cast<float4 *>(row + x0) =
+                            make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 4; i++)
+                            if (x0 + i < nx) row[(int64_t)(x0 + i) * g.ds[0]] = v[16 * k + 4 * j + i];
+                    }
+                }
+            }
+        }
+    }
+}
+
+// ================================================================= 1-D kernels
+// Blocks of 4 values along x; a block is 4r bits (32 or 64), kept in one
+// register and moved with one coalesced 4- or 8-byte access per lane.
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+encode1_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t b0 = (c - m.unit0) * 32;
+        const int nact = (int)min((int64_t)32, m.nblocks - b0);
+        if (lane >= nact) continue;
+        const int nx = m.nx, bxn = m.bx, byn = m.by;
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        const int b = (int)b0 + lane;
+        const int bxi = b % bxn, t = b / bxn;
+        const int y = t % byn, z = t / byn;
+        const int x0 = 4 * bxi;
+        const float *row = src + m.src_off + (int64_t)z * g.ss[2] + (int64_t)y * g.ss[1];
+        float r[4];
+        if (vec && x0 + 4 <= nx) {
+            const float4 f = __ldg(reinterpret_cast<const float4 *>(row + x0));
+            r[0] = f.x; r[1] = f.y; r[2] = f.z; r[3] = f.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++) r[i] = __ldg(row + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
+        }
+        const uint64_t w = encode_block1<RATE>(r);
+        if (RATE == 16) reinterpret_cast<uint64_t *>(out + boff)[b] = w;
+        else reinterpret_cast<uint32_t *>(out + boff)[b] = (uint32_t)w;
+    }
+}
+
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t b0 = (c - m.unit0) * 32;
+        const int nact = (int)min((int64_t)32, m.nblocks - b0);
+        if (lane >= nact) continue;
+        const int nx = m.nx, bxn = m.bx, byn = m.by;
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        const int b = (int)b0 + lane;
+        uint64_t w;
+        if (RATE == 16) w = __ldg(reinterpret_cast<const uint64_t *>(in + boff) + b);
+        else w = __ldg(reinterpret_cast<const uint32_t *>(in + boff) + b);
+        float v[4];
+        decode_block1<RATE>(w, v);
+        const int bxi = b % bxn, t = b / bxn;
+        const int y = t % byn, z = t / byn;
+        const int x0 = 4 * bxi;
+        float *row = dstf + m.dst_off + (int64_t)z * g.ds[2] + (int64_t)y * g.ds[1];
+        if (vec && x0 + 4 <= nx) {
+            *reinterpret_cast<float4 *>(row + x0) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++)
+                if (x0 + i < nx) row[(int64_t)(x0 + i) * g.ds[0]] = v[i];
+        }
+    }
+}
+
+// ================================================================= launch
+template <class K>
+int grid_for(K kernel, int64_t nunits)
+{
+    const int occ = occupancy((const void *)kernel, kThreads);
+    const int64_t want = (nunits + kWarps - 1) / kWarps;
+    const int64_t cap = (int64_t)num_sms() * occ;
+    return (int)std::max<int64_t>(1, std::min(want, cap));
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+// vec: rows start on 16 bytes wherever a block starts (x0 multiple of 4).
+bool vec_ok(const void *ptr, const int64_t s[3], const zfpx_plan_s *p, int which /*0 src,1 dst*/)
+{
+    if (!aligned16(ptr) || s[0] != 1 || (s[1] & 3) || (s[2] & 3)) return false;
+    (void)which;
+    for (const HostMsg &m : p->msgs)
+        if (m.x0 & 3) return false;
+    return true;
+}
+
+int launch_encode(int dims, int rate, const float *src, uint8_t *out, const LaunchGeom &g, int layout, int vec,
+                  cudaStream_t st)
+{
+    if (g.nunits == 0) return ZFPX_OK;
+    if (dims == 3) {
+        if (rate == 8) encode3_kernel<8><<<grid_for(encode3_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+        else encode3_kernel<16><<<grid_for(encode3_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+    } else {
+        if (rate == 8) encode1_kernel<8><<<grid_for(encode1_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+        else encode1_kernel<16><<<grid_for(encode1_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+    }
+    count_launch();
+    return check_launch();
+}
+
+int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const LaunchGeom &g, int layout, int vec,
+                  cudaStream_t st)
+{
+    if (g.nunits == 0) return ZFPX_OK;
+    if (dims == 3) {
+        if (rate == 8) decode3_kernel<8><<<grid_for(decode3_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+        else decode3_kernel<16><<<grid_for(decode3_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+    } else {
+        if (rate == 8) decode1_kernel<8><<<grid_for(decode1_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+        else decode1_kernel<16><<<grid_for(decode1_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+    }
+    count_launch();
+    return check_launch();
+}
+
+}  // namespace
+}  // namespace zfpx
+
+using namespace zfpx;
+
+extern "C" {
+
+int zfpx_pack_compress(zfpx_plan p, int rate, const float *d_src, uint8_t *d_out, size_t cap, int layout,
+                       void *stream)
+{
+    if (!p || !d_src || !d_out || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    if (layout != ZFPX_LAYOUT_SEND && layout != ZFPX_LAYOUT_RECV) return ZFPX_EINVAL;
+    if ((uintptr_t)d_out & 15u) return ZFPX_EINVAL;
+    if ((int64_t)cap < buffer_bytes(p, rate)) return ZFPX_ESIZE;
+    DevTable *t = nullptr;
+    int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
+    if (rc) return rc;
+    LaunchGeom g{};
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
+    for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
+    const int vec = vec_ok(d_src, p->ss, p, 0) ? 1 : 0;
+    return launch_encode(p->dims, rate, d_src, d_out, g, layout, vec, (cudaStream_t)stream);
+}
+
+int zfpx_decompress_unpack(zfpx_plan p, int rate, const uint8_t *d_in, size_t len, float *d_dst, int layout,
+                           void *stream)
+{
+    if (!p || !d_in || !d_dst || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    if (layout != ZFPX_LAYOUT_SEND && layout != ZFPX_LAYOUT_RECV) return ZFPX_EINVAL;
+    if ((uintptr_t)d_in & 15u) return ZFPX_EINVAL;
+    if ((int64_t)len < buffer_bytes(p, rate)) return ZFPX_ESIZE;
+    DevTable *t = nullptr;
+    int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
+    if (rc) return rc;
+    LaunchGeom g{};
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
+    for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
+    const int vec = vec_ok(d_dst, p->ds, p, 1) ? 1 : 0;
+    return launch_decode(p->dims, rate, d_in, d_dst, g, layout, vec, (cudaStream_t)stream);
+}
+
+size_t zfpx_stream_bytes(int dims, int rate, const int64_t n[3])
+{
+    if (!n || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return 0;
+    for (int a = 0; a < 3; a++) if (n[a] < 1) return 0;
+    const int64_t bx = (n[0] + 3) / 4;
+    if (dims == 3) return (size_t)(bx * ((n[1] + 3) / 4) * ((n[2] + 3) / 4) * 8 * rate);
+    return (size_t)(bx * n[1] * n[2] * rate / 2);
+}
+
+}  // extern "C"
+
+// The raw-array entry points run the same kernels on a one-message table
+// that lives in a small per-device cache of plans keyed by shape.
+#include <map>
+#include <tuple>
+namespace zfpx {
+namespace {
+std::mutex g_raw_mu;
+std::map<std::tuple<int, int, int64_t, int64_t, int64_t, int64_t, int64_t, int64_t>, zfpx_plan> g_raw_plans;
+
+int raw_plan(int dims, const int64_t n[3], const int64_t s[3], zfpx_plan *out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ZFPX_ECUDA;
+    auto key = std::make_tuple(dev, dims, n[0], n[1], n[2], s[0], s[1], s[2]);
+    std::lock_guard<std::mutex> g(g_raw_mu);
+    auto it = g_raw_plans.find(key);
+    if (it != g_raw_plans.end()) { *out = it->second; return ZFPX_OK; }
+    if (g_raw_plans.size() > 256) {   // bounded cache
+        for (auto &kv : g_raw_plans) zfpx_plan_destroy(kv.second);
+        g_raw_plans.clear();
+    }
+    zfpx_view3 v;
+    for (int a = 0; a < 3; a++) { v.n[a] = n[a]; v.stride[a] = s[a]; }
+    int rc = zfpx_plan_create(out, &v, &v, 1, 1, 0, dims, ZFPX_SPLIT_BALANCED);
+    if (rc) return rc;
+    g_raw_plans[key] = *out;
+    return ZFPX_OK;
+}
+}  // namespace
+}  // namespace zfpx
+
+extern "C" {
+
+int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3], const int64_t stride[3],
+                uint8_t *d_out, size_t cap, void *stream)
+{
+    if (!d_in || !d_out || !n || !stride || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
+    if (cap < zfpx_stream_bytes(dims, rate, n)) return ZFPX_ESIZE;
+    zfpx_plan p = nullptr;
+    int rc = raw_plan(dims, n, stride, &p);
+    if (rc) return rc;
+    return zfpx_pack_compress(p, rate, d_in, d_out, cap + 256, ZFPX_LAYOUT_SEND, stream);
+}
+
+int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3], const int64_t stride[3],
+                float *d_out, void *stream)
+{
+    if (!d_in || !d_out || !n || !stride || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
+    if (len < zfpx_stream_bytes(dims, rate, n)) return ZFPX_ESIZE;
+    zfpx_plan p = nullptr;
+    int rc = raw_plan(dims, n, stride, &p);
+    if (rc) return rc;
+    return zfpx_decompress_unpack(p, rate, d_in, len + 256, d_out, ZFPX_LAYOUT_SEND, stream);
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <vector>
+#include <mutex>
+#include <map>
+
+#include <cuda_runtime.h>
+
+#include "../../include/zfpx.h"
+
+namespace zfpx {
+
+// One message as the kernels see it.  Element offsets are into the plan's
+// src / dst views; byte offsets into the send / receive layouts.
+struct MsgDev {
+    int64_t src_off;    // element offset of the box origin in the source view
+    int64_t dst_off;    // element offset of the box origin in the destination view
+    int64_t off[2];     // byte offset in the send [0] and receive [1] layout
+    int64_t unit0;      // first work unit (warp chunk or row quad) of this message
+    int32_t nx, ny, nz; // box extents
+    int32_t bx, by, bz; // block counts (dims 3: ceil(n/4) each; dims 1: ceil(nx/4), ny, nz)
+    int64_t nblocks;    // bx * by * bz
+};
+
+// Arguments common to every plan-driven launch.
+struct LaunchGeom {
+    const MsgDev *msgs; // device table (nmsg entries)
+    int nmsg;
+    int64_t nunits;     // total work units
+    int64_t ss[3];      // source strides (elements)
+    int64_t ds[3];      // destination strides (elements)
+};
+
+struct HostMsg {
+    int32_t src, dst, src_peer, dst_peer;
+    int64_t x0, nx, y0, ny, z0, nz;
+};
+
+// Device tables of one (rate, unit kind, device) for a plan.
+struct DevTable {
+    MsgDev *d_msgs = nullptr;
+    int64_t nunits = 0;
+};
+
+}  // namespace zfpx
+
+struct zfpx_plan_s {
+    int64_t n[3];
+    int64_t ss[3], ds[3];
+    int pr, pc, P, transposition, dims, split_mode;
+    std::vector<zfpx::HostMsg> msgs;              // send order
+    std::mutex mu;
+    std::map<long long, zfpx::DevTable> tables;   // key: (device, rate, unit kind)
+};
+
+namespace zfpx {
+
+// Work-unit kinds: codec kernels take 32 blocks (one warp) per unit; packs
+// take 4-value quads of one row per unit; the permutation 16 stream bytes.
+enum UnitKind { UNIT_BLOCKS32 = 0, UNIT_QUADS = 1, UNIT_CHUNK16 = 2 };
+
+int64_t message_bytes(const zfpx_plan_s *p, const HostMsg &m, int rate);
+int64_t buffer_bytes(const zfpx_plan_s *p, int rate);
+// Fetches (building on first use) the device table; returns ZFPX_OK or an error.
+int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out);
+
+int num_sms();
+// Resident CTAs per SM of `fn` at `threads` threads (cached per kernel).
+int occupancy(const void *fn, int threads);
+void count_launch();
+bool valid_codec_rate(int rate);
+int check_launch();   // cudaGetLastError -> ZFPX_OK / ZFPX_ECUDA
+
+}  // namespace zfpx

@@ -1,0 +1,266 @@
+"""Python binding of libzfpx.so (include/zfpx.h): argument marshalling only.
+
+Every compute call runs in the library's CUDA kernels; this module turns
+torch tensors into device pointers and byte counts, passes the current CUDA
+stream, and raises ``ZfpxError`` on a non-zero return code.  The functions
+carry the C names.  If the library has not been built the first call raises.
+"""
+import ctypes
+import os
+import re
+
+import torch
+
+from . import build as _build
+
+RATE_F32 = 0
+RATE_F16 = -16
+LAYOUT_SEND = 0
+LAYOUT_RECV = 1
+ROUND_NEAREST = 0
+ROUND_ZERO = 1
+SPLIT_BALANCED = 0
+SPLIT_TABLE1 = 1
+
+_lib = None
+
+
+class ZfpxError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__("%s: zfpx error %d (%s)" % (what, code, _strerror(code)))
+
+
+class View3(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64 * 3), ("stride", ctypes.c_int64 * 3)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """The loaded library; raises if libzfpx.so is missing (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ZfpxError(-3, "libzfpx.so is not built (run paper_2609_24294_gb300.build.build())")
+    L = ctypes.CDLL(path)
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "zfpx_strerror": ([ctypes.c_int], ctypes.c_char_p),
+        "zfpx_launch_count": ([], ctypes.c_uint64),
+        "zfpx_plan_create": ([ctypes.POINTER(vp), ctypes.POINTER(View3), ctypes.POINTER(View3), ctypes.c_int,
+                              ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_plan_destroy": ([vp], None),
+        "zfpx_plan_prepare": ([vp, ctypes.c_int], ctypes.c_int),
+        "zfpx_plan_num_messages": ([vp], ctypes.c_int),
+        "zfpx_plan_message": ([vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), i64p], ctypes.c_int),
+        "zfpx_message_bytes": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int], sz),
+        "zfpx_message_offset": ([vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int], i64),
+        "zfpx_buffer_bytes": ([vp, ctypes.c_int], sz),
+        "zfpx_pack_compress": ([vp, ctypes.c_int, vp, vp, sz, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_decompress_unpack": ([vp, ctypes.c_int, vp, sz, vp, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_cast_fp16_pack": ([vp, ctypes.c_int, vp, vp, sz, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_fp16_unpack": ([vp, vp, sz, vp, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_pack": ([vp, vp, vp, sz, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_unpack": ([vp, vp, sz, vp, ctypes.c_int, vp], ctypes.c_int),
+        "zfpx_permute": ([vp, ctypes.c_int, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_stream_bytes": ([ctypes.c_int, ctypes.c_int, i64p], sz),
+        "zfpx_encode": ([ctypes.c_int, ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
+        "zfpx_decode": ([ctypes.c_int, ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def declared_symbols():
+    """Names of every entry point declared in include/zfpx.h."""
+    hdr = os.path.join(os.path.dirname(_build.PKG), "include", "zfpx.h")
+    return re.findall(r"ZFPX_API\s+[\w\s\*]*?\b(zfpx_\w+)\s*\(", open(hdr).read())
+
+
+def _strerror(code):
+    try:
+        return lib().zfpx_strerror(int(code)).decode()
+    except Exception:
+        return "?"
+
+
+def _check(rc, what):
+    if rc != 0:
+        raise ZfpxError(rc, what)
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, what):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % what)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _nbytes(t):
+    return t.numel() * t.element_size()
+
+
+def _i64x3(v):
+    return (ctypes.c_int64 * 3)(*[int(x) for x in v])
+
+
+def field_view(t):
+    """(n, strides) in (lon, lat, lev) order of a [lev][lat][lon] float32 tensor."""
+    if t.dim() != 3:
+        raise ValueError("field must be a 3-D [lev][lat][lon] tensor")
+    return tuple(reversed(t.shape)), tuple(reversed(t.stride()))
+
+
+def zfpx_launch_count():
+    return int(lib().zfpx_launch_count())
+
+
+class Plan:
+    """A pencil-transposition plan (zfpx_plan_create / zfpx_plan_destroy)."""
+
+    def __init__(self, n, pr, pc, transposition=0, dims=3, split=SPLIT_BALANCED,
+                 src_strides=None, dst_strides=None):
+        nlon, nlat, nlev = (int(x) for x in n)
+        contiguous = (1, nlon, nlon * nlat)
+        self.n = (nlon, nlat, nlev)
+        self.src_strides = tuple(src_strides or contiguous)
+        self.dst_strides = tuple(dst_strides or contiguous)
+        self.pr, self.pc, self.transposition, self.dims = pr, pc, transposition, dims
+        sv = View3(_i64x3(self.n), _i64x3(self.src_strides))
+        dv = View3(_i64x3(self.n), _i64x3(self.dst_strides))
+        h = ctypes.c_void_p()
+        _check(lib().zfpx_plan_create(ctypes.byref(h), ctypes.byref(sv), ctypes.byref(dv), pr, pc,
+                                      transposition, dims, split), "zfpx_plan_create")
+        self._h = h
+
+    @classmethod
+    def for_fields(cls, src, pr, pc, transposition=0, dims=3, dst=None, split=SPLIT_BALANCED):
+        n, ss = field_view(src)
+        ds = field_view(dst)[1] if dst is not None else ss
+        if dst is not None and field_view(dst)[0] != n:
+            raise ValueError("src and dst fields differ in shape")
+        return cls(n, pr, pc, transposition, dims, split, ss, ds)
+
+    @property
+    def handle(self):
+        if self._h is None:
+            raise ValueError("plan destroyed")
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.zfpx_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def prepare(self, rate):
+        _check(lib().zfpx_plan_prepare(self.handle, rate), "zfpx_plan_prepare")
+
+    def num_messages(self):
+        return lib().zfpx_plan_num_messages(self.handle)
+
+    def messages(self):
+        out = []
+        ranks = (ctypes.c_int32 * 4)()
+        box = (ctypes.c_int64 * 6)()
+        for i in range(self.num_messages()):
+            _check(lib().zfpx_plan_message(self.handle, i, ranks, box), "zfpx_plan_message")
+            out.append((tuple(ranks), tuple(box)))
+        return out
+
+    def message_bytes(self, rate, src, dst):
+        return int(lib().zfpx_message_bytes(self.handle, rate, src, dst))
+
+    def message_offset(self, rate, layout, src, dst):
+        return int(lib().zfpx_message_offset(self.handle, rate, layout, src, dst))
+
+    def buffer_bytes(self, rate):
+        return int(lib().zfpx_buffer_bytes(self.handle, rate))
+
+    def _check_field(self, t, strides, what):
+        if t.dtype != torch.float32:
+            raise ValueError("%s must be float32" % what)
+        n, s = field_view(t)
+        if tuple(n) != self.n or tuple(s) != tuple(strides):
+            raise ValueError("%s shape/strides %s/%s do not match the plan %s/%s" % (what, n, s, self.n, strides))
+
+
+def zfpx_pack_compress(plan, rate, src, out, layout=LAYOUT_SEND, stream=None):
+    plan._check_field(src, plan.src_strides, "src")
+    _check(lib().zfpx_pack_compress(plan.handle, rate, _dev(src, "src"), _dev(out, "out"), _nbytes(out), layout,
+                                    _stream(stream)), "zfpx_pack_compress")
+
+
+def zfpx_decompress_unpack(plan, rate, inp, dst, layout=LAYOUT_RECV, stream=None):
+    plan._check_field(dst, plan.dst_strides, "dst")
+    _check(lib().zfpx_decompress_unpack(plan.handle, rate, _dev(inp, "in"), _nbytes(inp), _dev(dst, "dst"), layout,
+                                        _stream(stream)), "zfpx_decompress_unpack")
+
+
+def zfpx_cast_fp16_pack(plan, round_mode, src, out, layout=LAYOUT_SEND, stream=None):
+    plan._check_field(src, plan.src_strides, "src")
+    _check(lib().zfpx_cast_fp16_pack(plan.handle, round_mode, _dev(src, "src"), _dev(out, "out"), _nbytes(out),
+                                     layout, _stream(stream)), "zfpx_cast_fp16_pack")
+
+
+def zfpx_fp16_unpack(plan, inp, dst, layout=LAYOUT_RECV, stream=None):
+    plan._check_field(dst, plan.dst_strides, "dst")
+    _check(lib().zfpx_fp16_unpack(plan.handle, _dev(inp, "in"), _nbytes(inp), _dev(dst, "dst"), layout,
+                                  _stream(stream)), "zfpx_fp16_unpack")
+
+
+def zfpx_pack(plan, src, out, layout=LAYOUT_SEND, stream=None):
+    plan._check_field(src, plan.src_strides, "src")
+    _check(lib().zfpx_pack(plan.handle, _dev(src, "src"), _dev(out, "out"), _nbytes(out), layout, _stream(stream)),
+           "zfpx_pack")
+
+
+def zfpx_unpack(plan, inp, dst, layout=LAYOUT_RECV, stream=None):
+    plan._check_field(dst, plan.dst_strides, "dst")
+    _check(lib().zfpx_unpack(plan.handle, _dev(inp, "in"), _nbytes(inp), _dev(dst, "dst"), layout, _stream(stream)),
+           "zfpx_unpack")
+
+
+def zfpx_permute(plan, rate, send, recv, stream=None):
+    _check(lib().zfpx_permute(plan.handle, rate, _dev(send, "send"), _dev(recv, "recv"),
+                              min(_nbytes(send), _nbytes(recv)), _stream(stream)), "zfpx_permute")
+
+
+def zfpx_stream_bytes(dims, rate, n):
+    return int(lib().zfpx_stream_bytes(dims, rate, _i64x3(n)))
+
+
+def zfpx_encode(dims, rate, src, out, stream=None):
+    if src.dtype != torch.float32:
+        raise ValueError("src must be float32")
+    n, s = field_view(src)
+    _check(lib().zfpx_encode(dims, rate, _dev(src, "src"), _i64x3(n), _i64x3(s), _dev(out, "out"), _nbytes(out),
+                             _stream(stream)), "zfpx_encode")
+
+
+def zfpx_decode(dims, rate, inp, dst, stream=None):
+    if dst.dtype != torch.float32:
+        raise ValueError("dst must be float32")
+    n, s = field_view(dst)
+    _check(lib().zfpx_decode(dims, rate, _dev(inp, "in"), _nbytes(inp), _i64x3(n), _i64x3(s), _dev(dst, "dst"),
+                             _stream(stream)), "zfpx_decode")

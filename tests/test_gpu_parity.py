@@ -1,0 +1,274 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact everywhere: compressed bytes (Sec. II-C fixed-rate streams, at
+their fixed offsets), decompressed float32 values compared as bit patterns,
+float16 casts and the permutation (Sec. II-B).
+"""
+import numpy as np
+import pytest
+import torch
+
+import fieldgen
+from oracle import codec as oc
+from oracle import packs as op
+from oracle import plan as opl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def z():
+    from paper_2609_24294_gb300 import build, zfpx
+    build.build()
+    zfpx.lib()
+    return zfpx
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def same_bits(a, b):
+    a = np.asarray(a, dtype=np.float32)
+    b = np.asarray(b, dtype=np.float32)
+    assert a.shape == b.shape
+    diff = a.view(np.uint32) != b.view(np.uint32)
+    assert not diff.any(), "%d of %d values differ, first at %s" % (diff.sum(), diff.size, np.argwhere(diff)[0])
+
+
+def smooth_field(shape, seed, offset=0.0):
+    rng = np.random.default_rng(seed)
+    nz, ny, nx = shape
+    x = np.linspace(0, 2 * np.pi, nx)[None, None, :]
+    y = np.linspace(0, np.pi, ny)[None, :, None]
+    zz = np.linspace(0, 1, nz)[:, None, None]
+    f = np.sin(3 * x + zz) * np.cos(2 * y) + 0.3 * np.sin(7 * x * y + 2 * zz) + 0.01 * rng.standard_normal(shape)
+    return (offset + f).astype(np.float32)
+
+
+# ---------------------------------------------------------------- raw arrays
+@pytest.mark.parametrize("dims", [3, 1])
+@pytest.mark.parametrize("rate", [16, 8])
+def test_config1_raw_codec(z, dims, rate):
+    f = fieldgen.config1_field()                   # 64 lon x 32 lat x 8 levels
+    n = (64, 32, 8)
+    nb = z.zfpx_stream_bytes(dims, rate, n)
+    out = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    z.zfpx_encode(dims, rate, dev(f), out)
+    ref = oc.encode_array(dims, rate, f)
+    g = host(out)
+    assert g.tobytes() == ref.tobytes(), "first differing byte %d" % int(np.argmax(g != ref))
+    dec = torch.full_like(dev(f), float("nan"))
+    z.zfpx_decode(dims, rate, out, dec)
+    rdec = np.empty_like(f)
+    oc.decode_array(dims, rate, ref, rdec)
+    same_bits(host(dec), rdec)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 5), (7, 5, 3), (2, 9, 33), (17, 6, 130)])
+@pytest.mark.parametrize("dims", [3, 1])
+def test_small_and_ragged_arrays(z, shape, dims):
+    x = smooth_field(shape, 3, offset=10.0)
+    n = tuple(reversed(shape))
+    for rate in (8, 16):
+        out = torch.zeros(z.zfpx_stream_bytes(dims, rate, n), dtype=torch.uint8, device="cuda")
+        z.zfpx_encode(dims, rate, dev(x), out)
+        ref = oc.encode_array(dims, rate, x)
+        assert host(out).tobytes() == ref.tobytes()
+        dec = torch.full(shape, float("nan"), device="cuda")
+        z.zfpx_decode(dims, rate, out, dec)
+        rdec = np.empty_like(x)
+        oc.decode_array(dims, rate, ref, rdec)
+        same_bits(host(dec), rdec)
+
+
+def _special_values(shape, seed):
+    rng = np.random.default_rng(seed)
+    x = (rng.standard_normal(shape) * 10.0 ** rng.integers(-40, 38, shape)).astype(np.float32)
+    nz, ny, nx = shape
+    x[0:4, 0:4, 0:4] = 0.0                               # zero block
+    x[0:4, 0:4, 4:8] = -0.0
+    x[0:4, 4:8, 0:4] = 3.25                              # constant block
+    x[0:4, 4:8, 4:8] = np.float32(2e-39)                 # subnormal, above 2^-127
+    x[4:8, 0:4, 0:4] = np.float32(5e-40)                 # subnormal, below 2^-127
+    x[4:8, 0:4, 4:8] = np.float32(3.4e38) * np.sign(rng.standard_normal((4, 4, 4))).astype(np.float32)
+    x[4:8, 4:8, 0:4] = rng.standard_normal((4, 4, 4)).astype(np.float32)
+    x[5, 5, 1] = np.inf                                  # non-finite blocks
+    x[4:8, 4:8, 4:8] = rng.standard_normal((4, 4, 4)).astype(np.float32)
+    x[6, 6, 6] = np.nan
+    x[0:4, 8:12, 0:4] = 1e-30 * rng.standard_normal((4, 4, 4)).astype(np.float32)   # small e_max
+    return x
+
+
+def test_special_values(z):
+    x = _special_values((8, 12, 16), 5)
+    n = (16, 12, 8)
+    for dims in (3, 1):
+        for rate in (8, 16):
+            out = torch.zeros(z.zfpx_stream_bytes(dims, rate, n), dtype=torch.uint8, device="cuda")
+            z.zfpx_encode(dims, rate, dev(x), out)
+            ref = oc.encode_array(dims, rate, x)
+            assert host(out).tobytes() == ref.tobytes()
+            dec = torch.empty_like(dev(x))
+            z.zfpx_decode(dims, rate, out, dec)
+            rdec = np.empty_like(x)
+            oc.decode_array(dims, rate, ref, rdec)
+            same_bits(host(dec), rdec)
+
+
+def test_random_streams_decode_like_oracle(z):
+    # the decoder is defined on any byte stream
+    rng = np.random.default_rng(11)
+    n = (32, 8, 8)
+    for dims in (3, 1):
+        for rate in (8, 16):
+            nb = z.zfpx_stream_bytes(dims, rate, n)
+            s = rng.integers(0, 256, nb, dtype=np.uint8)
+            dec = torch.empty((8, 8, 32), device="cuda")
+            z.zfpx_decode(dims, rate, dev(s), dec)
+            rdec = np.empty((8, 8, 32), dtype=np.float32)
+            oc.decode_array(dims, rate, s, rdec)
+            same_bits(host(dec), rdec)
+
+
+# ---------------------------------------------------------------- plans
+PLANS = [((17, 23, 37), 3, 2), ((8, 32, 64), 2, 2), ((5, 9, 11), 2, 3), ((20, 16, 48), 1, 4)]
+
+
+@pytest.mark.parametrize("t", [0, 1])
+@pytest.mark.parametrize("dims", [3, 1])
+@pytest.mark.parametrize("shape,pr,pc", PLANS)
+def test_pack_compress_permute_decompress(z, t, dims, shape, pr, pc):
+    x = smooth_field(shape, 7, offset=250.0)
+    nz, ny, nx = shape
+    xd = dev(x)
+    oplan = opl.Plan(nx, ny, nz, pr, pc, t, dims)
+    # destination with a padded row pitch (e.g. room for an in-place real FFT)
+    dst_store = torch.full((nz, ny, nx + 6), float("nan"), device="cuda")
+    dst = dst_store[:, :, :nx]
+    plan = z.Plan.for_fields(xd, pr, pc, t, dims, dst=dst)
+    for rate in (8, 16):
+        ref_send = op.pack(oplan, rate, x, which="send")
+        ref_recv = op.permute(oplan, rate, ref_send)
+        send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+        z.zfpx_pack_compress(plan, rate, xd, send, z.LAYOUT_SEND)
+        assert host(send).tobytes() == ref_send.tobytes()
+        recv = torch.zeros_like(send)
+        z.zfpx_permute(plan, rate, send, recv)
+        assert host(recv).tobytes() == ref_recv.tobytes()
+        folded = torch.zeros_like(send)
+        z.zfpx_pack_compress(plan, rate, xd, folded, z.LAYOUT_RECV)
+        assert torch.equal(folded, recv)
+        dst.fill_(float("nan"))
+        z.zfpx_decompress_unpack(plan, rate, recv, dst, z.LAYOUT_RECV)
+        rdst = np.full_like(x, np.nan)
+        op.unpack(oplan, rate, ref_recv, rdst)
+        same_bits(host(dst), rdst)
+        # padding columns untouched
+        assert torch.isnan(dst_store[:, :, nx:]).all()
+
+
+@pytest.mark.parametrize("t", [0, 1])
+def test_comparator_packs(z, t):
+    rng = np.random.default_rng(9)
+    shape = (13, 10, 22)
+    x = (rng.standard_normal(shape) * 10.0 ** rng.integers(-9, 6, shape)).astype(np.float32)
+    x.reshape(-1)[:6] = [65504.0, 65520.0, -1e6, 6e-8, np.inf, -np.inf]
+    nz, ny, nx = shape
+    xd = dev(x)
+    oplan = opl.Plan(nx, ny, nz, 2, 3, t, 3)
+    plan = z.Plan.for_fields(xd, 2, 3, t, 3)
+    # float32
+    send = torch.zeros(plan.buffer_bytes(z.RATE_F32) // 4, dtype=torch.float32, device="cuda")
+    z.zfpx_pack(plan, xd, send)
+    ref = op.pack(oplan, 0, x)
+    assert host(send).view(np.uint8).tobytes() == ref.tobytes()
+    recv = torch.zeros_like(send)
+    z.zfpx_permute(plan, z.RATE_F32, send, recv)
+    assert host(recv).view(np.uint8).tobytes() == op.permute(oplan, 0, ref).tobytes()
+    out = torch.full_like(xd, float("nan"))
+    z.zfpx_unpack(plan, recv, out)
+    same_bits(host(out), x)
+    # float16, both roundings
+    for mode, name in ((z.ROUND_NEAREST, "rn"), (z.ROUND_ZERO, "rz")):
+        h = torch.zeros(plan.buffer_bytes(z.RATE_F16) // 2, dtype=torch.int16, device="cuda")
+        z.zfpx_cast_fp16_pack(plan, mode, xd, h)
+        ref = op.pack(oplan, -16, x, round_mode=name)
+        assert host(h).view(np.uint8).tobytes() == ref.tobytes(), name
+        hr = torch.zeros_like(h)
+        z.zfpx_permute(plan, z.RATE_F16, h, hr)
+        out = torch.full_like(xd, float("nan"))
+        z.zfpx_fp16_unpack(plan, hr, out)
+        rout = np.full_like(x, np.nan)
+        op.unpack(oplan, -16, op.permute(oplan, -16, ref), rout)
+        same_bits(host(out), rout)
+
+
+def test_strided_sources(z):
+    rng = np.random.default_rng(12)
+    big = smooth_field((12, 20, 48), 4)
+    # unaligned x offset: vector loads off
+    src = dev(big)[1:10, 2:19, 3:40]
+    x = np.ascontiguousarray(big[1:10, 2:19, 3:40])
+    # longitude not the fastest axis: [lev][lon][lat] storage viewed as [lev][lat][lon]
+    alt_store = dev(np.ascontiguousarray(np.transpose(x, (0, 2, 1))))
+    alt = alt_store.permute(0, 2, 1)
+    for s in (src, alt):
+        nz, ny, nx = x.shape
+        oplan = opl.Plan(nx, ny, nz, 2, 2, 0, 3)
+        plan = z.Plan.for_fields(s, 2, 2, 0, 3)
+        for rate in (8, 16):
+            send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+            z.zfpx_pack_compress(plan, rate, s, send)
+            assert host(send).tobytes() == op.pack(oplan, rate, x).tobytes()
+    del rng
+
+
+# ---------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def config2():
+    return fieldgen.config2_field()
+
+
+@pytest.mark.parametrize("rate", [8, 16])
+def test_config2_full_size_sampled(z, config2, rate):
+    """1280 x 640 x 137, 8 x 8 ranks, z->lambda: the launch the benchmark
+    times, checked message by message on a sample (the oracle codes one
+    message in well under a second) and as a whole by invariants."""
+    x = config2
+    xd = dev(x)
+    nz, ny, nx = x.shape
+    plan = z.Plan.for_fields(xd, 8, 8, 0, 3)
+    oplan = opl.Plan(nx, ny, nz, 8, 8, 0, 3)
+    send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+    z.zfpx_pack_compress(plan, rate, xd, send)
+    recv = torch.zeros_like(send)
+    z.zfpx_permute(plan, rate, send, recv)
+    folded = torch.zeros_like(send)
+    z.zfpx_pack_compress(plan, rate, xd, folded, z.LAYOUT_RECV)
+    assert torch.equal(folded, recv)
+    out = torch.full_like(xd, float("nan"))
+    z.zfpx_decompress_unpack(plan, rate, recv, out)
+    so, ro, total = oplan.layout(rate)
+    hs = host(send)
+    ho = host(out)
+    rng = np.random.default_rng(rate)
+    sample = [oplan.messages[0], oplan.messages[-1]] + [oplan.messages[i] for i in
+                                                        rng.choice(len(oplan.messages), 4, replace=False)]
+    for m in sample:
+        nb = opl.message_bytes(m, rate, 3)
+        ref = op.message_stream(oplan, rate, x, m)
+        o = so[(m.src, m.dst)]
+        assert hs[o:o + nb].tobytes() == ref.tobytes(), (m.src, m.dst)
+        box = np.empty((m.nz, m.ny, m.nx), dtype=np.float32)
+        oc.decode_array(3, rate, ref, box)
+        same_bits(ho[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx], box)
+    # whole field: every value written, finite, within the rate's accuracy
+    assert np.isfinite(ho).all()
+    rel = np.linalg.norm(ho.astype(np.float64) - x) / np.linalg.norm(x.astype(np.float64))
+    assert rel < (5e-3 if rate == 8 else 5e-5)
