@@ -60,6 +60,18 @@ struct SmemWriter {
     }
 };
 
+// Bit planes of one block, parked in this lane's column of a [plane][lane]
+// shared-memory tile (conflict-free: a warp touches 32 consecutive words).
+struct SmemPlanes {
+    uint64_t *sm;
+    int lane;
+    __device__ __forceinline__ void store(int k, uint64_t X) { sm[k * 32 + lane] = X; }
+    __device__ __forceinline__ uint64_t load(int k) const { return sm[k * 32 + lane]; }
+    // the same tile seen as 64 32-bit words per lane
+    __device__ __forceinline__ uint32_t *words() { return reinterpret_cast<uint32_t *>(sm); }
+    __device__ __forceinline__ int word_index(int i) const { return (i >> 1) * 64 + 2 * lane + (i & 1); }
+};
+
 // Reader over this lane's column; two zero rows follow the stream.
 struct SmemReader {
     const uint64_t *sm;
@@ -121,8 +133,10 @@ __global__ void __launch_bounds__(kThreads)
 encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
 {
     __shared__ uint64_t smem[kWarps][RATE * 32];
+    __shared__ uint64_t splanes[kWarps][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
+    SmemPlanes pl{splanes[wid], lane};
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
     int64_t c = gw * g.nunits / W;
@@ -164,7 +178,7 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
                 }
             }
             SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
-            encode_block3<RATE>(x, wr);
+            encode_block3<RATE>(x, wr, pl);
         }
         __syncwarp();
         uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * RATE;
@@ -181,8 +195,10 @@ __global__ void __launch_bounds__(kThreads)
 decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
     __shared__ uint64_t smem[kWarps][(RATE + 2) * 32];
+    __shared__ uint64_t splanes[kWarps][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
+    SmemPlanes pl{splanes[wid], lane};
     wsm[RATE * 32 + lane] = 0ull;
     wsm[(RATE + 1) * 32 + lane] = 0ull;
     const int64_t W = (int64_t)gridDim.x * kWarps;
@@ -215,7 +231,7 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
             float v[64];
             SmemReader rd;
             rd.init(wsm, lane);
-            decode_block3<RATE>(rd, v);
+            decode_block3<RATE>(rd, v, pl);
             float *base = dstf + dst_off;
             const bool full = vec && (x0 + 4 <= nx);
 #pragma unroll

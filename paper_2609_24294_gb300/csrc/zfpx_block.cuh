@@ -47,14 +47,6 @@ ZFPX_HD float u2f(uint32_t u)
     float x; std::memcpy(&x, &u, 4); return x;
 #endif
 }
-ZFPX_HD double ll2d(long long v)
-{
-#ifdef __CUDA_ARCH__
-    return __longlong_as_double(v);
-#else
-    double d; std::memcpy(&d, &v, 8); return d;
-#endif
-}
 ZFPX_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t sel)
 {
 #ifdef __CUDA_ARCH__
@@ -83,43 +75,74 @@ ZFPX_HD int32_t wadd(int32_t a, int32_t b) { return (int32_t)((uint32_t)a + (uin
 ZFPX_HD int32_t wsub(int32_t a, int32_t b) { return (int32_t)((uint32_t)a - (uint32_t)b); }
 
 // ----------------------------------------------------------------- block float
-// q = trunc(x 2^(30 - e_max)), e_max = E - 126 with E the biased exponent of
-// a normal max.  For E >= 29 the scale is a normal float and the product is
-// exact wherever its integer part is non-zero; smaller E go through double.
-ZFPX_HD int32_t quantize(float x, int E)
+ZFPX_HD int32_t f2i_rz(float y)
 {
-    if (E >= 29) {
-        const float y = x * u2f((uint32_t)(283 - E) << 23);
 #ifdef __CUDA_ARCH__
-        return __float2int_rz(y);
-#else
-        return (int32_t)y;
-#endif
-    }
-    const double y = (double)x * ll2d((long long)(1023 + 156 - E) << 52);
-#ifdef __CUDA_ARCH__
-    return __double2int_rz(y);
+    return __float2int_rz(y);
 #else
     return (int32_t)y;
 #endif
 }
-// x = (float)(q 2^(e_max - 30)), e = e_max + 127: for e >= 31 the scale is a
-// normal float and rounding q once to float then scaling is exact.
-ZFPX_HD float dequantize(int32_t q, int e)
+ZFPX_HD float i2f_rn(int32_t q)
 {
-    if (e >= 31) {
 #ifdef __CUDA_ARCH__
-        return __int2float_rn(q) * u2f((uint32_t)(e - 30) << 23);
+    return __int2float_rn(q);
 #else
-        return (float)q * u2f((uint32_t)(e - 30) << 23);
+    return (float)q;
 #endif
+}
+
+// q = trunc(x 2^(30 - e_max)), e_max = E - 126 (E: biased exponent of the
+// block maximum, 0..254).  The scale 2^(156 - E) is applied as two exact
+// power-of-two products, (x * s1) * s2 with s1 = 1 for E >= 29 and 2^64
+// below, so every factor is a normal float and no product rounds wherever
+// the integer part is non-zero.  No branch, no double precision.
+struct QuantScale {
+    float s1, s2;
+    ZFPX_HD explicit QuantScale(int E)
+    {
+        const bool small = E < 29;
+        s1 = small ? 18446744073709551616.0f : 1.0f;                 // 2^64
+        s2 = u2f((uint32_t)((small ? 92 - E : 156 - E) + 127) << 23);
     }
-    const double y = (double)q * ll2d((long long)(1023 + e - 157) << 52);
+    ZFPX_HD int32_t operator()(float x) const { return f2i_rz((x * s1) * s2); }
+};
+
+ZFPX_HD float u2f_rn(uint32_t a)
+{
 #ifdef __CUDA_ARCH__
-    return __double2float_rn(y);
+    return __uint2float_rn(a);
 #else
-    return (float)y;
+    return (float)a;
 #endif
+}
+
+// x = (float)(q 2^(e - 157)) rounded once to nearest even (e = e_max + 127).
+// For e >= 31 the scale is a normal float and converting q then scaling is
+// exact after the conversion's single rounding.
+ZFPX_HD float dequantize_fast(int32_t q, float scale) { return i2f_rn(q) * scale; }
+ZFPX_HD float dequant_scale(int e) { return u2f((uint32_t)(e - 30) << 23); }
+
+// The rare headers e < 31, where the result may be subnormal: integer
+// rounding at the subnormal quantum 2^-149, no double precision.
+ZFPX_HD float dequantize_small(int32_t q, int e)
+{
+    if (q == 0) return 0.0f;
+    const uint32_t sign = q < 0 ? 0x80000000u : 0u;
+    const uint32_t a = q < 0 ? 0u - (uint32_t)q : (uint32_t)q;        // |q| <= 2^31
+    uint32_t bits;
+    if ((uint64_t)a >= (1ull << (31 - e))) {
+        // normal result (>= 2^-126): the conversion rounds once, the two
+        // power-of-two scalings (2^-64, then 2^(e-93)) are exact
+        bits = f2u((u2f_rn(a) * 5.42101086242752217e-20f) * u2f((uint32_t)(e + 34) << 23));
+    } else if (e >= 8) {
+        bits = a << (e - 8);                                             // exact subnormal
+    } else {
+        const int d = 8 - e;                                             // a / 2^d to nearest even
+        const uint32_t m = a >> d, rem = a & ((1u << d) - 1u), half = 1u << (d - 1);
+        bits = m + ((rem > half || (rem == half && (m & 1u))) ? 1u : 0u);
+    }
+    return u2f(bits | sign);
 }
 
 // ----------------------------------------------------------------- transform
@@ -282,11 +305,62 @@ ZFPX_HD uint64_t decode_plane(Reader &rd, int &n, int &R)
     return X;
 }
 
+// Fast paths for a plane that is known to fit: every plane of S = 64
+// coefficients costs at most 127 bits, so with R >= 127 no bit can hit the
+// budget and the per-bit budget checks drop out.  Same bits as code_plane /
+// decode_plane.
+template <int S, class Writer>
+ZFPX_HD void code_plane_fit(Writer &wr, uint64_t X, int &n, int &R)
+{
+    if (n >= S) { wr.put(X, S); R -= S; return; }
+    uint64_t rest = X >> n;
+    if (!rest) { wr.put(X & low_mask(n), n + 1); R -= n + 1; return; }    // verbatim, then G = 0
+    if (n > 0) { wr.put(X & low_mask(n), n); R -= n; }
+    for (;;) {
+        const int p = lowest_set(rest);
+        if (n + p == S - 1) { wr.put(1ull, p + 1); R -= p + 1; n = S; return; }   // last one implied
+        wr.put(1ull | (1ull << (p + 1)), p + 2);
+        R -= p + 2;
+        n += p + 1;
+        rest >>= p + 1;
+        if (!rest) { wr.put(0ull, 1); R -= 1; return; }                  // n < S here
+    }
+}
+
+template <int S, class Reader>
+ZFPX_HD uint64_t decode_plane_fit(Reader &rd, int &n, int &R)
+{
+    uint64_t w = rd.peek();
+    if (n >= S) { rd.skip(S); R -= S; return w; }
+    uint64_t X = w & low_mask(n);
+    if (!((w >> n) & 1ull)) { rd.skip(n + 1); R -= n + 1; return X; }   // verbatim, then G = 0
+    rd.skip(n + 1);
+    R -= n + 1;
+    for (;;) {                                                            // a group bit 1 was read
+        const int lim = S - 1 - n;
+        w = rd.peek();
+        const int tz = w ? lowest_set(w) : 64;
+        if (tz >= lim) {                                                  // only the implied one left
+            rd.skip(lim); R -= lim;
+            X |= 1ull << (S - 1);
+            n = S;
+            return X;
+        }
+        X |= 1ull << (n + tz);
+        n += tz + 1;                                                      // n < S
+        const uint64_t g = (w >> (tz + 1)) & 1ull;                         // the next group bit
+        rd.skip(tz + 2); R -= tz + 2;
+        if (!g) return X;
+    }
+}
+
 // ----------------------------------------------------------------- 3-D block
 // Encodes 64 values (x[i + 4j + 16k]) into exactly 64 RATE bits through wr;
-// wr.finish() is called once at the end to flush and zero-fill.
-template <int RATE, class Writer>
-ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr)
+// wr.finish() flushes and zero-fills.  The 32 bit planes are parked in `pl`
+// (store(k, X) / load(k)) so the coding loop over planes stays rolled and
+// the kernel's code stays small.
+template <int RATE, class Writer, class Planes>
+ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
 {
     constexpr int kSeq[64] = ZFPX_SEQ3;
     uint32_t amax = 0;
@@ -298,9 +372,10 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr)
     // E = e_max + 126; a subnormal max in [2^-127, 2^-126) has e_max = -126 too
     const int E = (int)(amax >> 23);
     if (amax < 0x00400000u || E == 255) { wr.finish(); return; }
+    const QuantScale qs(E);
     int32_t q[64];
 #pragma unroll
-    for (int i = 0; i < 64; i++) q[i] = quantize(x[i], E);
+    for (int i = 0; i < 64; i++) q[i] = qs(x[i]);
     xform3_fwd(q);
     uint32_t lo[32], hi[32];
 #pragma unroll
@@ -310,17 +385,21 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr)
     }
     transpose32(lo);
     transpose32(hi);
+#pragma unroll
+    for (int k = 0; k < 32; k++) pl.store(k, ((uint64_t)hi[k] << 32) | lo[k]);
     wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
     int n = 0, R = 64 * RATE - 9;
-#pragma unroll
-    for (int k = 31; k >= 0; k--) {
-        if (R > 0) code_plane<64>(wr, ((uint64_t)hi[k] << 32) | lo[k], n, R);
+#pragma unroll 1
+    for (int k = 31; k >= 0 && R > 0; k--) {
+        const uint64_t X = pl.load(k);
+        if (R >= 127) code_plane_fit<64>(wr, X, n, R);
+        else code_plane<64>(wr, X, n, R);
     }
     wr.finish();
 }
 
-template <int RATE, class Reader>
-ZFPX_HD void decode_block3(Reader &rd, float (&x)[64])
+template <int RATE, class Reader, class Planes>
+ZFPX_HD void decode_block3(Reader &rd, float (&x)[64], Planes &pl)
 {
     constexpr int kSeq[64] = ZFPX_SEQ3;
     const uint64_t head = rd.peek();
@@ -331,12 +410,18 @@ ZFPX_HD void decode_block3(Reader &rd, float (&x)[64])
     }
     const int e = (int)((head >> 1) & 0xffu);
     rd.skip(9);
-    uint32_t lo[32], hi[32];
     int n = 0, R = 64 * RATE - 9;
-#pragma unroll
+#pragma unroll 1
     for (int k = 31; k >= 0; k--) {
         uint64_t X = 0;
-        if (R > 0) X = decode_plane<64>(rd, n, R);
+        if (R >= 127) X = decode_plane_fit<64>(rd, n, R);
+        else if (R > 0) X = decode_plane<64>(rd, n, R);
+        pl.store(k, X);
+    }
+    uint32_t lo[32], hi[32];
+#pragma unroll
+    for (int k = 0; k < 32; k++) {
+        const uint64_t X = pl.load(k);
         lo[k] = (uint32_t)X;
         hi[k] = (uint32_t)(X >> 32);
     }
@@ -349,8 +434,21 @@ ZFPX_HD void decode_block3(Reader &rd, float (&x)[64])
         q[kSeq[32 + t]] = from_negabinary(hi[t]);
     }
     xform3_inv(q);
+    if (e >= 31) {
+        const float sc = dequant_scale(e);
 #pragma unroll
-    for (int i = 0; i < 64; i++) x[i] = dequantize(q[i], e);
+        for (int i = 0; i < 64; i++) x[i] = dequantize_fast(q[i], sc);
+    } else {
+        // rare: park q in the plane tile and convert in a rolled loop, so the
+        // common path above never pays for the slow one
+        uint32_t *w = pl.words();
+#pragma unroll
+        for (int i = 0; i < 64; i++) w[pl.word_index(i)] = (uint32_t)q[i];
+#pragma unroll 1
+        for (int i = 0; i < 64; i++) w[pl.word_index(i)] = f2u(dequantize_small((int32_t)w[pl.word_index(i)], e));
+#pragma unroll
+        for (int i = 0; i < 64; i++) x[i] = u2f(w[pl.word_index(i)]);
+    }
 }
 
 // ----------------------------------------------------------------- 1-D block
@@ -379,7 +477,8 @@ ZFPX_HD uint64_t encode_block1(const float (&x)[4])
     const int E = (int)(amax >> 23);
     RegWriter wr{0ull, 0};
     if (amax < 0x00400000u || E == 255) return 0ull;
-    int32_t q0 = quantize(x[0], E), q1 = quantize(x[1], E), q2 = quantize(x[2], E), q3 = quantize(x[3], E);
+    const QuantScale qs(E);
+    int32_t q0 = qs(x[0]), q1 = qs(x[1]), q2 = qs(x[2]), q3 = qs(x[3]);
     lift_fwd(q0, q1, q2, q3);
     const uint32_t u0 = to_negabinary(q0), u1 = to_negabinary(q1);
     const uint32_t u2 = to_negabinary(q2), u3 = to_negabinary(q3);
@@ -416,8 +515,14 @@ ZFPX_HD void decode_block1(uint64_t w, float (&x)[4])
     int32_t q0 = from_negabinary(u[0]), q1 = from_negabinary(u[1]);
     int32_t q2 = from_negabinary(u[2]), q3 = from_negabinary(u[3]);
     lift_inv(q0, q1, q2, q3);
-    x[0] = dequantize(q0, e); x[1] = dequantize(q1, e);
-    x[2] = dequantize(q2, e); x[3] = dequantize(q3, e);
+    if (e >= 31) {
+        const float sc = dequant_scale(e);
+        x[0] = dequantize_fast(q0, sc); x[1] = dequantize_fast(q1, sc);
+        x[2] = dequantize_fast(q2, sc); x[3] = dequantize_fast(q3, sc);
+    } else {
+        x[0] = dequantize_small(q0, e); x[1] = dequantize_small(q1, e);
+        x[2] = dequantize_small(q2, e); x[3] = dequantize_small(q3, e);
+    }
 }
 
 }  // namespace blk
