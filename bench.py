@@ -48,10 +48,8 @@ def log(*a):
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_2609_24294_gb300 import multirank
+    return multirank.env()
 
 
 def measured_peak():
@@ -211,11 +209,10 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    from paper_2609_24294_gb300 import multirank
+    ws, rank, local = multirank.env()
     torch.cuda.set_device(local)
+    multirank.init()
     from paper_2609_24294_gb300 import build, zfpx as z
     build.build()
     z.lib()
@@ -253,10 +250,7 @@ def run_gpu(args):
         if ev is not None:
             ev[k].record(stream)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = multirank.barrier
 
     for _ in range(args.warmup):
         step()
@@ -283,12 +277,8 @@ def run_gpu(args):
     for i in range(args.steps):
         for j, n in enumerate(names):
             per_kernel[n] += evs[i][j].elapsed_time(evs[i][j + 1])
-    elapsed = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        barrier()
-        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
-    total_ms = float(elapsed.item())
+    barrier()
+    total_ms = multirank.max_over_ranks(total_ms, device="cuda")
     ms_per_step = total_ms / args.steps
     pass_bytes = 2 * len(RATES) * field_bytes            # f32 bytes through the codec passes
     value = ws * pass_bytes * args.steps / (total_ms / 1e3) / 1e9
@@ -387,11 +377,8 @@ def run_gpu(args):
         e2e_step()
     b.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = torch.tensor([a.elapsed_time(b)], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = ws * pass_bytes * args.steps / (float(e2e_ms.item()) / 1e3) / 1e9
+    e2e_ms = multirank.max_over_ranks(a.elapsed_time(b), device="cuda")
+    e2e_value = ws * pass_bytes * args.steps / (e2e_ms / 1e3) / 1e9
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -418,9 +405,7 @@ def run_gpu(args):
             "error": err,
         }
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+    multirank.finalize()
     return 0
 
 

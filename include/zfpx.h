@@ -76,6 +76,19 @@ typedef struct {
 } zfpx_view3;
 
 typedef struct zfpx_plan_s *zfpx_plan;
+typedef struct zfpx_graph_s *zfpx_graph;
+typedef struct zfpx_batch_s *zfpx_batch;
+
+/* One field of a batch on a grid of ragged rows, stored [level][point]. */
+typedef struct {
+    const float *d_src;   /* values to encode (device), NULL if the batch only decodes */
+    float *d_dst;         /* decode target, same layout (device), NULL if it only encodes */
+    int64_t lev_stride;   /* elements between levels (>= points per level when nlev > 1) */
+    int32_t nlev;         /* levels, >= 1 */
+    int32_t dims;         /* 1: 4 points of a row; 3: 4 points x 4 rows x 4 levels */
+    int32_t rate;         /* 8 or 16 */
+    int32_t reserved;     /* 0 */
+} zfpx_field;
 
 ZFPX_API const char *zfpx_strerror(int code);
 
@@ -160,6 +173,66 @@ ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[
                 const int64_t stride[3], uint8_t *d_out, size_t cap, void *stream);
 ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                 const int64_t stride[3], float *d_out, void *stream);
+
+/* ---- batched ragged-row fields in one persistent launch -------------------
+ * Many fields with different level counts, block dimensionality and rate
+ * (ZFP fixed rate, Sec. II-C) on one grid of ragged rows: rows back to back,
+ * row r holding row_len[r] points -- the octahedral reduced Gaussian grid of
+ * IFS-class models has 20 + 4i points per row, mirrored.
+ *   dims 1: blocks of 4 consecutive points of one row of one level;
+ *   dims 3: 4 points x 4 consecutive rows (a row-quad) x 4 consecutive
+ *     levels over x < the longest row of the quad, shorter rows repeating
+ *     their last point, a missing last row / level repeating the last one.
+ * Stream of a field: items (dims 3: level quads, dims 1: levels) in level
+ * order, inside an item the blocks in row (row-quad) order then along x;
+ * every field at a 256-byte aligned offset (zfpx_batch_field_offset).
+ * zfpx_batch_create copies row_len and the descriptors (host arrays) and
+ * uploads the work list to the current device (it allocates; the encode and
+ * decode calls do not).  Each of zfpx_batch_encode / zfpx_batch_decode is
+ * one kernel launch over every field.  The device pointers in the field
+ * descriptors must stay valid while the batch is used.
+ * Errors: ZFPX_EINVAL, ZFPX_ESIZE, ZFPX_ECUDA, ZFPX_ENOMEM. */
+ZFPX_API int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const zfpx_field *fields,
+                               int nfields);
+ZFPX_API void zfpx_batch_destroy(zfpx_batch batch);
+/* Total stream bytes of the batch; offset and bytes of field f's stream. */
+ZFPX_API size_t zfpx_batch_bytes(zfpx_batch batch);
+ZFPX_API int64_t zfpx_batch_field_offset(zfpx_batch batch, int f);
+ZFPX_API size_t zfpx_batch_field_bytes(zfpx_batch batch, int f);
+/* Launch shape used by later calls: warps per CTA (4 or 8) and CTAs per SM
+ * (0 = as many as fit).  Picked by the autotuner; results never depend on it. */
+ZFPX_API int zfpx_batch_set_launch(zfpx_batch batch, int warps_per_cta, int ctas_per_sm);
+ZFPX_API int zfpx_batch_encode(zfpx_batch batch, uint8_t *d_out, size_t cap, void *stream);
+ZFPX_API int zfpx_batch_decode(zfpx_batch batch, const uint8_t *d_in, size_t len, void *stream);
+
+/* ---- capturing any sequence of calls into a CUDA graph ---------------------
+ * zfpx_capture_begin starts stream capture on `stream` (which must not be the
+ * legacy default stream); every zfpx call enqueued on it until
+ * zfpx_capture_end is recorded, not run; zfpx_capture_end instantiates the
+ * graph.  Plans and batches used must have their device tables uploaded
+ * before the capture starts (zfpx_plan_prepare; batches upload at creation). */
+ZFPX_API int zfpx_capture_begin(void *stream);
+ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
+
+/* ---- the transposition pair as one CUDA graph (Sec. II-B; Sec. VI) -------
+ * Records, on a private stream, pack+compress -> all-to-all -> decompress+
+ * unpack with `first` (src field -> d_mid) and then with `second` (d_mid ->
+ * d_dst): six kernels, or four with fold_permute != 0 (compress writes the
+ * receive layout directly).  The plans must share extents; `first`'s dst
+ * view and `second`'s src view both describe d_mid.  d_send / d_recv are
+ * caller-owned scratch of buf_bytes each, at least the larger
+ * zfpx_buffer_bytes of the two plans.  All pointers must stay valid for the
+ * graph's lifetime.  Creation uploads the plans' device tables first, so it
+ * allocates; launching does not.  Errors: ZFPX_EINVAL, ZFPX_ESIZE,
+ * ZFPX_ECUDA, ZFPX_ENOMEM. */
+ZFPX_API int zfpx_pair_graph_create(zfpx_graph *out, zfpx_plan first, zfpx_plan second, int rate,
+                                    const float *d_src, float *d_mid, float *d_dst, uint8_t *d_send,
+                                    uint8_t *d_recv, size_t buf_bytes, int fold_permute);
+/* Enqueues one replay of the graph on `stream`. */
+ZFPX_API int zfpx_graph_launch(zfpx_graph graph, void *stream);
+/* Kernels recorded in the graph. */
+ZFPX_API int zfpx_graph_num_kernels(zfpx_graph graph);
+ZFPX_API void zfpx_graph_destroy(zfpx_graph graph);
 
 #ifdef __cplusplus
 }

@@ -72,31 +72,6 @@ struct SmemPlanes {
     __device__ __forceinline__ int word_index(int i) const { return (i >> 1) * 64 + 2 * lane + (i & 1); }
 };
 
-// Reader over this lane's column; two zero rows follow the stream.
-struct SmemReader {
-    const uint64_t *sm;
-    uint64_t w0, w1;
-    int off, widx, lane;
-    __device__ __forceinline__ void init(const uint64_t *s, int l)
-    {
-        sm = s; lane = l; off = 0; widx = 0;
-        w0 = sm[0 * 32 + (l ^ 0)];
-        w1 = sm[1 * 32 + (l ^ 1)];
-    }
-    __device__ __forceinline__ uint64_t peek() const { return off ? ((w0 >> off) | (w1 << (64 - off))) : w0; }
-    __device__ __forceinline__ void skip(int k)    // 0 <= k <= 64
-    {
-        off += k;
-        if (off >= 64) {
-            off -= 64;
-            widx++;
-            w0 = w1;
-            const int r = widx + 1;
-            w1 = sm[r * 32 + (lane ^ r)];
-        }
-    }
-};
-
 // ----------------------------------------------------------------- message walk
 __device__ __forceinline__ int find_msg(const MsgDev *msgs, int nmsg, int64_t u)
 {
@@ -190,17 +165,27 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
     }
 }
 
+// Stream tile of one warp: 32-bit words in a [word][lane] layout (word i of
+// lane l at i * 32 + l), so every lane reads its own column without bank
+// conflicts; three zero rows follow the stream for the 64-bit read window.
+struct StreamTile {
+    const uint32_t *sm;
+    int lane;
+    __device__ __forceinline__ uint32_t get(int i) const { return sm[i * 32 + lane]; }
+};
+
 template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
-    __shared__ uint64_t smem[kWarps][(RATE + 2) * 32];
+    __shared__ uint32_t stile[kWarps][(2 * RATE + 3) * 32];
     __shared__ uint64_t splanes[kWarps][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t *wsm = smem[wid];
+    uint32_t *t32 = stile[wid];
     SmemPlanes pl{splanes[wid], lane};
-    wsm[RATE * 32 + lane] = 0ull;
-    wsm[(RATE + 1) * 32 + lane] = 0ull;
+    const StreamTile tile{t32, lane};
+#pragma unroll
+    for (int r = 0; r < 3; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
     int64_t c = gw * g.nunits / W;
@@ -216,39 +201,39 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
         const int64_t b0 = (c - unit0) * 32;
         const int nact = (int)min((int64_t)32, nblocks - b0);
-        const uint64_t *srcw = reinterpret_cast<const uint64_t *>(in + boff) + b0 * RATE;
-        __syncwarp();
-        for (int idx = lane; idx < nact * RATE; idx += 32) {
-            const int l = idx / RATE, w = idx % RATE;
-            wsm[w * 32 + (l ^ w)] = __ldg(srcw + idx);
+        if (lane >= nact) continue;
+        const int b = (int)b0 + lane;
+        // this lane's block: RATE / 2 16-byte loads into its own tile column
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(in + boff) + (int64_t)b * (RATE / 2);
+#pragma unroll
+        for (int i = 0; i < RATE / 2; i++) {
+            const uint4 v = __ldg(src4 + i);
+            t32[(4 * i) * 32 + lane] = v.x;
+            t32[(4 * i + 1) * 32 + lane] = v.y;
+            t32[(4 * i + 2) * 32 + lane] = v.z;
+            t32[(4 * i + 3) * 32 + lane] = v.w;
         }
-        __syncwarp();
-        if (lane < nact) {
-            const int b = (int)b0 + lane;
-            const int bxi = b % bxn, t = b / bxn;
-            const int byi = t % byn, bzi = t / byn;
-            const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
-            float v[64];
-            SmemReader rd;
-            rd.init(wsm, lane);
-            decode_block3<RATE>(rd, v, pl);
-            float *base = dstf + dst_off;
-            const bool full = vec && (x0 + 4 <= nx);
+        const int bxi = b % bxn, t = b / bxn;
+        const int byi = t % byn, bzi = t / byn;
+        const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
+        float v[64];
+        decode_block3_tile<RATE>(tile, v, pl);
+        float *base = dstf + dst_off;
+        const bool full = vec && (x0 + 4 <= nx);
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (z0 + k >= nz) continue;
+        for (int k = 0; k < 4; k++) {
+            if (z0 + k >= nz) continue;
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    if (y0 + j >= ny) continue;
-                    float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1];
-                    if (full) {
-                        *reinterpret_cast<float4 *>(row + x0) =
-                            make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
-                    } else {
+            for (int j = 0; j < 4; j++) {
+                if (y0 + j >= ny) continue;
+                float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1];
+                if (full) {
+                    *reinterpret_cast<float4 *>(row + x0) =
+                        make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+                } else {
 #pragma unroll
-                        for (int i = 0; i < 4; i++)
-                            if (x0 + i < nx) row[(int64_t)(x0 + i) * g.ds[0]] = v[16 * k + 4 * j + i];
-                    }
+                    for (int i = 0; i < 4; i++)
+                        if (x0 + i < nx) row[(int64_t)(x0 + i) * g.ds[0]] = v[16 * k + 4 * j + i];
                 }
             }
         }

@@ -11,6 +11,7 @@ namespace zfpx {
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 bool valid_codec_rate(int rate) { return rate == 8 || rate == 16; }
 
@@ -235,9 +236,9 @@ int zfpx_plan_prepare(zfpx_plan p, int rate)
 {
     if (!p || !valid_rate(rate)) return ZFPX_EINVAL;
     DevTable *t = nullptr;
-    int rc = get_table(p, rate, valid_codec_rate(rate) ? UNIT_BLOCKS32 : UNIT_QUADS, &t);
-    if (rc) return rc;
-    return get_table(p, rate, UNIT_QUADS, &t);
+    int rc = get_table(p, rate, UNIT_CHUNK16, &t);                 // the permutation
+    if (!rc) rc = get_table(p, rate, valid_codec_rate(rate) ? UNIT_BLOCKS32 : UNIT_QUADS, &t);
+    return rc;
 }
 
 int zfpx_plan_num_messages(zfpx_plan p) { return p ? (int)p->msgs.size() : ZFPX_EINVAL; }

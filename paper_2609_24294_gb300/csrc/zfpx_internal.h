@@ -71,6 +71,7 @@ int num_sms();
 // Resident CTAs per SM of `fn` at `threads` threads (cached per kernel).
 int occupancy(const void *fn, int threads);
 void count_launch();
+void uncount_launches(uint64_t n);   // launches recorded into a graph, not run
 bool valid_codec_rate(int rate);
 int check_launch();   // cudaGetLastError -> ZFPX_OK / ZFPX_ECUDA
 

@@ -35,6 +35,12 @@ class View3(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64 * 3), ("stride", ctypes.c_int64 * 3)]
 
 
+class Field(ctypes.Structure):
+    _fields_ = [("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p), ("lev_stride", ctypes.c_int64),
+                ("nlev", ctypes.c_int32), ("dims", ctypes.c_int32), ("rate", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 def library_path():
     return _build.LIB
 
@@ -72,6 +78,22 @@ def lib():
         "zfpx_stream_bytes": ([ctypes.c_int, ctypes.c_int, i64p], sz),
         "zfpx_encode": ([ctypes.c_int, ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_decode": ([ctypes.c_int, ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
+        "zfpx_pair_graph_create": ([ctypes.POINTER(vp), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, sz, ctypes.c_int],
+                                   ctypes.c_int),
+        "zfpx_graph_launch": ([vp, vp], ctypes.c_int),
+        "zfpx_capture_begin": ([vp], ctypes.c_int),
+        "zfpx_capture_end": ([ctypes.POINTER(vp), vp], ctypes.c_int),
+        "zfpx_batch_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, ctypes.POINTER(Field), ctypes.c_int],
+                              ctypes.c_int),
+        "zfpx_batch_destroy": ([vp], None),
+        "zfpx_batch_bytes": ([vp], sz),
+        "zfpx_batch_field_offset": ([vp, ctypes.c_int], i64),
+        "zfpx_batch_field_bytes": ([vp, ctypes.c_int], sz),
+        "zfpx_batch_set_launch": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_batch_encode": ([vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_batch_decode": ([vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_graph_num_kernels": ([vp], ctypes.c_int),
+        "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -264,3 +286,138 @@ def zfpx_decode(dims, rate, inp, dst, stream=None):
     n, s = field_view(dst)
     _check(lib().zfpx_decode(dims, rate, _dev(inp, "in"), _nbytes(inp), _i64x3(n), _i64x3(s), _dev(dst, "dst"),
                              _stream(stream)), "zfpx_decode")
+
+
+class PairGraph:
+    """The transposition pair as one CUDA graph (zfpx_pair_graph_create):
+    first plan src -> mid, second plan mid -> dst, with caller-owned send /
+    receive scratch buffers.  The tensors must outlive the graph."""
+
+    def __init__(self, first, second, rate, src, mid, dst, send, recv, fold_permute=False):
+        first._check_field(src, first.src_strides, "src")
+        first._check_field(mid, first.dst_strides, "mid")
+        second._check_field(mid, second.src_strides, "mid")
+        second._check_field(dst, second.dst_strides, "dst")
+        h = ctypes.c_void_p()
+        _check(lib().zfpx_pair_graph_create(ctypes.byref(h), first.handle, second.handle, rate, _dev(src, "src"),
+                                            _dev(mid, "mid"), _dev(dst, "dst"), _dev(send, "send"),
+                                            _dev(recv, "recv"), min(_nbytes(send), _nbytes(recv)),
+                                            1 if fold_permute else 0), "zfpx_pair_graph_create")
+        self._h = h
+        self._keep = (first, second, src, mid, dst, send, recv)
+
+    def launch(self, stream=None):
+        _check(lib().zfpx_graph_launch(self._h, _stream(stream)), "zfpx_graph_launch")
+
+    def num_kernels(self):
+        return int(lib().zfpx_graph_num_kernels(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.zfpx_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A CUDA graph recorded from zfpx calls (zfpx_capture_begin / _end)."""
+
+    def __init__(self, handle):
+        self._h = handle
+
+    def launch(self, stream=None):
+        _check(lib().zfpx_graph_launch(self._h, _stream(stream)), "zfpx_graph_launch")
+
+    def num_kernels(self):
+        return int(lib().zfpx_graph_num_kernels(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.zfpx_graph_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def capture(fn, stream):
+    """Records every zfpx call fn() makes on `stream` (a torch.cuda.Stream,
+    not the default stream) into a Graph."""
+    _check(lib().zfpx_capture_begin(ctypes.c_void_p(stream.cuda_stream)), "zfpx_capture_begin")
+    try:
+        with torch.cuda.stream(stream):
+            fn()
+    finally:
+        h = ctypes.c_void_p()
+        rc = lib().zfpx_capture_end(ctypes.byref(h), ctypes.c_void_p(stream.cuda_stream))
+    _check(rc, "zfpx_capture_end")
+    return Graph(h)
+
+
+class Batch:
+    """Batched ragged-row fields (zfpx_batch_create): fields is a list of
+    (src tensor or None, dst tensor or None, dims, rate) with tensors
+    [nlev][points] float32 on the device."""
+
+    def __init__(self, row_len, fields):
+        self.row_len = [int(v) for v in row_len]
+        arr = (ctypes.c_int64 * len(self.row_len))(*self.row_len)
+        descs = (Field * len(fields))()
+        self._keep = []
+        for i, (src, dst, dims, rate) in enumerate(fields):
+            t = src if src is not None else dst
+            if t is None or t.dim() != 2 or t.dtype != torch.float32:
+                raise ValueError("field %d: need a [nlev][points] float32 tensor" % i)
+            for u in (src, dst):
+                if u is not None and (u.shape != t.shape or u.stride() != t.stride() or not u.is_cuda):
+                    raise ValueError("field %d: src and dst must match" % i)
+            descs[i].d_src = src.data_ptr() if src is not None else None
+            descs[i].d_dst = dst.data_ptr() if dst is not None else None
+            descs[i].lev_stride = t.stride(0)
+            descs[i].nlev = t.shape[0]
+            descs[i].dims = dims
+            descs[i].rate = rate
+            descs[i].reserved = 0
+            self._keep.append((src, dst))
+        h = ctypes.c_void_p()
+        _check(lib().zfpx_batch_create(ctypes.byref(h), arr, len(self.row_len), descs, len(fields)),
+               "zfpx_batch_create")
+        self._h = h
+        self.nfields = len(fields)
+
+    def nbytes(self):
+        return int(lib().zfpx_batch_bytes(self._h))
+
+    def field_offset(self, f):
+        return int(lib().zfpx_batch_field_offset(self._h, f))
+
+    def field_bytes(self, f):
+        return int(lib().zfpx_batch_field_bytes(self._h, f))
+
+    def set_launch(self, warps_per_cta, ctas_per_sm=0):
+        _check(lib().zfpx_batch_set_launch(self._h, warps_per_cta, ctas_per_sm), "zfpx_batch_set_launch")
+
+    def encode(self, out, stream=None):
+        _check(lib().zfpx_batch_encode(self._h, _dev(out, "out"), _nbytes(out), _stream(stream)), "zfpx_batch_encode")
+
+    def decode(self, inp, stream=None):
+        _check(lib().zfpx_batch_decode(self._h, _dev(inp, "in"), _nbytes(inp), _stream(stream)), "zfpx_batch_decode")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and _lib is not None:
+            _lib.zfpx_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
