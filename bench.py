@@ -115,10 +115,14 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+CODEC_SOURCES = ("codec.cu", "zfpx_block.cuh", "zfpx_internal.h")
+
+
 def kernel_source_sha():
+    """Hash of the sources that define the plan codec kernels."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2609_24294_gb300", "csrc", "*"))):
-        h.update(open(f, "rb").read())
+    for name in CODEC_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2609_24294_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -204,6 +208,128 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------------------ other workloads (reported beside the headline)
+def _events_ms(fn, reps, warmup=2):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_batched(z, reps, peak):
+    """Ten fields on the O1280 octahedral grid (levels 137,137,137,137,1,137,
+    91,60,30,1; 1-D blocks for the single-level fields, 3-D row-quads for the
+    rest; rates 8 and 16 alternating): one persistent launch encodes them all,
+    one decodes them all; autotuned launch shape; against the float32 and
+    float16 packs of the same fields."""
+    import torch
+    from fieldgen import octahedral as og
+    from paper_2609_24294_gb300 import autotune
+    lens = og.row_lengths(1280)
+    npts = int(lens.sum())
+    fields, specs = [], []
+    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+        src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
+        fields.append((src, torch.empty_like(src), dims, rate))
+        specs.append((nlev, dims, rate))
+    batch = z.Batch(lens, fields)
+    out = torch.empty(batch.nbytes(), dtype=torch.uint8, device="cuda")
+    choice, timings = autotune.tune_batch(batch, specs, out, use_cache=False)
+    f32_bytes = sum(4 * f[0].numel() for f in fields)
+    enc_ms = _events_ms(lambda: batch.encode(out), reps)
+    dec_ms = _events_ms(lambda: batch.decode(out), reps)
+    moved = f32_bytes + batch.nbytes()
+    err = {}
+    for i, (src, dst, dims, rate) in enumerate(fields):
+        d = (dst.double() - src.double())
+        err["field%d_r%d_d%d" % (i, rate, dims)] = float(d.norm() / src.double().norm())
+    # comparators: every field as one message of a 1 x 1 plan
+    comp = {}
+    plans = [z.Plan((npts, 1, f[0].shape[0]), 1, 1, 0, 3) for f in fields]
+    for label, rate in (("float32", z.RATE_F32), ("float16_rn", z.RATE_F16)):
+        bufs = [torch.empty(p.buffer_bytes(rate), dtype=torch.uint8, device="cuda") for p in plans]
+        views = [f[0].view(f[0].shape[0], 1, npts) for f in fields]
+
+        def pk():
+            for p, v, bb in zip(plans, views, bufs):
+                if rate == z.RATE_F32:
+                    z.zfpx_pack(p, v, bb)
+                else:
+                    z.zfpx_cast_fp16_pack(p, z.ROUND_NEAREST, v, bb)
+        ms = _events_ms(pk, reps)
+        comp[label] = {"pack_f32_GBps": f32_bytes / (ms / 1e3) / 1e9, "ms": ms}
+        del bufs
+    res = {"workload": "O1280 octahedral, 10 fields, 868 levels, 5.73e9 values (22.9 GB), rates 8/16, dims 1/3",
+           "launch": {"warps_per_cta": choice[0], "ctas_per_sm": choice[1], "tuned_ms": timings},
+           "encode_ms": enc_ms, "decode_ms": dec_ms,
+           "encode_f32_GBps": f32_bytes / (enc_ms / 1e3) / 1e9, "decode_f32_GBps": f32_bytes / (dec_ms / 1e3) / 1e9,
+           "encode_frac_of_measured_hbm": moved / (enc_ms / 1e3) / 1e9 / peak,
+           "decode_frac_of_measured_hbm": moved / (dec_ms / 1e3) / 1e9 / peak,
+           "stream_bytes": batch.nbytes(), "comparators": comp, "rel_l2_error": err}
+    batch.close()
+    return res
+
+
+def extra_pair(z, reps, peak):
+    """2560 x 1280 x 137 float32 (T1279 power-law field), z->lambda then
+    lambda->theta over 8 x 8 ranks at rate 8, with the all-to-all, as one
+    CUDA graph; against the same pair with float32 and float16 messages."""
+    import torch
+    from fieldgen.sht_torch import sht_field_torch
+    x = sht_field_torch(2560, 1280, 137, 1279, seed=2, device="cuda")
+    mid = torch.empty_like(x)
+    dst = torch.empty_like(x)
+    p1 = z.Plan.for_fields(x, 8, 8, 0, 3, dst=mid)
+    p2 = z.Plan.for_fields(mid, 8, 8, 1, 3, dst=dst)
+    fbytes = 4 * x.numel()
+    res = {"workload": "2560x1280x137 f32 (1.8 GB) T1279, z->lambda then lambda->theta, 8x8 ranks, CUDA graph"}
+    for rate in (8, 16):
+        nb = max(p1.buffer_bytes(rate), p2.buffer_bytes(rate))
+        send = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        recv = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        g = z.PairGraph(p1, p2, rate, x, mid, dst, send, recv)
+        ms = _events_ms(lambda: g.launch(), reps)
+        rel = float((dst.double() - x.double()).norm() / x.double().norm())
+        res["r%d" % rate] = {"ms_per_pair": ms, "kernels": g.num_kernels(),
+                             "f32_GBps_through_codec": 4 * fbytes / (ms / 1e3) / 1e9, "rel_l2_error_after_pair": rel}
+        g.close()
+        del send, recv
+    s = torch.cuda.Stream()
+    for label, rate in (("float32", z.RATE_F32), ("float16_rn", z.RATE_F16)):
+        nb = max(p1.buffer_bytes(rate), p2.buffer_bytes(rate))
+        send = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        recv = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        for p in (p1, p2):
+            p.prepare(rate)
+
+        def run():
+            for p, a, b in ((p1, x, mid), (p2, mid, dst)):
+                if rate == z.RATE_F32:
+                    z.zfpx_pack(p, a, send, stream=s)
+                    z.zfpx_permute(p, rate, send, recv, stream=s)
+                    z.zfpx_unpack(p, recv, b, stream=s)
+                else:
+                    z.zfpx_cast_fp16_pack(p, z.ROUND_NEAREST, a, send, stream=s)
+                    z.zfpx_permute(p, rate, send, recv, stream=s)
+                    z.zfpx_fp16_unpack(p, recv, b, stream=s)
+        graph = z.capture(run, s)
+        with torch.cuda.stream(s):
+            ms = _events_ms(lambda: graph.launch(s), reps)
+        res[label] = {"ms_per_pair": ms, "f32_GBps": 4 * fbytes / (ms / 1e3) / 1e9}
+        graph.close()
+        del send, recv
+    del x, mid, dst
+    return res
 
 
 # ------------------------------------------------------------------ GPU arm
@@ -380,6 +506,15 @@ def run_gpu(args):
     e2e_ms = multirank.max_over_ranks(a.elapsed_time(b), device="cuda")
     e2e_value = ws * pass_bytes * args.steps / (e2e_ms / 1e3) / 1e9
 
+    extras = {}
+    if not args.no_extras:
+        for name, fn in (("batched_ragged", extra_batched), ("transposition_pair", extra_pair)):
+            try:
+                extras[name] = fn(z, max(3, args.steps // 2), peak)
+            except Exception as e:          # reported, never silently dropped
+                extras[name] = {"error": repr(e)}
+            torch.cuda.empty_cache()
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         b_, s_, threads, done = oracle_sample(x, args.cpu_seconds)
@@ -403,6 +538,7 @@ def run_gpu(args):
             "kernels": kern,
             "comparators": comp,
             "error": err,
+            "extras": extras,
         }
         print(json.dumps(line), flush=True)
     multirank.finalize()
@@ -418,6 +554,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
