@@ -214,6 +214,25 @@ ZFPX_API int zfpx_batch_decode(zfpx_batch batch, const uint8_t *d_in, size_t len
 ZFPX_API int zfpx_capture_begin(void *stream);
 ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
 
+/* ---- a transposition that allocates nothing --------------------------------
+ * No counterpart in the paper: this serves callers that cannot allocate
+ * device memory where they call -- inside another framework's memory pool or
+ * allocator, in loops that must not pay for an allocation, with a fixed
+ * device memory map.  It does what zfpx_pack_compress (ZFPX_LAYOUT_RECV)
+ * followed by zfpx_decompress_unpack do, d_src -> d_dst through the plan at
+ * `rate` (8 or 16), with the same result, but it keeps the plan's message
+ * table and the compressed messages in one library-owned device array of
+ * ZFPX_NOALLOC_SCRATCH_BYTES (64 MiB), reserved on every GPU that loads the
+ * library until the process exits, and calls no allocation routine; the plan
+ * needs no zfpx_plan_prepare.  The first call on each device looks the array
+ * up with that device current.  Every call shares the array, so calls that
+ * overlap on the GPU (other streams, other host threads) race; calls in order
+ * on one stream do not.  The message table is copied from host memory, so the
+ * call returns after the copy has read it.  Errors: ZFPX_EINVAL, ZFPX_ESIZE
+ * (table plus compressed messages larger than the array), ZFPX_ECUDA. */
+#define ZFPX_NOALLOC_SCRATCH_BYTES (64u << 20)
+ZFPX_API int zfpx_transpose_noalloc(zfpx_plan plan, int rate, const float *d_src, float *d_dst, void *stream);
+
 /* ---- the transposition pair as one CUDA graph (Sec. II-B; Sec. VI) -------
  * Records, on a private stream, pack+compress -> all-to-all -> decompress+
  * unpack with `first` (src field -> d_mid) and then with `second` (d_mid ->

@@ -484,3 +484,106 @@ int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// A transposition that allocates nothing.
+//
+// For callers that cannot allocate device memory at the point of the call --
+// code running inside another framework's memory pool or allocator, real-time
+// loops that must not pay for an allocation, programs with a fixed device
+// memory map -- zfpx_transpose_noalloc keeps everything it needs beyond the
+// caller's source and destination fields in one file-scope device array: the
+// message table of the plan and the compressed messages (written straight
+// into the receive layout, then decoded).  The array is ZFPX_NOALLOC_SCRATCH_BYTES
+// long and stays reserved on every GPU that loads the library until the
+// process exits.  Every call shares it and leaves its contents behind; nothing
+// here depends on what an earlier call left (each call rewrites the table and
+// every stream byte it later reads), but calls that overlap on the GPU -- on
+// different streams, or from different host threads -- race on it.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[ZFPX_NOALLOC_SCRATCH_BYTES];
+
+namespace zfpx {
+namespace {
+// device address of the scratch array, looked up once per device with that
+// device current (a host-side name of the array is not a device address)
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {nullptr};
+
+int noalloc_scratch(void **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return ZFPX_ECUDA;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return ZFPX_ECUDA;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return ZFPX_OK;
+}
+}  // namespace
+}  // namespace zfpx
+
+extern "C" int zfpx_transpose_noalloc(zfpx_plan p, int rate, const float *d_src, float *d_dst, void *stream)
+{
+    if (!p || !d_src || !d_dst || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    // message table (32-block work units, receive-layout offsets), built on the host
+    const size_t M = p->msgs.size();
+    std::vector<MsgDev> h(M);
+    int64_t units = 0, so = 0, ro = 0;
+    std::vector<int64_t> recv_off(M, 0);
+    {
+        std::vector<size_t> order(M);
+        for (size_t i = 0; i < M; i++) order[i] = i;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+            const HostMsg &x = p->msgs[a], &y = p->msgs[b];
+            return x.dst != y.dst ? x.dst < y.dst : x.src_peer < y.src_peer;
+        });
+        for (size_t i : order) {
+            recv_off[i] = ro;
+            ro = (ro + message_bytes(p, p->msgs[i], rate) + 255) / 256 * 256;
+        }
+    }
+    for (size_t i = 0; i < M; i++) {
+        const HostMsg &m = p->msgs[i];
+        MsgDev &d = h[i];
+        const int64_t bx = (m.nx + 3) / 4;
+        const int64_t by = p->dims == 3 ? (m.ny + 3) / 4 : m.ny;
+        const int64_t bz = p->dims == 3 ? (m.nz + 3) / 4 : m.nz;
+        d.src_off = m.x0 * p->ss[0] + m.y0 * p->ss[1] + m.z0 * p->ss[2];
+        d.dst_off = m.x0 * p->ds[0] + m.y0 * p->ds[1] + m.z0 * p->ds[2];
+        d.off[0] = so;
+        d.off[1] = recv_off[i];
+        so = (so + message_bytes(p, m, rate) + 255) / 256 * 256;
+        d.nx = (int32_t)m.nx; d.ny = (int32_t)m.ny; d.nz = (int32_t)m.nz;
+        d.bx = (int32_t)bx; d.by = (int32_t)by; d.bz = (int32_t)bz;
+        d.nblocks = bx * by * bz;
+        d.unit0 = units;
+        units += (d.nblocks + 31) / 32;
+    }
+    const size_t table_bytes = (M * sizeof(MsgDev) + 255) / 256 * 256;
+    const size_t stream_bytes = (size_t)ro;
+    if (table_bytes + stream_bytes > ZFPX_NOALLOC_SCRATCH_BYTES) return ZFPX_ESIZE;
+    void *scratch = nullptr;
+    int rc = noalloc_scratch(&scratch);
+    if (rc) return rc;
+    if (units == 0) return ZFPX_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    // pageable source: the copy has read h before this call returns
+    if (cudaMemcpyAsync(scratch, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return ZFPX_ECUDA;
+    uint8_t *buf = static_cast<uint8_t *>(scratch) + table_bytes;
+    LaunchGeom g{};
+    g.msgs = static_cast<const MsgDev *>(scratch);
+    g.nmsg = (int)M;
+    g.nunits = units;
+    for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
+    rc = launch_encode(p->dims, rate, d_src, buf, g, ZFPX_LAYOUT_RECV, vec_ok(d_src, p->ss, p, 0) ? 1 : 0, st);
+    if (rc) return rc;
+    return launch_decode(p->dims, rate, buf, d_dst, g, ZFPX_LAYOUT_RECV, vec_ok(d_dst, p->ds, p, 1) ? 1 : 0, st);
+}

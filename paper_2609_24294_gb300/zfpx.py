@@ -81,6 +81,7 @@ def lib():
         "zfpx_pair_graph_create": ([ctypes.POINTER(vp), vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, sz, ctypes.c_int],
                                    ctypes.c_int),
         "zfpx_graph_launch": ([vp, vp], ctypes.c_int),
+        "zfpx_transpose_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "zfpx_capture_begin": ([vp], ctypes.c_int),
         "zfpx_capture_end": ([ctypes.POINTER(vp), vp], ctypes.c_int),
         "zfpx_batch_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, ctypes.POINTER(Field), ctypes.c_int],
@@ -421,3 +422,15 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def zfpx_transpose_noalloc(plan, rate, src, dst, stream=None):
+    """Compress (receive layout) then decompress through the library's fixed
+    device array; allocates nothing (see include/zfpx.h)."""
+    plan._check_field(src, plan.src_strides, "src")
+    plan._check_field(dst, plan.dst_strides, "dst")
+    _check(lib().zfpx_transpose_noalloc(plan.handle, rate, _dev(src, "src"), _dev(dst, "dst"), _stream(stream)),
+           "zfpx_transpose_noalloc")
