@@ -226,22 +226,26 @@ def _events_ms(fn, reps, warmup=2):
     return a.elapsed_time(b) / reps
 
 
-def extra_batched(z, reps, peak):
+def _octahedral_fields():
+    import torch
+    from fieldgen import octahedral as og
+    fields = []
+    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+        src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
+        fields.append((src, torch.empty_like(src), dims, rate))
+    return og.row_lengths(1280), fields
+
+
+def extra_batched(z, reps, peak, lens, fields):
     """Ten fields on the O1280 octahedral grid (levels 137,137,137,137,1,137,
     91,60,30,1; 1-D blocks for the single-level fields, 3-D row-quads for the
     rest; rates 8 and 16 alternating): one persistent launch encodes them all,
     one decodes them all; autotuned launch shape; against the float32 and
     float16 packs of the same fields."""
     import torch
-    from fieldgen import octahedral as og
     from paper_2609_24294_gb300 import autotune
-    lens = og.row_lengths(1280)
     npts = int(lens.sum())
-    fields, specs = [], []
-    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
-        src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
-        fields.append((src, torch.empty_like(src), dims, rate))
-        specs.append((nlev, dims, rate))
+    specs = [(f[0].shape[0], f[2], f[3]) for f in fields]
     batch = z.Batch(lens, fields)
     out = torch.empty(batch.nbytes(), dtype=torch.uint8, device="cuda")
     choice, timings = autotune.tune_batch(batch, specs, out, use_cache=False)
@@ -253,7 +257,6 @@ def extra_batched(z, reps, peak):
     for i, (src, dst, dims, rate) in enumerate(fields):
         d = (dst.double() - src.double())
         err["field%d_r%d_d%d" % (i, rate, dims)] = float(d.norm() / src.double().norm())
-    # comparators: every field as one message of a 1 x 1 plan
     comp = {}
     plans = [z.Plan((npts, 1, f[0].shape[0]), 1, 1, 0, 3) for f in fields]
     for label, rate in (("float32", z.RATE_F32), ("float16_rn", z.RATE_F16)):
@@ -277,6 +280,66 @@ def extra_batched(z, reps, peak):
            "decode_frac_of_measured_hbm": moved / (dec_ms / 1e3) / 1e9 / peak,
            "stream_bytes": batch.nbytes(), "comparators": comp, "rel_l2_error": err}
     batch.close()
+    return res
+
+
+def extra_serving(z, peak, lens, fields, n=2000, rate_hz=50e3, arena=40 << 30):
+    """Request loop: n messages (row x level slabs of the resident O1280
+    fields, sizes lognormal around 1 MiB clipped to 16 KiB..64 MiB), Poisson
+    arrivals at rate_hz, rates 8 / 16, admitted into a 40 GB arena, batched
+    continuously over 4 streams; p50 / p99 latency from arrival to completion
+    seen by the host, sustained GB/s; beside float32 / float16 pack+unpack of
+    the same slabs."""
+    import torch
+    from fieldgen import octahedral as og
+    from paper_2609_24294_gb300 import serve
+    reqs = og.serving_requests(n, [f[0].shape[0] for f in fields], [f[2] for f in fields], 5, lens)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    calls = []
+    for r in reqs:
+        f = fields[r["field"]][0]
+        ptr = f.data_ptr() + 4 * (r["z0"] * f.stride(0) + int(offs[r["row0"]]))
+        calls.append(dict(src=ptr, lev_stride=f.stride(0), nlev=r["nz"], dims=r["dims"], rate=r["rate"],
+                          row0=r["row0"], row1=r["row1"]))
+    srv = serve.Server(lens, arena_bytes=arena, nstreams=4, max_batch=64)
+    serve.run_requests(srv, calls[:50])                                   # warm-up
+    arrivals = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate_hz, n))
+    lat, wall, busy_max, _ = serve.run_requests(srv, calls, arrivals=arrivals)
+    st = srv.stats()
+    total = float(sum(r["bytes"] for r in reqs))
+    res = {"workload": "%d O1280 slabs, lognormal sizes (median %.2f MB, max %.1f MB), Poisson %.0f/s, rates 8/16, "
+                       "40 GB arena, 4 streams" % (n, np.median([r["bytes"] for r in reqs]) / 1e6,
+                                                  max(r["bytes"] for r in reqs) / 1e6, rate_hz),
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "mean_ms": float(lat.mean() * 1e3), "wall_ms": wall * 1e3, "f32_GBps_sustained": total / wall / 1e9,
+           "offered_GBps": total * rate_hz / n / 1e9, "batches": st["batches"], "max_streams_busy": busy_max}
+    srv.close()
+    # comparators: the same slabs through float32 / float16 pack + unpack, back to back
+    plans, views, outs = [], [], []
+    for r in reqs:
+        f = fields[r["field"]][0]
+        span = int(offs[r["row1"]] - offs[r["row0"]])
+        v = f[r["z0"]:r["z0"] + r["nz"], int(offs[r["row0"]]):int(offs[r["row0"]]) + span].unsqueeze(1)
+        p = z.Plan.for_fields(v, 1, 1, 0, 3, dst=torch.empty((r["nz"], 1, span), device="cuda"))
+        plans.append(p)
+        views.append(v)
+    for label, rate in (("float32", z.RATE_F32), ("float16_rn", z.RATE_F16)):
+        bufs = [torch.empty(p.buffer_bytes(rate), dtype=torch.uint8, device="cuda") for p in plans]
+        dsts = [torch.empty((v.shape[0], 1, v.shape[2]), device="cuda") for v in views]
+        for p in plans:
+            p.prepare(rate)
+
+        def run():
+            for p, v, bb, d in zip(plans, views, bufs, dsts):
+                if rate == z.RATE_F32:
+                    z.zfpx_pack(p, v, bb)
+                    z.zfpx_unpack(p, bb, d)
+                else:
+                    z.zfpx_cast_fp16_pack(p, z.ROUND_NEAREST, v, bb)
+                    z.zfpx_fp16_unpack(p, bb, d)
+        ms = _events_ms(run, 2, warmup=1)
+        res["comparator_" + label] = {"f32_GBps": total / (ms / 1e3) / 1e9, "ms_all": ms}
+        del bufs, dsts
     return res
 
 
@@ -508,12 +571,26 @@ def run_gpu(args):
 
     extras = {}
     if not args.no_extras:
-        for name, fn in (("batched_ragged", extra_batched), ("transposition_pair", extra_pair)):
+        reps = max(3, args.steps // 2)
+        try:
+            extras["transposition_pair"] = extra_pair(z, reps, peak)
+        except Exception as e:              # reported, never silently dropped
+            extras["transposition_pair"] = {"error": repr(e)}
+        torch.cuda.empty_cache()
+        try:
+            lens, ofields = _octahedral_fields()
             try:
-                extras[name] = fn(z, max(3, args.steps // 2), peak)
-            except Exception as e:          # reported, never silently dropped
-                extras[name] = {"error": repr(e)}
-            torch.cuda.empty_cache()
+                extras["batched_ragged"] = extra_batched(z, reps, peak, lens, ofields)
+            except Exception as e:
+                extras["batched_ragged"] = {"error": repr(e)}
+            try:
+                extras["serving"] = extra_serving(z, peak, lens, ofields)
+            except Exception as e:
+                extras["serving"] = {"error": repr(e)}
+            del ofields
+        except Exception as e:
+            extras["octahedral_fields"] = {"error": repr(e)}
+        torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

@@ -85,3 +85,33 @@ CONFIG3_FIELDS = [
     (1, "temperature", 1, 8), (137, "humidity", 3, 16), (91, "power", 3, 8), (60, "humidity", 3, 16),
     (30, "temperature", 3, 8), (1, "humidity", 1, 16),
 ]
+
+
+def serving_requests(n, fields_nlev, fields_dims, seed, lens, min_bytes=16 << 10, max_bytes=64 << 20,
+                     median_bytes=1 << 20, sigma=1.34):
+    """Request mix for the serving workload: sizes lognormal (median 1 MiB,
+    sigma 1.34, clipped to [16 KiB, 64 MiB]), each a slab of rows x levels of
+    a random field: 3-D fields take whole row-quads and up to 16 levels, 1-D
+    (single-level) fields take rows; rate 8 or 16 uniformly.  Returns dicts
+    (field, z0, nz, row0, row1, rate, dims, bytes)."""
+    rng = np.random.default_rng(seed)
+    sizes = np.clip(np.exp(np.log(median_bytes) + sigma * rng.standard_normal(n)), min_bytes, max_bytes)
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    nrows = len(lens)
+    out = []
+    for s in sizes:
+        f = int(rng.integers(len(fields_nlev)))
+        nlev, dims = fields_nlev[f], fields_dims[f]
+        nz = 1 if dims == 1 else int(rng.integers(1, min(16, nlev) + 1))
+        z0 = int(rng.integers(0, nlev - nz + 1))
+        target_pts = max(1, int(s) // (4 * nz))
+        step = 4 if dims == 3 else 1
+        r0 = int(rng.integers(0, nrows // step)) * step
+        r1 = r0
+        while r1 < nrows and offs[r1] - offs[r0] < target_pts:
+            r1 = min(nrows, r1 + step)
+        while r0 > 0 and offs[r1] - offs[r0] < target_pts:      # ran into the last row: grow downwards
+            r0 -= step
+        out.append(dict(field=f, z0=z0, nz=nz, row0=r0, row1=r1, rate=int(rng.choice([8, 16])), dims=dims,
+                        bytes=int(4 * nz * (offs[r1] - offs[r0]))))
+    return out

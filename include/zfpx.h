@@ -78,16 +78,21 @@ typedef struct {
 typedef struct zfpx_plan_s *zfpx_plan;
 typedef struct zfpx_graph_s *zfpx_graph;
 typedef struct zfpx_batch_s *zfpx_batch;
+typedef struct zfpx_server_s *zfpx_server;
 
-/* One field of a batch on a grid of ragged rows, stored [level][point]. */
+/* One field of a batch on a grid of ragged rows, stored [level][point]: the
+ * rows [row0, row1) of the grid (row0 = row1 = 0: all rows) on nlev levels.
+ * d_src and d_dst point at level 0, first point of row row0. */
 typedef struct {
-    const float *d_src;   /* values to encode (device), NULL if the batch only decodes */
-    float *d_dst;         /* decode target, same layout (device), NULL if it only encodes */
-    int64_t lev_stride;   /* elements between levels (>= points per level when nlev > 1) */
-    int32_t nlev;         /* levels, >= 1 */
-    int32_t dims;         /* 1: 4 points of a row; 3: 4 points x 4 rows x 4 levels */
-    int32_t rate;         /* 8 or 16 */
-    int32_t reserved;     /* 0 */
+    const float *d_src;       /* values to encode (device), NULL if the batch only decodes */
+    float *d_dst;             /* decode target (device), NULL if it only encodes */
+    int64_t lev_stride;       /* d_src elements between levels (>= the rows' points when nlev > 1) */
+    int64_t dst_lev_stride;   /* d_dst elements between levels; 0 = lev_stride */
+    int32_t nlev;             /* levels, >= 1 */
+    int32_t dims;             /* 1: 4 points of a row; 3: 4 points x 4 rows x 4 levels */
+    int32_t rate;             /* 8 or 16 */
+    int32_t row0, row1;       /* dims 3: row0 % 4 == 0 and (row1 % 4 == 0 or row1 == nrows) */
+    int32_t reserved;         /* 0 */
 } zfpx_field;
 
 ZFPX_API const char *zfpx_strerror(int code);
@@ -204,6 +209,41 @@ ZFPX_API size_t zfpx_batch_field_bytes(zfpx_batch batch, int f);
 ZFPX_API int zfpx_batch_set_launch(zfpx_batch batch, int warps_per_cta, int ctas_per_sm);
 ZFPX_API int zfpx_batch_encode(zfpx_batch batch, uint8_t *d_out, size_t cap, void *stream);
 ZFPX_API int zfpx_batch_decode(zfpx_batch batch, const uint8_t *d_in, size_t len, void *stream);
+
+/* ---- serving: a request loop with continuous batching ---------------------
+ * The paper's exchange as a service: messages (row x level slabs of fields
+ * resident on the device, one zfpx_field each, d_dst unused) arrive one by
+ * one and are compressed and decompressed (the sender's and the receiver's
+ * side of Sec. I) as they come.  A request is admitted when its compressed
+ * stream plus its decoded copy fit in the server's arena -- one device
+ * allocation of arena_bytes, the HBM budget, made at creation; a request that
+ * can never fit is refused by zfpx_server_submit with ZFPX_ENOMEM_BUDGET.
+ * zfpx_server_pump admits waiting requests (first come, first served, at
+ * most max_batch) into one batch -- one encode and one decode launch -- on the
+ * next of nstreams streams whose previous batch has finished, so batches
+ * overlap on the device; *launched = requests put in flight (0 if none).
+ * zfpx_server_poll returns ids of finished requests (up to max); their
+ * results (device pointers from zfpx_server_result) stay valid until
+ * zfpx_server_release returns the memory.  A request's bytes and values do
+ * not depend on which other requests share its batch.  Nothing is allocated
+ * after creation.  One host thread per server.
+ * zfpx_server_stats: [queued, streams busy, arena bytes used, arena bytes,
+ * batches launched, finished-not-polled]. */
+ZFPX_API int zfpx_server_create(zfpx_server *out, const int64_t *row_len, int nrows, size_t arena_bytes, int nstreams,
+                                int max_batch);
+ZFPX_API void zfpx_server_destroy(zfpx_server server);
+ZFPX_API int zfpx_server_set_launch(zfpx_server server, int warps_per_cta, int ctas_per_sm);
+ZFPX_API int zfpx_server_submit(zfpx_server server, const zfpx_field *request, int64_t *id);
+ZFPX_API int zfpx_server_pump(zfpx_server server, int *launched);
+ZFPX_API int zfpx_server_poll(zfpx_server server, int64_t *done, int max, int *ndone);
+ZFPX_API int zfpx_server_result(zfpx_server server, int64_t id, const uint8_t **d_stream, size_t *stream_bytes,
+                                const float **d_values, size_t *values_bytes);
+/* Synchronous copy of a finished request's stream and values to host memory
+ * (either pointer may be NULL). */
+ZFPX_API int zfpx_server_copy_result(zfpx_server server, int64_t id, uint8_t *h_stream, size_t stream_cap,
+                                     float *h_values, size_t values_cap);
+ZFPX_API int zfpx_server_release(zfpx_server server, int64_t id);
+ZFPX_API int zfpx_server_stats(zfpx_server server, int64_t out[6]);
 
 /* ---- capturing any sequence of calls into a CUDA graph ---------------------
  * zfpx_capture_begin starts stream capture on `stream` (which must not be the

@@ -18,7 +18,10 @@
 // range of chunks.  The class is uniform across a warp.
 #include <algorithm>
 #include <climits>
+#include <cstring>
+#include <deque>
 #include <map>
+#include <unordered_map>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -32,11 +35,14 @@ namespace {
 using namespace blk;
 
 struct FieldDevB {
-    const float *src;
+    const float *src;      // (level 0, first point of row row0)
     float *dst;
-    int64_t lev_stride;
-    int64_t out_off;   // byte offset of the field's stream
+    int64_t src_ls, dst_ls;  // elements between levels
+    int64_t out_off;       // byte offset of the field's stream
+    int64_t b0;            // first global block of the row range (row-quad or row prefix)
+    int64_t roff0;         // grid offset of row row0
     int32_t nlev, dims, rate, vec;
+    int32_t row0, row1;    // rows [row0, row1)
 };
 
 struct ItemDevB {
@@ -142,12 +148,12 @@ __device__ __forceinline__ void gather_quad(const FieldDevB &f, const GridDev &g
     const int x0 = 4 * bxi;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        const int r = min(4 * q + j, g.nrows - 1);
-        const int64_t roff = __ldg(g.row_off + r);
+        const int r = min(4 * q + j, f.row1 - 1);
+        const int64_t roff = __ldg(g.row_off + r) - f.roff0;
         const int len = __ldg(g.row_len + r);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const float *row = f.src + (int64_t)(z0 + min(k, nz - 1)) * f.lev_stride + roff;
+            const float *row = f.src + (int64_t)(z0 + min(k, nz - 1)) * f.src_ls + roff;
             if (f.vec && x0 + 4 <= len) {
                 const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x0));
                 x[16 * k + 4 * j] = v.x; x[16 * k + 4 * j + 1] = v.y;
@@ -167,14 +173,14 @@ __device__ __forceinline__ void scatter_quad(const FieldDevB &f, const GridDev &
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const int r = 4 * q + j;
-        if (r >= g.nrows) continue;
-        const int64_t roff = __ldg(g.row_off + r);
+        if (r >= f.row1) continue;
+        const int64_t roff = __ldg(g.row_off + r) - f.roff0;
         const int len = __ldg(g.row_len + r);
         if (x0 >= len) continue;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
             if (k >= nz) continue;
-            float *row = f.dst + (int64_t)(z0 + k) * f.lev_stride + roff;
+            float *row = f.dst + (int64_t)(z0 + k) * f.dst_ls + roff;
             if (f.vec && x0 + 4 <= len) {
                 *reinterpret_cast<float4 *>(row + x0) =
                     make_float4(x[16 * k + 4 * j], x[16 * k + 4 * j + 1], x[16 * k + 4 * j + 2], x[16 * k + 4 * j + 3]);
@@ -192,9 +198,9 @@ __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g,
                                            int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint8_t *out)
 {
     if (lane < nact) {
-        const int64_t b = b0 + lane;
-        const int q = upper_index(g.qpre, g.nq + 1, b);
-        const int bxi = (int)(b - __ldg(g.qpre + q));
+        const int64_t bg = b0 + lane + f.b0;
+        const int q = upper_index(g.qpre, g.nq + 1, bg);
+        const int bxi = (int)(bg - __ldg(g.qpre + q));
         float x[64];
         gather_quad(f, g, q, bxi, it.z0, it.nz, x);
         SmemWriterB<RATE> wr{wsm, 0ull, 0, 0, lane};
@@ -216,10 +222,11 @@ __device__ __forceinline__ void enc1_chunk(const FieldDevB &f, const GridDev &g,
 {
     if (lane >= nact) return;
     const int64_t b = b0 + lane;
-    const int r = upper_index(g.rpre, g.nrows + 1, b);
-    const int x0 = 4 * (int)(b - __ldg(g.rpre + r));
+    const int64_t bg = b + f.b0;
+    const int r = upper_index(g.rpre, g.nrows + 1, bg);
+    const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
     const int len = __ldg(g.row_len + r);
-    const float *row = f.src + (int64_t)it.z0 * f.lev_stride + __ldg(g.row_off + r);
+    const float *row = f.src + (int64_t)it.z0 * f.src_ls + (__ldg(g.row_off + r) - f.roff0);
     float x[4];
     if (f.vec && x0 + 4 <= len) {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x0));
@@ -278,8 +285,9 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
     }
 #pragma unroll
     for (int r = 0; r < 3; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
-    const int q = upper_index(g.qpre, g.nq + 1, b);
-    const int bxi = (int)(b - __ldg(g.qpre + q));
+    const int64_t bg = b + f.b0;
+    const int q = upper_index(g.qpre, g.nq + 1, bg);
+    const int bxi = (int)(bg - __ldg(g.qpre + q));
     float x[64];
     const StreamTileB tile{t32, lane};
     SmemPlanesB pl{wpl, lane};
@@ -296,10 +304,11 @@ __device__ __forceinline__ void dec1_lane(const FieldDevB &f, const GridDev &g, 
     else w = __ldg(reinterpret_cast<const uint32_t *>(in + it.out_off) + b);
     float x[4];
     decode_block1<RATE>(w, x);
-    const int r = upper_index(g.rpre, g.nrows + 1, b);
-    const int x0 = 4 * (int)(b - __ldg(g.rpre + r));
+    const int64_t bg = b + f.b0;
+    const int r = upper_index(g.rpre, g.nrows + 1, bg);
+    const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
     const int len = __ldg(g.row_len + r);
-    float *row = f.dst + (int64_t)it.z0 * f.lev_stride + __ldg(g.row_off + r);
+    float *row = f.dst + (int64_t)it.z0 * f.dst_ls + (__ldg(g.row_off + r) - f.roff0);
     if (f.vec && x0 + 4 <= len) {
         *reinterpret_cast<float4 *>(row + x0) = make_float4(x[0], x[1], x[2], x[3]);
     } else {
@@ -344,27 +353,51 @@ batch_decode_kernel(BatchGeom bg, const uint8_t *__restrict__ in)
 }  // namespace
 }  // namespace zfpx
 
-struct zfpx_batch_s {
-    int dev = -1;
+namespace zfpx {
+namespace {
+
+// Grid tables shared by every batch on one grid (host copies and device).
+struct GridHost {
     int nrows = 0, nq = 0;
-    std::vector<zfpx_field> fields;
-    std::vector<int64_t> field_off;
-    std::vector<int64_t> field_bytes;
-    int64_t total = 0;
-    int nitems = 0;
-    int64_t nunits = 0;
-    int warps = 4, ctas_per_sm = 0;     // 0 = as many as fit
-    // device allocations
+    std::vector<int64_t> roff, qpre, rpre;
+    std::vector<int32_t> rlen;
+    bool mult4 = true;
     int64_t *d_row_off = nullptr;
     int32_t *d_row_len = nullptr;
     int64_t *d_qpre = nullptr, *d_rpre = nullptr;
-    zfpx::FieldDevB *d_fields = nullptr;
-    zfpx::ItemDevB *d_items = nullptr;
+
+    int init(const int64_t *row_len, int n)
+    {
+        nrows = n;
+        nq = (n + 3) / 4;
+        roff.assign(n, 0);
+        rlen.assign(n, 0);
+        qpre.assign(nq + 1, 0);
+        rpre.assign(n + 1, 0);
+        int64_t o = 0;
+        for (int r = 0; r < n; r++) {
+            if (row_len[r] < 1 || row_len[r] > (1 << 30)) return ZFPX_EINVAL;
+            roff[r] = o;
+            o += row_len[r];
+            rlen[r] = (int32_t)row_len[r];
+            mult4 = mult4 && (row_len[r] % 4 == 0);
+        }
+        for (int q = 0; q < nq; q++) {
+            int64_t mx = 0;
+            for (int j = 0; j < 4 && 4 * q + j < n; j++) mx = std::max(mx, row_len[4 * q + j]);
+            qpre[q + 1] = qpre[q] + (mx + 3) / 4;
+        }
+        for (int r = 0; r < n; r++) rpre[r + 1] = rpre[r] + (row_len[r] + 3) / 4;
+        return ZFPX_OK;
+    }
+    GridDev dev() const { return GridDev{d_row_off, d_row_len, d_qpre, d_rpre, nrows, nq}; }
+    void free_dev()
+    {
+        cudaFree(d_row_off); cudaFree(d_row_len); cudaFree(d_qpre); cudaFree(d_rpre);
+        d_row_off = nullptr; d_row_len = nullptr; d_qpre = nullptr; d_rpre = nullptr;
+    }
 };
 
-using namespace zfpx;
-
-namespace {
 template <class T>
 int upload(T **dptr, const std::vector<T> &h)
 {
@@ -373,88 +406,80 @@ int upload(T **dptr, const std::vector<T> &h)
     if (cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return ZFPX_ECUDA;
     return ZFPX_OK;
 }
-}  // namespace
 
-extern "C" {
-
-void zfpx_batch_destroy(zfpx_batch b)
+int upload_grid(GridHost &g)
 {
-    if (!b) return;
-    cudaFree(b->d_row_off);
-    cudaFree(b->d_row_len);
-    cudaFree(b->d_qpre);
-    cudaFree(b->d_rpre);
-    cudaFree(b->d_fields);
-    cudaFree(b->d_items);
-    delete b;
+    int rc = upload(&g.d_row_off, g.roff);
+    if (!rc) rc = upload(&g.d_row_len, g.rlen);
+    if (!rc) rc = upload(&g.d_qpre, g.qpre);
+    if (!rc) rc = upload(&g.d_rpre, g.rpre);
+    return rc;
 }
 
-int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const zfpx_field *fields, int nfields)
+int check_field(const GridHost &g, const zfpx_field &F)
 {
-    if (!out) return ZFPX_EINVAL;
-    *out = nullptr;
-    if (!row_len || nrows < 1 || !fields || nfields < 1) return ZFPX_EINVAL;
-    int64_t npts = 0;
-    bool mult4 = true;
-    for (int r = 0; r < nrows; r++) {
-        if (row_len[r] < 1 || row_len[r] > (1 << 30)) return ZFPX_EINVAL;
-        npts += row_len[r];
-        mult4 = mult4 && (row_len[r] % 4 == 0);
-    }
+    if (F.nlev < 1 || (F.dims != 1 && F.dims != 3) || !valid_codec_rate(F.rate)) return ZFPX_EINVAL;
+    const int r0 = F.row0, r1 = (F.row0 == 0 && F.row1 == 0) ? g.nrows : F.row1;
+    if (r0 < 0 || r1 > g.nrows || r0 >= r1) return ZFPX_EINVAL;
+    if (F.dims == 3 && ((r0 & 3) || ((r1 & 3) && r1 != g.nrows))) return ZFPX_EINVAL;
+    const int64_t span = g.roff[r1 - 1] + g.rlen[r1 - 1] - g.roff[r0];
+    const int64_t dls = F.dst_lev_stride ? F.dst_lev_stride : F.lev_stride;
+    if (F.nlev > 1 && (F.lev_stride < span || dls < span)) return ZFPX_EINVAL;
+    return ZFPX_OK;
+}
+
+// Blocks of one item of field F (all items of a field have the same count).
+int64_t field_item_blocks(const GridHost &g, const zfpx_field &F, int r0, int r1)
+{
+    if (F.dims == 3) return g.qpre[(r1 + 3) / 4] - g.qpre[r0 / 4];
+    return g.rpre[r1] - g.rpre[r0];
+}
+
+int64_t field_stream_bytes(const GridHost &g, const zfpx_field &F, int r0, int r1)
+{
+    const int64_t per_block = F.dims == 3 ? 8 * F.rate : F.rate / 2;
+    const int64_t items = F.dims == 3 ? (F.nlev + 3) / 4 : F.nlev;
+    return items * field_item_blocks(g, F, r0, r1) * per_block;
+}
+
+// Field and item descriptors of a set of fields whose streams start at the
+// given byte offsets; items grouped by (dims, rate) class.
+void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stream_off, int nfields,
+                std::vector<FieldDevB> &fd, std::vector<ItemDevB> &items, int64_t &units)
+{
+    fd.resize(nfields);
     for (int f = 0; f < nfields; f++) {
         const zfpx_field &F = fields[f];
-        if (F.nlev < 1 || (F.dims != 1 && F.dims != 3) || !valid_codec_rate(F.rate)) return ZFPX_EINVAL;
-        if (F.lev_stride < npts && F.nlev > 1) return ZFPX_EINVAL;
+        const int r0 = F.row0, r1 = (F.row0 == 0 && F.row1 == 0) ? g.nrows : F.row1;
+        const int64_t dls = F.dst_lev_stride ? F.dst_lev_stride : F.lev_stride;
+        const bool vec = g.mult4 && (F.lev_stride % 4 == 0 || F.nlev == 1) && (dls % 4 == 0 || F.nlev == 1) &&
+                         !((uintptr_t)F.d_src & 15u) && !((uintptr_t)F.d_dst & 15u);
+        FieldDevB d;
+        d.src = F.d_src;
+        d.dst = F.d_dst;
+        d.src_ls = F.lev_stride;
+        d.dst_ls = dls;
+        d.out_off = stream_off[f];
+        d.b0 = F.dims == 3 ? g.qpre[r0 / 4] : g.rpre[r0];
+        d.roff0 = g.roff[r0];
+        d.nlev = F.nlev; d.dims = F.dims; d.rate = F.rate; d.vec = vec ? 1 : 0;
+        d.row0 = r0; d.row1 = r1;
+        fd[f] = d;
     }
-    zfpx_batch_s *b = new (std::nothrow) zfpx_batch_s;
-    if (!b) return ZFPX_ENOMEM;
-    if (cudaGetDevice(&b->dev) != cudaSuccess) { delete b; return ZFPX_ECUDA; }
-    b->nrows = nrows;
-    b->nq = (nrows + 3) / 4;
-    b->fields.assign(fields, fields + nfields);
-
-    std::vector<int64_t> roff(nrows), qpre(b->nq + 1, 0), rpre(nrows + 1, 0);
-    std::vector<int32_t> rlen(nrows);
-    int64_t o = 0;
-    for (int r = 0; r < nrows; r++) { roff[r] = o; o += row_len[r]; rlen[r] = (int32_t)row_len[r]; }
-    for (int q = 0; q < b->nq; q++) {
-        int64_t mx = 0;
-        for (int j = 0; j < 4 && 4 * q + j < nrows; j++) mx = std::max(mx, row_len[4 * q + j]);
-        qpre[q + 1] = qpre[q] + (mx + 3) / 4;
-    }
-    for (int r = 0; r < nrows; r++) rpre[r + 1] = rpre[r] + (row_len[r] + 3) / 4;
-
-    // field layout and items; chunks ordered by (dims, rate) class, then field, then item
-    std::vector<FieldDevB> fd(nfields);
-    b->field_off.resize(nfields);
-    b->field_bytes.resize(nfields);
-    int64_t off = 0;
-    for (int f = 0; f < nfields; f++) {
-        const zfpx_field &F = fields[f];
-        const int64_t per_block = F.dims == 3 ? 8 * F.rate : F.rate / 2;
-        const int64_t items = F.dims == 3 ? (F.nlev + 3) / 4 : F.nlev;
-        const int64_t blocks = F.dims == 3 ? qpre[b->nq] : rpre[nrows];
-        b->field_off[f] = off;
-        b->field_bytes[f] = items * blocks * per_block;
-        off = (off + b->field_bytes[f] + 255) / 256 * 256;
-        const bool vec = mult4 && (F.lev_stride % 4 == 0 || F.nlev == 1) && !((uintptr_t)F.d_src & 15u) &&
-                         !((uintptr_t)F.d_dst & 15u);
-        fd[f] = FieldDevB{F.d_src, F.d_dst, F.lev_stride, b->field_off[f], F.nlev, F.dims, F.rate, vec ? 1 : 0};
-    }
-    b->total = off;
     std::vector<int> order(nfields);
     for (int f = 0; f < nfields; f++) order[f] = f;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         return std::make_tuple(fields[a].dims, fields[a].rate) < std::make_tuple(fields[c].dims, fields[c].rate);
     });
-    std::vector<ItemDevB> items;
-    int64_t units = 0;
+    items.clear();
+    units = 0;
     for (int f : order) {
         const zfpx_field &F = fields[f];
+        const int r0 = fd[f].row0, r1 = fd[f].row1;
         const int64_t per_block = F.dims == 3 ? 8 * F.rate : F.rate / 2;
-        const int64_t blocks = F.dims == 3 ? qpre[b->nq] : rpre[nrows];
+        const int64_t blocks = field_item_blocks(g, F, r0, r1);
         const int step = F.dims == 3 ? 4 : 1;
-        int64_t ioff = b->field_off[f];
+        int64_t ioff = stream_off[f];
         for (int z = 0; z < F.nlev; z += step) {
             ItemDevB it;
             it.unit0 = units;
@@ -469,12 +494,85 @@ int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const 
             ioff += blocks * per_block;
         }
     }
+}
+
+int launch_batch(const BatchGeom &g, int warps, int ctas_per_sm, bool encode, const uint8_t *in, uint8_t *out,
+                 cudaStream_t st)
+{
+    if (g.nunits == 0) return ZFPX_OK;
+    const void *fn = nullptr;
+    if (encode) fn = warps == 8 ? (const void *)batch_encode_kernel<8> : (const void *)batch_encode_kernel<4>;
+    else fn = warps == 8 ? (const void *)batch_decode_kernel<8> : (const void *)batch_decode_kernel<4>;
+    const int fit = occupancy(fn, 32 * warps);
+    const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, fit) : fit;
+    const int64_t want = (g.nunits + warps - 1) / warps;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
+    if (encode) {
+        if (warps == 8) batch_encode_kernel<8><<<grid, 256, 0, st>>>(g, out);
+        else batch_encode_kernel<4><<<grid, 128, 0, st>>>(g, out);
+    } else {
+        if (warps == 8) batch_decode_kernel<8><<<grid, 256, 0, st>>>(g, in);
+        else batch_decode_kernel<4><<<grid, 128, 0, st>>>(g, in);
+    }
+    count_launch();
+    return check_launch();
+}
+
+}  // namespace
+}  // namespace zfpx
+
+struct zfpx_batch_s {
+    zfpx::GridHost grid;
+    std::vector<zfpx_field> fields;
+    std::vector<int64_t> field_off, field_bytes;
+    int64_t total = 0;
+    int nitems = 0;
+    int64_t nunits = 0;
+    int warps = 4, ctas_per_sm = 0;     // 0 = as many as fit
+    zfpx::FieldDevB *d_fields = nullptr;
+    zfpx::ItemDevB *d_items = nullptr;
+};
+
+using namespace zfpx;
+
+extern "C" {
+
+void zfpx_batch_destroy(zfpx_batch b)
+{
+    if (!b) return;
+    b->grid.free_dev();
+    cudaFree(b->d_fields);
+    cudaFree(b->d_items);
+    delete b;
+}
+
+int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const zfpx_field *fields, int nfields)
+{
+    if (!out) return ZFPX_EINVAL;
+    *out = nullptr;
+    if (!row_len || nrows < 1 || !fields || nfields < 1) return ZFPX_EINVAL;
+    zfpx_batch_s *b = new (std::nothrow) zfpx_batch_s;
+    if (!b) return ZFPX_ENOMEM;
+    int rc = b->grid.init(row_len, nrows);
+    for (int f = 0; f < nfields && !rc; f++) rc = check_field(b->grid, fields[f]);
+    if (rc) { delete b; return rc; }
+    b->fields.assign(fields, fields + nfields);
+    b->field_off.resize(nfields);
+    b->field_bytes.resize(nfields);
+    int64_t off = 0;
+    for (int f = 0; f < nfields; f++) {
+        const zfpx_field &F = fields[f];
+        const int r0 = F.row0, r1 = (F.row0 == 0 && F.row1 == 0) ? nrows : F.row1;
+        b->field_off[f] = off;
+        b->field_bytes[f] = field_stream_bytes(b->grid, F, r0, r1);
+        off = (off + b->field_bytes[f] + 255) / 256 * 256;
+    }
+    b->total = off;
+    std::vector<FieldDevB> fd;
+    std::vector<ItemDevB> items;
+    build_work(b->grid, fields, b->field_off.data(), nfields, fd, items, b->nunits);
     b->nitems = (int)items.size();
-    b->nunits = units;
-    int rc = upload(&b->d_row_off, roff);
-    if (!rc) rc = upload(&b->d_row_len, rlen);
-    if (!rc) rc = upload(&b->d_qpre, qpre);
-    if (!rc) rc = upload(&b->d_rpre, rpre);
+    rc = upload_grid(b->grid);
     if (!rc) rc = upload(&b->d_fields, fd);
     if (!rc) rc = upload(&b->d_items, items);
     if (rc) { zfpx_batch_destroy(b); return rc; }
@@ -504,31 +602,15 @@ int zfpx_batch_set_launch(zfpx_batch b, int warps_per_cta, int ctas_per_sm)
     return ZFPX_OK;
 }
 
-static int batch_launch(zfpx_batch b, bool encode, const uint8_t *in, uint8_t *out, cudaStream_t st)
+static BatchGeom batch_geom(zfpx_batch b)
 {
     BatchGeom g;
     g.items = b->d_items;
     g.fields = b->d_fields;
-    g.grid = GridDev{b->d_row_off, b->d_row_len, b->d_qpre, b->d_rpre, b->nrows, b->nq};
+    g.grid = b->grid.dev();
     g.nitems = b->nitems;
     g.nunits = b->nunits;
-    if (g.nunits == 0) return ZFPX_OK;
-    const void *fn = nullptr;
-    if (encode) fn = b->warps == 8 ? (const void *)batch_encode_kernel<8> : (const void *)batch_encode_kernel<4>;
-    else fn = b->warps == 8 ? (const void *)batch_decode_kernel<8> : (const void *)batch_decode_kernel<4>;
-    const int fit = occupancy(fn, 32 * b->warps);
-    const int per_sm = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, fit) : fit;
-    const int64_t want = (g.nunits + b->warps - 1) / b->warps;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
-    if (encode) {
-        if (b->warps == 8) batch_encode_kernel<8><<<grid, 256, 0, st>>>(g, out);
-        else batch_encode_kernel<4><<<grid, 128, 0, st>>>(g, out);
-    } else {
-        if (b->warps == 8) batch_decode_kernel<8><<<grid, 256, 0, st>>>(g, in);
-        else batch_decode_kernel<4><<<grid, 128, 0, st>>>(g, in);
-    }
-    count_launch();
-    return check_launch();
+    return g;
 }
 
 int zfpx_batch_encode(zfpx_batch b, uint8_t *d_out, size_t cap, void *stream)
@@ -537,7 +619,7 @@ int zfpx_batch_encode(zfpx_batch b, uint8_t *d_out, size_t cap, void *stream)
     if ((int64_t)cap < b->total) return ZFPX_ESIZE;
     for (const zfpx_field &F : b->fields)
         if (!F.d_src || ((uintptr_t)F.d_src & 3u)) return ZFPX_EINVAL;
-    return batch_launch(b, true, nullptr, d_out, (cudaStream_t)stream);
+    return launch_batch(batch_geom(b), b->warps, b->ctas_per_sm, true, nullptr, d_out, (cudaStream_t)stream);
 }
 
 int zfpx_batch_decode(zfpx_batch b, const uint8_t *d_in, size_t len, void *stream)
@@ -546,7 +628,323 @@ int zfpx_batch_decode(zfpx_batch b, const uint8_t *d_in, size_t len, void *strea
     if ((int64_t)len < b->total) return ZFPX_ESIZE;
     for (const zfpx_field &F : b->fields)
         if (!F.d_dst || ((uintptr_t)F.d_dst & 3u)) return ZFPX_EINVAL;
-    return batch_launch(b, false, d_in, nullptr, (cudaStream_t)stream);
+    return launch_batch(batch_geom(b), b->warps, b->ctas_per_sm, false, d_in, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Serving: a request loop with continuous batching.
+//
+// Requests are row x level slabs of fields already resident in device memory
+// (one zfpx_field each).  A request is admitted when its memory -- its
+// compressed stream and its decoded copy -- fits in the server's arena, which
+// is one device allocation made at creation and sized by the HBM budget;
+// requests that can never fit are refused at submission.  Every pump() puts
+// all requests admitted since the previous batch (first come, first served;
+// at most max_batch) into one batch -- one encode launch and one decode
+// launch -- on the next of `nstreams` streams, so batches launched while
+// earlier ones are still running overlap on the device.  poll() reports the
+// requests of finished batches; their results stay valid until released,
+// which returns their memory to the arena.  The descriptors of a batch go
+// through pinned staging buffers, one per stream, reused once the stream's
+// previous batch has finished; nothing is allocated after creation.
+// Not thread safe: one host thread drives a server.
+namespace zfpx {
+namespace {
+
+struct ServerReq {
+    zfpx_field f;            // d_dst / dst_lev_stride filled in at admission
+    int r0, r1;
+    int64_t span;            // points per level in the slab
+    int64_t stream_bytes, values_bytes, mem_bytes;
+    int64_t mem_off = -1;    // arena offset (stream, then values)
+    int state = 0;           // 0 queued, 1 in flight, 2 done
+};
+
+struct ServerSlot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    uint8_t *h_stage = nullptr;   // pinned
+    uint8_t *d_desc = nullptr;
+    size_t cap = 0;
+    bool busy = false;
+    std::vector<int64_t> ids;
+};
+
+// first-fit allocator over the arena with coalescing
+struct ArenaAlloc {
+    std::map<int64_t, int64_t> free_;   // offset -> size
+    int64_t total = 0, used = 0;
+    void init(int64_t bytes) { free_.clear(); free_[0] = bytes; total = bytes; used = 0; }
+    int64_t take(int64_t n)
+    {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                const int64_t off = it->first, rest = it->second - n;
+                free_.erase(it);
+                if (rest > 0) free_[off + n] = rest;
+                used += n;
+                return off;
+            }
+        }
+        return -1;
+    }
+    void give(int64_t off, int64_t n)
+    {
+        used -= n;
+        auto it = free_.emplace(off, n).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) { it->second += nx->second; free_.erase(nx); }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) { pv->second += it->second; free_.erase(it); }
+        }
+    }
+};
+
+constexpr int kItemsPerRequest = 160;   // descriptor room per admitted request (137 levels + margin)
+
+}  // namespace
+}  // namespace zfpx
+
+struct zfpx_server_s {
+    zfpx::GridHost grid;
+    uint8_t *d_arena = nullptr;
+    zfpx::ArenaAlloc arena;
+    std::deque<int64_t> queue;
+    std::unordered_map<int64_t, zfpx::ServerReq> reqs;
+    std::vector<zfpx::ServerSlot> slots;
+    int next_slot = 0;
+    int64_t next_id = 1;
+    int max_batch = 64;
+    int warps = 4, ctas_per_sm = 0;
+    std::deque<int64_t> completed;
+    int64_t batches = 0;
+};
+
+extern "C" {
+
+void zfpx_server_destroy(zfpx_server s)
+{
+    if (!s) return;
+    for (auto &sl : s->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+        if (sl.h_stage) cudaFreeHost(sl.h_stage);
+        if (sl.d_desc) cudaFree(sl.d_desc);
+    }
+    cudaFree(s->d_arena);
+    s->grid.free_dev();
+    delete s;
+}
+
+int zfpx_server_create(zfpx_server *out, const int64_t *row_len, int nrows, size_t arena_bytes, int nstreams,
+                       int max_batch)
+{
+    if (!out) return ZFPX_EINVAL;
+    *out = nullptr;
+    if (!row_len || nrows < 1 || arena_bytes < 4096 || nstreams < 1 || nstreams > 64 || max_batch < 1 ||
+        max_batch > 4096)
+        return ZFPX_EINVAL;
+    zfpx_server_s *s = new (std::nothrow) zfpx_server_s;
+    if (!s) return ZFPX_ENOMEM;
+    int rc = s->grid.init(row_len, nrows);
+    if (!rc) rc = upload_grid(s->grid);
+    if (!rc && cudaMalloc((void **)&s->d_arena, arena_bytes) != cudaSuccess) rc = ZFPX_ENOMEM;
+    s->arena.init((int64_t)arena_bytes / 256 * 256);
+    s->max_batch = max_batch;
+    const size_t cap = (size_t)max_batch * (sizeof(FieldDevB) + kItemsPerRequest * sizeof(ItemDevB)) + 256;
+    s->slots.resize(nstreams);
+    for (auto &sl : s->slots) {
+        if (rc) break;
+        sl.cap = cap;
+        if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+            rc = ZFPX_ECUDA;
+        else if (cudaMallocHost((void **)&sl.h_stage, cap) != cudaSuccess || cudaMalloc((void **)&sl.d_desc, cap) != cudaSuccess)
+            rc = ZFPX_ENOMEM;
+    }
+    if (rc) { zfpx_server_destroy(s); return rc; }
+    *out = s;
+    return ZFPX_OK;
+}
+
+int zfpx_server_set_launch(zfpx_server s, int warps_per_cta, int ctas_per_sm)
+{
+    if (!s || (warps_per_cta != 4 && warps_per_cta != 8) || ctas_per_sm < 0) return ZFPX_EINVAL;
+    s->warps = warps_per_cta;
+    s->ctas_per_sm = ctas_per_sm;
+    return ZFPX_OK;
+}
+
+int zfpx_server_submit(zfpx_server s, const zfpx_field *req, int64_t *id)
+{
+    if (!s || !req || !id || !req->d_src) return ZFPX_EINVAL;
+    int rc = check_field(s->grid, *req);
+    if (rc) return rc;
+    if (((req->dims == 3 ? (req->nlev + 3) / 4 : req->nlev)) > kItemsPerRequest) return ZFPX_EINVAL;
+    ServerReq r;
+    r.f = *req;
+    r.r0 = req->row0;
+    r.r1 = (req->row0 == 0 && req->row1 == 0) ? s->grid.nrows : req->row1;
+    r.span = s->grid.roff[r.r1 - 1] + s->grid.rlen[r.r1 - 1] - s->grid.roff[r.r0];
+    r.stream_bytes = field_stream_bytes(s->grid, *req, r.r0, r.r1);
+    r.values_bytes = 4 * r.span * req->nlev;
+    r.mem_bytes = (r.stream_bytes + 255) / 256 * 256 + (r.values_bytes + 255) / 256 * 256;
+    if (r.mem_bytes > s->arena.total) return ZFPX_ENOMEM_BUDGET;
+    const int64_t rid = s->next_id++;
+    s->reqs.emplace(rid, r);
+    s->queue.push_back(rid);
+    *id = rid;
+    return ZFPX_OK;
+}
+
+static void server_reap(zfpx_server s)
+{
+    for (auto &sl : s->slots) {
+        if (!sl.busy) continue;
+        if (cudaEventQuery(sl.done) != cudaSuccess) continue;
+        for (int64_t rid : sl.ids) {
+            s->reqs[rid].state = 2;
+            s->completed.push_back(rid);
+        }
+        sl.ids.clear();
+        sl.busy = false;
+    }
+}
+
+int zfpx_server_pump(zfpx_server s, int *launched)
+{
+    if (!s) return ZFPX_EINVAL;
+    if (launched) *launched = 0;
+    server_reap(s);
+    if (s->queue.empty()) return ZFPX_OK;
+    // the next stream whose previous batch has finished
+    int si = -1;
+    for (int t = 0; t < (int)s->slots.size(); t++) {
+        const int c = (s->next_slot + t) % (int)s->slots.size();
+        if (!s->slots[c].busy) { si = c; break; }
+    }
+    if (si < 0) return ZFPX_OK;
+    ServerSlot &sl = s->slots[si];
+    // admit first come, first served while the arena has room
+    std::vector<int64_t> ids;
+    while (!s->queue.empty() && (int)ids.size() < s->max_batch) {
+        ServerReq &r = s->reqs[s->queue.front()];
+        const int64_t off = s->arena.take(r.mem_bytes);
+        if (off < 0) break;
+        r.mem_off = off;
+        r.f.d_dst = reinterpret_cast<float *>(s->d_arena + off + (r.stream_bytes + 255) / 256 * 256);
+        r.f.dst_lev_stride = r.span;
+        r.state = 1;
+        ids.push_back(s->queue.front());
+        s->queue.pop_front();
+    }
+    if (ids.empty()) return ZFPX_OK;
+    std::vector<zfpx_field> fields(ids.size());
+    std::vector<int64_t> soff(ids.size());
+    for (size_t i = 0; i < ids.size(); i++) {
+        const ServerReq &r = s->reqs[ids[i]];
+        fields[i] = r.f;
+        soff[i] = r.mem_off;          // stream first, at the start of the request's memory
+    }
+    std::vector<FieldDevB> fd;
+    std::vector<ItemDevB> items;
+    int64_t units = 0;
+    build_work(s->grid, fields.data(), soff.data(), (int)fields.size(), fd, items, units);
+    const size_t fbytes = fd.size() * sizeof(FieldDevB);
+    const size_t ioff = (fbytes + 255) / 256 * 256;
+    const size_t total = ioff + items.size() * sizeof(ItemDevB);
+    if (total > sl.cap) return ZFPX_ESIZE;
+    std::memcpy(sl.h_stage, fd.data(), fbytes);
+    std::memcpy(sl.h_stage + ioff, items.data(), items.size() * sizeof(ItemDevB));
+    if (cudaMemcpyAsync(sl.d_desc, sl.h_stage, total, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+        return ZFPX_ECUDA;
+    BatchGeom g;
+    g.fields = reinterpret_cast<const FieldDevB *>(sl.d_desc);
+    g.items = reinterpret_cast<const ItemDevB *>(sl.d_desc + ioff);
+    g.grid = s->grid.dev();
+    g.nitems = (int)items.size();
+    g.nunits = units;
+    int rc = launch_batch(g, s->warps, s->ctas_per_sm, true, nullptr, s->d_arena, sl.stream);
+    if (!rc) rc = launch_batch(g, s->warps, s->ctas_per_sm, false, s->d_arena, nullptr, sl.stream);
+    if (!rc && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = ZFPX_ECUDA;
+    if (rc) return rc;
+    sl.ids = ids;
+    sl.busy = true;
+    s->next_slot = (si + 1) % (int)s->slots.size();
+    s->batches++;
+    if (launched) *launched = (int)ids.size();
+    return ZFPX_OK;
+}
+
+int zfpx_server_poll(zfpx_server s, int64_t *done, int max, int *ndone)
+{
+    if (!s || !ndone || (max > 0 && !done)) return ZFPX_EINVAL;
+    server_reap(s);
+    int n = 0;
+    while (n < max && !s->completed.empty()) {
+        done[n++] = s->completed.front();
+        s->completed.pop_front();
+    }
+    *ndone = n;
+    return ZFPX_OK;
+}
+
+int zfpx_server_result(zfpx_server s, int64_t id, const uint8_t **d_stream, size_t *stream_bytes,
+                       const float **d_values, size_t *values_bytes)
+{
+    if (!s) return ZFPX_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end() || it->second.state != 2) return ZFPX_EINVAL;
+    const ServerReq &r = it->second;
+    if (d_stream) *d_stream = s->d_arena + r.mem_off;
+    if (stream_bytes) *stream_bytes = (size_t)r.stream_bytes;
+    if (d_values) *d_values = r.f.d_dst;
+    if (values_bytes) *values_bytes = (size_t)r.values_bytes;
+    return ZFPX_OK;
+}
+
+int zfpx_server_copy_result(zfpx_server s, int64_t id, uint8_t *h_stream, size_t stream_cap, float *h_values,
+                            size_t values_cap)
+{
+    if (!s) return ZFPX_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end() || it->second.state != 2) return ZFPX_EINVAL;
+    const ServerReq &r = it->second;
+    if ((h_stream && stream_cap < (size_t)r.stream_bytes) || (h_values && values_cap < (size_t)r.values_bytes))
+        return ZFPX_ESIZE;
+    if (h_stream && cudaMemcpy(h_stream, s->d_arena + r.mem_off, r.stream_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ZFPX_ECUDA;
+    if (h_values && cudaMemcpy(h_values, r.f.d_dst, r.values_bytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return ZFPX_ECUDA;
+    return ZFPX_OK;
+}
+
+int zfpx_server_release(zfpx_server s, int64_t id)
+{
+    if (!s) return ZFPX_EINVAL;
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end() || it->second.state != 2) return ZFPX_EINVAL;
+    s->arena.give(it->second.mem_off, it->second.mem_bytes);
+    s->reqs.erase(it);
+    return ZFPX_OK;
+}
+
+int zfpx_server_stats(zfpx_server s, int64_t out[6])
+{
+    if (!s || !out) return ZFPX_EINVAL;
+    int busy = 0;
+    for (auto &sl : s->slots) busy += sl.busy ? 1 : 0;
+    out[0] = (int64_t)s->queue.size();
+    out[1] = busy;
+    out[2] = s->arena.used;
+    out[3] = s->arena.total;
+    out[4] = s->batches;
+    out[5] = (int64_t)s->completed.size();
+    return ZFPX_OK;
 }
 
 }  // extern "C"

@@ -330,10 +330,9 @@ ZFPX_HD uint64_t decode_plane(Reader &rd, int &n, int &R)
     return X;
 }
 
-// Fast paths for a plane that is known to fit: every plane of S = 64
+// Fast path for a plane that is known to fit: every plane of S = 64
 // coefficients costs at most 127 bits, so with R >= 127 no bit can hit the
-// budget and the per-bit budget checks drop out.  Same bits as code_plane /
-// decode_plane.
+// budget and the per-bit budget checks drop out.  Same bits as code_plane.
 template <int S, class Writer>
 ZFPX_HD void code_plane_fit(Writer &wr, uint64_t X, int &n, int &R)
 {
@@ -349,33 +348,6 @@ ZFPX_HD void code_plane_fit(Writer &wr, uint64_t X, int &n, int &R)
         n += p + 1;
         rest >>= p + 1;
         if (!rest) { wr.put(0ull, 1); R -= 1; return; }                  // n < S here
-    }
-}
-
-template <int S, class Reader>
-ZFPX_HD uint64_t decode_plane_fit(Reader &rd, int &n, int &R)
-{
-    uint64_t w = rd.peek();
-    if (n >= S) { rd.skip(S); R -= S; return w; }
-    uint64_t X = w & low_mask(n);
-    if (!((w >> n) & 1ull)) { rd.skip(n + 1); R -= n + 1; return X; }   // verbatim, then G = 0
-    rd.skip(n + 1);
-    R -= n + 1;
-    for (;;) {                                                            // a group bit 1 was read
-        const int lim = S - 1 - n;
-        w = rd.peek();
-        const int tz = w ? lowest_set(w) : 64;
-        if (tz >= lim) {                                                  // only the implied one left
-            rd.skip(lim); R -= lim;
-            X |= 1ull << (S - 1);
-            n = S;
-            return X;
-        }
-        X |= 1ull << (n + tz);
-        n += tz + 1;                                                      // n < S
-        const uint64_t g = (w >> (tz + 1)) & 1ull;                         // the next group bit
-        rd.skip(tz + 2); R -= tz + 2;
-        if (!g) return X;
     }
 }
 
@@ -423,202 +395,7 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
     wr.finish();
 }
 
-template <int RATE, class Reader, class Planes>
-ZFPX_HD void decode_block3(Reader &rd, float (&x)[64], Planes &pl)
-{
-    constexpr int kSeq[64] = ZFPX_SEQ3;
-    const uint64_t head = rd.peek();
-    if (!(head & 1ull)) {
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = 0.0f;
-        return;
-    }
-    const int e = (int)((head >> 1) & 0xffu);
-    rd.skip(9);
-    int n = 0, R = 64 * RATE - 9;
-#pragma unroll 1
-    for (int k = 31; k >= 0; k--) {
-        uint64_t X = 0;
-        if (R >= 127) X = decode_plane_fit<64>(rd, n, R);
-        else if (R > 0) X = decode_plane<64>(rd, n, R);
-        pl.store(k, X);
-    }
-    uint32_t lo[32], hi[32];
-#pragma unroll
-    for (int k = 0; k < 32; k++) {
-        const uint64_t X = pl.load(k);
-        lo[k] = (uint32_t)X;
-        hi[k] = (uint32_t)(X >> 32);
-    }
-    transpose32(lo);
-    transpose32(hi);
-    int32_t q[64];
-#pragma unroll
-    for (int t = 0; t < 32; t++) {
-        q[kSeq[t]] = from_negabinary(lo[t]);
-        q[kSeq[32 + t]] = from_negabinary(hi[t]);
-    }
-    xform3_inv(q);
-    if (e >= 31) {
-        const float sc = dequant_scale(e);
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = dequantize_fast(q[i], sc);
-    } else {
-        // rare: park q in the plane tile and convert in a rolled loop, so the
-        // common path above never pays for the slow one
-        uint32_t *w = pl.words();
-#pragma unroll
-        for (int i = 0; i < 64; i++) w[pl.word_index(i)] = (uint32_t)q[i];
-#pragma unroll 1
-        for (int i = 0; i < 64; i++) w[pl.word_index(i)] = f2u(dequantize_small((int32_t)w[pl.word_index(i)], e));
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = u2f(w[pl.word_index(i)]);
-    }
-}
-
-// ----------------------------------------------------------------- 3-D block, tile coder
-// The same bits as encode_block3 / decode_block3, produced with less warp
-// divergence.  The stream of one block lives in a tile of 32-bit words
-// (Tile: get(i), set(i, v), orw(i, v); word i holds stream bits 32i..32i+31).
-//
-// Encoder, two passes.  Pass 1 walks the planes with closed forms only:
-// with n coefficients significant, plane X costs n verbatim bits plus, for
-// rest = X >> n with c set bits and highest set index j, j + 1 + c + [j<63]
-// - [j=63] bits (n + 1 if c = 0; 64 if n = 64).  It writes the verbatim
-// bits and the first group bit of each plane and leaves the rest of the
-// group section zero.  Pass 2 visits every newly significant coefficient
-// (any plane, any order): event t of a plane whose group section starts at
-// a (just after its first group bit) puts its 1 at a + (p_t - n) + t and,
-// when another event follows, the next group bit right after it.  The last
-// coefficient's 1 is implied and not written.  Bits at or past the budget
-// are never written.
-template <class Tile>
-struct TileWriter {
-    Tile &t;
-    uint64_t acc;
-    int nb, w, end_w;
-    ZFPX_HD void flush32()
-    {
-        if (w < end_w) t.set(w, (uint32_t)acc);
-        w++;
-        acc >>= 32;
-        nb -= 32;
-    }
-    ZFPX_HD void put(uint64_t bits, int len)          // 0 <= len <= 32, bits < 2^len
-    {
-        acc |= bits << nb;
-        nb += len;
-        if (nb >= 32) flush32();
-    }
-    ZFPX_HD void put64(uint64_t bits, int len)        // 0 <= len <= 64
-    {
-        if (len > 32) { put(bits & 0xffffffffull, 32); put(bits >> 32, len - 32); }
-        else put(bits, len);
-    }
-    ZFPX_HD void zeros(int len)                        // len >= 0
-    {
-        nb += len;
-        while (nb >= 32) flush32();
-    }
-    ZFPX_HD void finish()
-    {
-        while (w < end_w) { t.set(w, (uint32_t)acc); acc >>= 32; w++; }
-    }
-};
-
-template <int RATE, class Tile, class Planes, class Info>
-ZFPX_HD void encode_block3_tile(const float (&x)[64], Tile &tile, Planes &pl, Info &info)
-{
-    constexpr int kSeq[64] = ZFPX_SEQ3;
-    constexpr int END = 64 * RATE;
-    uint32_t amax = 0;
-#pragma unroll
-    for (int i = 0; i < 64; i++) {
-        const uint32_t a = f2u(x[i]) & 0x7fffffffu;
-        amax = a > amax ? a : amax;
-    }
-    const int E = (int)(amax >> 23);
-    if (amax < 0x00400000u || E == 255) {
-#pragma unroll
-        for (int i = 0; i < 2 * RATE; i++) tile.set(i, 0u);
-        return;
-    }
-    const QuantScale qs(E);
-    int32_t q[64];
-#pragma unroll
-    for (int i = 0; i < 64; i++) q[i] = qs(x[i]);
-    xform3_fwd(q);
-    uint32_t lo[32], hi[32];
-#pragma unroll
-    for (int t = 0; t < 32; t++) {
-        lo[t] = to_negabinary(q[kSeq[t]]);
-        hi[t] = to_negabinary(q[kSeq[32 + t]]);
-    }
-    transpose32(lo);
-    transpose32(hi);
-#pragma unroll
-    for (int k = 0; k < 32; k++) pl.store(k, ((uint64_t)hi[k] << 32) | lo[k]);
-
-    // pass 1: verbatim bits and first group bits, in stream order
-    TileWriter<Tile> wr{tile, 0ull, 0, 0, 2 * RATE};
-    wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    int n = 0, pos = 9;
-    uint32_t evplanes = 0;
-#pragma unroll 1
-    for (int k = 31; k >= 0 && pos < END; k--) {
-        const uint64_t X = pl.load(k);
-        const int room = END - pos;
-        if (n >= 64) {
-            wr.put64(X & low_mask(room), room < 64 ? room : 64);
-            pos += 64;
-            continue;
-        }
-        const uint64_t rest = X >> n;
-        const uint64_t verb = X & low_mask(n);
-        if (!rest) {                                             // n verbatim bits, G = 0
-            const int len = n + 1 < room ? n + 1 : room;
-            wr.put64(verb & low_mask(len), len);
-            pos += n + 1;
-            continue;
-        }
-        const int c = popc64(rest);
-        const int j = highest_set64(rest) + n;
-        const int L = j + 1 + c + (j < 63 ? 1 : 0) - (j == 63 ? 1 : 0);
-        // verbatim bits, then G = 1 at bit n
-        const int len = n + 1 < room ? n + 1 : room;
-        wr.put64((verb | (1ull << n)) & low_mask(len), len);
-        const int rest_len = L - (n + 1);
-        wr.zeros(rest_len < room - len ? rest_len : room - len);
-        info.set(k, (uint32_t)n | ((uint32_t)(pos + n + 1) << 8));
-        evplanes |= 1u << k;
-        pos += L;
-        n = j + 1;
-    }
-    wr.finish();
-
-    // pass 2: one iteration per newly significant coefficient
-    uint64_t rest = 0;
-    int a = 0, t = 0, nn = 0;
-#pragma unroll 1
-    while (rest || evplanes) {
-        if (!rest) {
-            const int k = highest_set32(evplanes);
-            evplanes &= ~(1u << k);
-            const uint32_t inf = info.get(k);
-            nn = (int)(inf & 0xffu);
-            a = (int)(inf >> 8);
-            rest = pl.load(k) >> nn;
-            t = 0;
-        }
-        const int qpos = lowest_set(rest);
-        rest &= rest - 1;
-        const int A = a + qpos + t;
-        if (nn + qpos != 63 && A < END) tile.orw(A >> 5, 1u << (A & 31));
-        if (rest && A + 1 < END) tile.orw((A + 1) >> 5, 1u << ((A + 1) & 31));
-        t++;
-    }
-}
-
+// ----------------------------------------------------------------- 3-D decoder over a stream tile
 // Decoder: one loop over "steps" -- the start of a plane (verbatim bits and
 // a group bit) or one newly significant coefficient (zeros, its 1, the next
 // group bit) -- so lanes that are in different planes still run the same
@@ -693,167 +470,6 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
         }
     }
     if (!start && k >= 0) pl.store(k, X);                        // budget ended inside a plane
-    uint32_t lo[32], hi[32];
-#pragma unroll
-    for (int kk = 0; kk < 32; kk++) {
-        const uint64_t P = pl.load(kk);
-        lo[kk] = (uint32_t)P;
-        hi[kk] = (uint32_t)(P >> 32);
-    }
-    transpose32(lo);
-    transpose32(hi);
-    int32_t q[64];
-#pragma unroll
-    for (int t = 0; t < 32; t++) {
-        q[kSeq[t]] = from_negabinary(lo[t]);
-        q[kSeq[32 + t]] = from_negabinary(hi[t]);
-    }
-    xform3_inv(q);
-    if (e >= 31) {
-        const float sc = dequant_scale(e);
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = dequantize_fast(q[i], sc);
-    } else {
-        uint32_t *wd = pl.words();
-#pragma unroll
-        for (int i = 0; i < 64; i++) wd[pl.word_index(i)] = (uint32_t)q[i];
-#pragma unroll 1
-        for (int i = 0; i < 64; i++) wd[pl.word_index(i)] = f2u(dequantize_small((int32_t)wd[pl.word_index(i)], e));
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = u2f(wd[pl.word_index(i)]);
-    }
-}
-
-// Encoder, one uniform step loop (the decoder's step structure, mirrored).
-// Every step emits some prefix bits followed by one group bit:
-//   plane start: the n verbatim bits, then G = [X has a 1 at or above n]
-//                (n = 64: 64 verbatim bits, no group bit);
-//   event:       p zeros and the 1 of the next significant coefficient, then
-//                G = [another 1 follows] (the last coefficient's 1 is implied:
-//                p zeros only, no group bit).
-// Both are computed with selects, so all lanes run the same instructions
-// whatever step they are on.  Writer: put(bits, len), 0 <= len <= 64.
-template <int RATE, class Writer, class Planes>
-ZFPX_HD void code_planes_steps(Writer &wr, Planes &pl)
-{
-    constexpr int END = 64 * RATE;
-    int pos = 9, n = 0, k = 31;
-    bool start = true;
-    uint64_t rest = 0;
-#pragma unroll 1
-    while (k >= 0 && pos < END) {
-        const uint64_t X = pl.load(k);
-        const uint64_t rs = start ? (n < 64 ? X >> n : 0ull) : rest;    // candidates, relative to n
-        const int p = rs ? lowest_set(rs) : 64;                          // zeros before the next one
-        const bool implied = !start && (n + p == 63);
-        const uint64_t after = (!start && p < 63) ? (rs >> (p + 1)) : rs;
-        // prefix
-        const int plen = start ? n : (implied ? p : p + 1);
-        const uint64_t pbits = start ? (X & low_mask(n)) : (implied ? 0ull : (1ull << p));
-        // group bit
-        const bool hasg = start ? (n < 64) : !implied;
-        const bool g = start ? (rs != 0) : (after != 0);
-        int len = plen + (hasg ? 1 : 0);
-        uint64_t bits = pbits | ((hasg && g && plen < 64) ? (1ull << plen) : 0ull);
-        const int room = END - pos;
-        if (len > room) { len = room; bits &= low_mask(room); }
-        wr.put(bits, len);
-        pos += len;
-        // state
-        const bool done = start ? (!hasg || !g) : (implied || !g);
-        if (!start) n = implied ? 64 : n + p + 1;
-        rest = start ? rs : after;
-        start = done;
-        k -= done ? 1 : 0;
-    }
-}
-
-template <int RATE, class Writer, class Planes>
-ZFPX_HD void encode_block3_steps(const float (&x)[64], Writer &wr, Planes &pl)
-{
-    constexpr int kSeq[64] = ZFPX_SEQ3;
-    uint32_t amax = 0;
-#pragma unroll
-    for (int i = 0; i < 64; i++) {
-        const uint32_t a = f2u(x[i]) & 0x7fffffffu;
-        amax = a > amax ? a : amax;
-    }
-    // E = e_max + 126; a subnormal max in [2^-127, 2^-126) has e_max = -126 too
-    const int E = (int)(amax >> 23);
-    if (amax < 0x00400000u || E == 255) { wr.finish(); return; }
-    const QuantScale qs(E);
-    int32_t q[64];
-#pragma unroll
-    for (int i = 0; i < 64; i++) q[i] = qs(x[i]);
-    xform3_fwd(q);
-    uint32_t lo[32], hi[32];
-#pragma unroll
-    for (int t = 0; t < 32; t++) {
-        lo[t] = to_negabinary(q[kSeq[t]]);
-        hi[t] = to_negabinary(q[kSeq[32 + t]]);
-    }
-    transpose32(lo);
-    transpose32(hi);
-#pragma unroll
-    for (int k = 0; k < 32; k++) pl.store(k, ((uint64_t)hi[k] << 32) | lo[k]);
-    wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    int n = 0, R = 64 * RATE - 9;
-    (void)n; (void)R;
-    code_planes_steps<RATE>(wr, pl);
-    wr.finish();
-}
-
-// Decoder step loop with the step type chosen by selects (see
-// code_planes_steps); reads 64-bit windows from a tile of 32-bit words.
-template <int RATE, class Tile, class Planes>
-ZFPX_HD void decode_planes_steps(const Tile &tile, Planes &pl)
-{
-    constexpr int END = 64 * RATE;
-#pragma unroll
-    for (int k = 0; k < 32; k++) pl.store(k, 0ull);
-    int pos = 9, n = 0, k = 31;
-    bool start = true, stop = false;
-    uint64_t X = 0;
-#pragma unroll 1
-    while (!stop && k >= 0 && (pos < END || (!start && n == 63))) {
-        const int rem = END - pos;
-        const uint64_t w = tile_peek(tile, pos);
-        const int tz = w ? lowest_set(w) : 64;
-        const int lim = 63 - n;
-        const bool implied = !start && tz >= lim;
-        const int plen = start ? n : (implied ? lim : tz + 1);           // bits before the group bit
-        const bool hasg = start ? (n < 64) : !implied;
-        // bits this step reads from the window, and what they set in X
-        const int take = plen < rem ? plen : rem;                        // start: verbatim bits read
-        const uint64_t vbits = start ? (w & low_mask(take)) : 0ull;
-        const bool setone = !start && (implied ? rem >= lim : rem >= tz + 1);
-        const uint64_t one = setone ? (1ull << (implied ? 63 : n + tz)) : 0ull;
-        const bool readg = hasg && rem >= plen + 1;                      // the group bit is within budget
-        const bool g = readg && ((plen < 64 ? (w >> plen) : 0ull) & 1ull);
-        X = (start ? vbits : X) | one;
-        // a step that cannot read its group bit (or has none) ends the plane
-        const bool plane_end = !g;
-        stop = (start ? rem <= n : (implied ? rem < lim : rem <= tz + 1)) && !(implied && rem >= lim);
-        if (!start) n = implied ? (setone ? 64 : n) : (setone ? n + tz + 1 : n);
-        pos += plen + (readg ? 1 : 0);
-        if (plane_end || stop) { pl.store(k, X); k--; }
-        start = plane_end;
-    }
-    if (!stop && !start && k >= 0) pl.store(k, X);               // budget ended inside a plane
-}
-
-template <int RATE, class Tile, class Planes>
-ZFPX_HD void decode_block3_steps(const Tile &tile, float (&x)[64], Planes &pl)
-{
-    constexpr int kSeq[64] = ZFPX_SEQ3;
-    const uint64_t head = tile_peek(tile, 0);
-    if (!(head & 1ull)) {
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = 0.0f;
-        return;
-    }
-    const int e = (int)((head >> 1) & 0xffu);
-    decode_planes_steps<RATE>(tile, pl);
     uint32_t lo[32], hi[32];
 #pragma unroll
     for (int kk = 0; kk < 32; kk++) {

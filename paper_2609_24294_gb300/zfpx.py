@@ -37,7 +37,8 @@ class View3(ctypes.Structure):
 
 class Field(ctypes.Structure):
     _fields_ = [("d_src", ctypes.c_void_p), ("d_dst", ctypes.c_void_p), ("lev_stride", ctypes.c_int64),
-                ("nlev", ctypes.c_int32), ("dims", ctypes.c_int32), ("rate", ctypes.c_int32),
+                ("dst_lev_stride", ctypes.c_int64), ("nlev", ctypes.c_int32), ("dims", ctypes.c_int32),
+                ("rate", ctypes.c_int32), ("row0", ctypes.c_int32), ("row1", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
 
 
@@ -83,6 +84,18 @@ def lib():
         "zfpx_graph_launch": ([vp, vp], ctypes.c_int),
         "zfpx_transpose_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
         "zfpx_capture_begin": ([vp], ctypes.c_int),
+        "zfpx_server_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, sz, ctypes.c_int, ctypes.c_int],
+                               ctypes.c_int),
+        "zfpx_server_destroy": ([vp], None),
+        "zfpx_server_set_launch": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_server_submit": ([vp, ctypes.POINTER(Field), i64p], ctypes.c_int),
+        "zfpx_server_pump": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "zfpx_server_poll": ([vp, i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "zfpx_server_result": ([vp, ctypes.c_int64, ctypes.POINTER(vp), ctypes.POINTER(sz), ctypes.POINTER(vp),
+                                ctypes.POINTER(sz)], ctypes.c_int),
+        "zfpx_server_release": ([vp, ctypes.c_int64], ctypes.c_int),
+        "zfpx_server_copy_result": ([vp, ctypes.c_int64, vp, sz, vp, sz], ctypes.c_int),
+        "zfpx_server_stats": ([vp, i64p], ctypes.c_int),
         "zfpx_capture_end": ([ctypes.POINTER(vp), vp], ctypes.c_int),
         "zfpx_batch_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, ctypes.POINTER(Field), ctypes.c_int],
                               ctypes.c_int),
@@ -383,9 +396,12 @@ class Batch:
             descs[i].d_src = src.data_ptr() if src is not None else None
             descs[i].d_dst = dst.data_ptr() if dst is not None else None
             descs[i].lev_stride = t.stride(0)
+            descs[i].dst_lev_stride = 0
             descs[i].nlev = t.shape[0]
             descs[i].dims = dims
             descs[i].rate = rate
+            descs[i].row0 = 0
+            descs[i].row1 = 0
             descs[i].reserved = 0
             self._keep.append((src, dst))
         h = ctypes.c_void_p()
