@@ -28,6 +28,7 @@
 
 #include "zfpx_internal.h"
 #include "zfpx_block.cuh"
+#include "zfpx_smem.cuh"
 
 namespace zfpx {
 namespace {
@@ -102,45 +103,6 @@ struct ItemWalk {
     }
 };
 
-template <int RATE>
-struct SmemWriterB {
-    uint64_t *sm;
-    uint64_t acc;
-    int nb, w, lane;
-    __device__ __forceinline__ void put(uint64_t bits, int len)
-    {
-        acc |= bits << nb;
-        int t = nb + len;
-        if (t >= 64) {
-            sm[w * 32 + (lane ^ w)] = acc;
-            w++;
-            acc = nb ? (bits >> (64 - nb)) : 0ull;
-            t -= 64;
-        }
-        nb = t;
-    }
-    __device__ __forceinline__ void finish()
-    {
-        if (nb > 0) { sm[w * 32 + (lane ^ w)] = acc; w++; }
-        for (; w < RATE; w++) sm[w * 32 + (lane ^ w)] = 0ull;
-    }
-};
-
-struct SmemPlanesB {
-    uint64_t *sm;
-    int lane;
-    __device__ __forceinline__ void store(int k, uint64_t X) { sm[k * 32 + lane] = X; }
-    __device__ __forceinline__ uint64_t load(int k) const { return sm[k * 32 + lane]; }
-    __device__ __forceinline__ uint32_t *words() { return reinterpret_cast<uint32_t *>(sm); }
-    __device__ __forceinline__ int word_index(int i) const { return (i >> 1) * 64 + 2 * lane + (i & 1); }
-};
-
-struct StreamTileB {
-    const uint32_t *sm;
-    int lane;
-    __device__ __forceinline__ uint32_t get(int i) const { return sm[i * 32 + lane]; }
-};
-
 // 64 values of a 3-D block of row-quad q, x block bxi, levels z0.. (clamped)
 __device__ __forceinline__ void gather_quad(const FieldDevB &f, const GridDev &g, int q, int bxi, int z0, int nz,
                                             float (&x)[64])
@@ -195,7 +157,8 @@ __device__ __forceinline__ void scatter_quad(const FieldDevB &f, const GridDev &
 
 template <int RATE>
 __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                           int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint8_t *out)
+                                           int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint16_t *wax,
+                                           uint8_t *out)
 {
     if (lane < nact) {
         const int64_t bg = b0 + lane + f.b0;
@@ -203,9 +166,10 @@ __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g,
         const int bxi = (int)(bg - __ldg(g.qpre + q));
         float x[64];
         gather_quad(f, g, q, bxi, it.z0, it.nz, x);
-        SmemWriterB<RATE> wr{wsm, 0ull, 0, 0, lane};
-        SmemPlanesB pl{wpl, lane};
-        encode_block3<RATE>(x, wr, pl);
+        SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
+        SmemPlanes pl{wpl, lane};
+        SmemAux aux{wax, lane};
+        encode_block3<RATE>(x, wr, pl, aux);
     }
     __syncwarp();
     uint64_t *dst = reinterpret_cast<uint64_t *>(out + it.out_off) + b0 * RATE;
@@ -246,6 +210,7 @@ batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
 {
     __shared__ uint64_t sout[WARPS][16 * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
+    __shared__ uint16_t saux[WARPS][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * WARPS;
     const int64_t gw = (int64_t)blockIdx.x * WARPS + wid;
@@ -261,8 +226,8 @@ batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
         const int64_t b0 = (c - it.unit0) * 32;
         const int nact = (int)min((int64_t)32, it.nblocks - b0);
         if (f.dims == 3) {
-            if (f.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
-            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
+            if (f.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], saux[wid], out);
+            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], saux[wid], out);
         } else {
             if (f.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
             else enc1_chunk<16>(f, bg.grid, it, b0, nact, lane, out);
@@ -289,8 +254,8 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
     const int q = upper_index(g.qpre, g.nq + 1, bg);
     const int bxi = (int)(bg - __ldg(g.qpre + q));
     float x[64];
-    const StreamTileB tile{t32, lane};
-    SmemPlanesB pl{wpl, lane};
+    const StreamTile tile{t32, lane};
+    SmemPlanes pl{wpl, lane};
     decode_block3_tile<RATE>(tile, x, pl);
     scatter_quad(f, g, q, bxi, it.z0, it.nz, x);
 }

@@ -24,6 +24,7 @@
 
 #include "zfpx_internal.h"
 #include "zfpx_block.cuh"
+#include "zfpx_smem.cuh"
 
 namespace zfpx {
 namespace {
@@ -32,45 +33,11 @@ using namespace blk;
 
 constexpr int kWarps = 4;
 constexpr int kThreads = 32 * kWarps;
-
-// ----------------------------------------------------------------- stream I/O
-// Writer into this lane's column of a [word][lane] shared-memory tile of
-// RATE 64-bit words (XOR-swizzled so a warp's stores spread over banks).
+// Resident CTAs per SM the 3-D decoder is compiled for: at rate 8 its shared
+// memory leaves room for five, and capping registers to fit them pays; at
+// rate 16 shared memory allows four whatever the registers.
 template <int RATE>
-struct SmemWriter {
-    uint64_t *sm;
-    uint64_t acc;
-    int nb, w, lane;
-    __device__ __forceinline__ void put(uint64_t bits, int len)   // 1 <= len <= 64
-    {
-        acc |= bits << nb;
-        int t = nb + len;
-        if (t >= 64) {
-            sm[w * 32 + (lane ^ w)] = acc;
-            w++;
-            acc = nb ? (bits >> (64 - nb)) : 0ull;
-            t -= 64;
-        }
-        nb = t;
-    }
-    __device__ __forceinline__ void finish()
-    {
-        if (nb > 0) { sm[w * 32 + (lane ^ w)] = acc; w++; }
-        for (; w < RATE; w++) sm[w * 32 + (lane ^ w)] = 0ull;
-    }
-};
-
-// Bit planes of one block, parked in this lane's column of a [plane][lane]
-// shared-memory tile (conflict-free: a warp touches 32 consecutive words).
-struct SmemPlanes {
-    uint64_t *sm;
-    int lane;
-    __device__ __forceinline__ void store(int k, uint64_t X) { sm[k * 32 + lane] = X; }
-    __device__ __forceinline__ uint64_t load(int k) const { return sm[k * 32 + lane]; }
-    // the same tile seen as 64 32-bit words per lane
-    __device__ __forceinline__ uint32_t *words() { return reinterpret_cast<uint32_t *>(sm); }
-    __device__ __forceinline__ int word_index(int i) const { return (i >> 1) * 64 + 2 * lane + (i & 1); }
-};
+constexpr int dec3_min_blocks() { return RATE == 8 ? 5 : 1; }
 
 // ----------------------------------------------------------------- message walk
 __device__ __forceinline__ int find_msg(const MsgDev *msgs, int nmsg, int64_t u)
@@ -109,9 +76,11 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
 {
     __shared__ uint64_t smem[kWarps][RATE * 32];
     __shared__ uint64_t splanes[kWarps][32 * 32];
+    __shared__ uint16_t saux[kWarps][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
     SmemPlanes pl{splanes[wid], lane};
+    SmemAux aux{saux[wid], lane};
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
     int64_t c = gw * g.nunits / W;
@@ -134,26 +103,35 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
             const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
             const float *base = src + src_off;
             float x[64];
-            const bool full = vec && (x0 + 4 <= nx);
+            if (vec && x0 + 4 <= nx) {
+                // the common case: sixteen 16-byte row loads (rows past the
+                // end of the box repeat its last row)
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int64_t zo = (int64_t)min(z0 + k, nz - 1) * g.ss[2];
+                for (int k = 0; k < 4; k++) {
+                    const int64_t zo = (int64_t)min(z0 + k, nz - 1) * g.ss[2];
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    const float *row = base + zo + (int64_t)min(y0 + j, ny - 1) * g.ss[1];
-                    if (full) {
-                        const float4 f = __ldg(reinterpret_cast<const float4 *>(row + x0));
+                    for (int j = 0; j < 4; j++) {
+                        const float4 f = __ldg(reinterpret_cast<const float4 *>(
+                            base + zo + (int64_t)min(y0 + j, ny - 1) * g.ss[1] + x0));
                         x[16 * k + 4 * j] = f.x; x[16 * k + 4 * j + 1] = f.y;
                         x[16 * k + 4 * j + 2] = f.z; x[16 * k + 4 * j + 3] = f.w;
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < 4; i++)
-                            x[16 * k + 4 * j + i] = __ldg(row + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
                     }
                 }
+            } else {
+                // partial in x or unaligned: element loads through a local
+                // array, kept rolled so the hot path's code stays compact
+                float t[64];
+#pragma unroll 1
+                for (int r = 0; r < 64; r++) {
+                    const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                    t[r] = __ldg(base + (int64_t)min(z0 + k, nz - 1) * g.ss[2] +
+                                 (int64_t)min(y0 + j, ny - 1) * g.ss[1] + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
+                }
+#pragma unroll
+                for (int r = 0; r < 64; r++) x[r] = t[r];
             }
             SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
-            encode_block3<RATE>(x, wr, pl);
+            encode_block3<RATE>(x, wr, pl, aux);
         }
         __syncwarp();
         uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * RATE;
@@ -165,17 +143,8 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
     }
 }
 
-// Stream tile of one warp: 32-bit words in a [word][lane] layout (word i of
-// lane l at i * 32 + l), so every lane reads its own column without bank
-// conflicts; three zero rows follow the stream for the 64-bit read window.
-struct StreamTile {
-    const uint32_t *sm;
-    int lane;
-    __device__ __forceinline__ uint32_t get(int i) const { return sm[i * 32 + lane]; }
-};
-
 template <int RATE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, dec3_min_blocks<RATE>())
 decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
     __shared__ uint32_t stile[kWarps][(2 * RATE + 3) * 32];
@@ -219,22 +188,26 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         float v[64];
         decode_block3_tile<RATE>(tile, v, pl);
         float *base = dstf + dst_off;
-        const bool full = vec && (x0 + 4 <= nx);
+        if (vec && x0 + 4 <= nx) {
 #pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (z0 + k >= nz) continue;
+            for (int k = 0; k < 4; k++) {
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                if (y0 + j >= ny) continue;
-                float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1];
-                if (full) {
-                    *reinterpret_cast<float4 *>(row + x0) =
-                        make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < 4; i++)
-                        if (x0 + i < nx) row[(int64_t)(x0 + i) * g.ds[0]] = v[16 * k + 4 * j + i];
+                for (int j = 0; j < 4; j++) {
+                    float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + x0;
+                    if (z0 + k < nz && y0 + j < ny)
+                        *reinterpret_cast<float4 *>(row) = make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1],
+                                                                       v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
                 }
+            }
+        } else {
+            float t[64];
+#pragma unroll
+            for (int r = 0; r < 64; r++) t[r] = v[r];
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) {
+                const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                if (x0 + i < nx && y0 + j < ny && z0 + k < nz)
+                    base[(int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + (int64_t)(x0 + i) * g.ds[0]] = t[r];
             }
         }
     }

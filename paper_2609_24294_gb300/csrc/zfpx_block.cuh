@@ -330,36 +330,30 @@ ZFPX_HD uint64_t decode_plane(Reader &rd, int &n, int &R)
     return X;
 }
 
-// Fast path for a plane that is known to fit: every plane of S = 64
-// coefficients costs at most 127 bits, so with R >= 127 no bit can hit the
-// budget and the per-bit budget checks drop out.  Same bits as code_plane.
-template <int S, class Writer>
-ZFPX_HD void code_plane_fit(Writer &wr, uint64_t X, int &n, int &R)
-{
-    if (n >= S) { wr.put(X, S); R -= S; return; }
-    uint64_t rest = X >> n;
-    if (!rest) { wr.put(X & low_mask(n), n + 1); R -= n + 1; return; }    // verbatim, then G = 0
-    if (n > 0) { wr.put(X & low_mask(n), n); R -= n; }
-    for (;;) {
-        const int p = lowest_set(rest);
-        if (n + p == S - 1) { wr.put(1ull, p + 1); R -= p + 1; n = S; return; }   // last one implied
-        wr.put(1ull | (1ull << (p + 1)), p + 2);
-        R -= p + 2;
-        n += p + 1;
-        rest >>= p + 1;
-        if (!rest) { wr.put(0ull, 1); R -= 1; return; }                  // n < S here
-    }
-}
-
 // ----------------------------------------------------------------- 3-D block
-// Encodes 64 values (x[i + 4j + 16k]) into exactly 64 RATE bits through wr;
-// wr.finish() flushes and zero-fills.  The 32 bit planes are parked in `pl`
-// (store(k, X) / load(k)) so the coding loop over planes stays rolled and
-// the kernel's code stays small.
-template <int RATE, class Writer, class Planes>
-ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
+// Encodes 64 values (x[i + 4j + 16k]) into exactly 64 RATE bits.
+//
+// Two passes over the bit planes, so that lanes coding different blocks do
+// not diverge per plane.  Pass 1 walks the planes with closed forms: plane k
+// with n significant coefficients costs n verbatim bits, a group bit and, if
+// its bits n..63 hold c ones with the highest at h, (h - n + 1) value bits
+// and c group bits after them (one value bit and one group bit less when
+// h = 63, whose one is implied).  It writes the verbatim bits and the first
+// group bit and leaves zeros for the rest.  Pass 2 visits each newly
+// significant coefficient once: the t-th one (t = 0, 1, ...) of a plane, at
+// coefficient p, sits at (plane start + n + 1) + (p - n) + t, that is plane
+// start + 1 + p + t, with its group bit right after; pass 2 ORs those bits
+// into the stream.
+//
+// Writer: put(bits, len) for 1 <= len <= 64, zeros(len), finish() (flush and
+// zero-fill to RATE words), orw(i, v) (OR v into 64-bit word i after finish).
+// Planes: store(k, X) / load(k), 32 slots.  Aux: set(e, v) / get(e), 32
+// slots of at least 16 bits.
+template <int RATE, class Writer, class Planes, class Aux>
+ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl, Aux &aux)
 {
     constexpr int kSeq[64] = ZFPX_SEQ3;
+    constexpr int END = 64 * RATE;
     uint32_t amax = 0;
 #pragma unroll
     for (int i = 0; i < 64; i++) {
@@ -385,14 +379,74 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
 #pragma unroll
     for (int k = 0; k < 32; k++) pl.store(k, ((uint64_t)hi[k] << 32) | lo[k]);
     wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    int n = 0, R = 64 * RATE - 9;
+    // pass 1: plane costs, verbatim bits, first group bits
+    int n = 0, pos = 9, ne = 0;
 #pragma unroll 1
-    for (int k = 31; k >= 0 && R > 0; k--) {
+    for (int k = 31; k >= 0 && pos < END; k--) {
         const uint64_t X = pl.load(k);
-        if (R >= 127) code_plane_fit<64>(wr, X, n, R);
-        else code_plane<64>(wr, X, n, R);
+        const int room = END - pos;
+        if (n >= 64) {                                           // every coefficient significant
+            if (room < 64) wr.put(X & low_mask(room), room);
+            else wr.put(X, 64);
+            pos += 64;
+            continue;
+        }
+        const uint64_t lm = low_mask(n);
+        const uint64_t Y = X & ~lm;                              // candidates for significance
+        uint64_t bits = (X & lm) | (Y ? lm + 1ull : 0ull);       // verbatim bits, group bit
+        int len = n + 1, L = n + 1;
+        int h = 0;
+        if (Y) {
+            h = highest_set64(Y);
+            const int c = popc64(Y);
+            L = h < 63 ? h + 2 + c : h + c;
+        }
+        if (room < len) { bits &= low_mask(room); len = room; }
+        wr.put(bits, len);
+        const int more = (L < room ? L : room) - len;
+        if (more > 0) wr.zeros(more);
+        if (Y) {
+            pl.store(31 - ne, Y);           // slot 31 - ne >= k: already read
+            aux.set(ne, (uint32_t)(pos + 1));
+            ne++;
+            n = h + 1;
+        }
+        pos += L;
     }
     wr.finish();
+    // pass 2: the bits of each newly significant coefficient, in stream order
+    uint64_t rest = 0, cacc = 0;
+    int ap = 0, t = 0, e = 0, cw = 0;
+#pragma unroll 1
+    for (;;) {
+        if (!rest) {
+            if (e >= ne) break;
+            rest = pl.load(31 - e);
+            ap = (int)aux.get(e);
+            e++;
+            t = 0;
+        }
+        const int p = lowest_set(rest);
+        rest &= rest - 1;
+        const int A = ap + p + t;
+        t++;
+        if (A >= END) break;                                     // positions only grow
+        uint64_t b = p != 63 ? 1ull : 0ull;                      // coefficient 63's one is implied
+        if (rest && A + 1 < END) b |= 2ull;                      // group bit: more ones follow
+        const int w = A >> 6, s = A & 63;
+        if (w != cw) {
+            if (cacc) wr.orw(cw, cacc);
+            cw = w;
+            cacc = 0;
+        }
+        cacc |= b << s;
+        if (s == 63 && (b & 2ull)) {
+            wr.orw(cw, cacc);
+            cw = w + 1;
+            cacc = 1ull;
+        }
+    }
+    if (cacc) wr.orw(cw, cacc);
 }
 
 // ----------------------------------------------------------------- 3-D decoder over a stream tile

@@ -121,6 +121,23 @@ def test_special_values(z):
             same_bits(host(dec), rdec)
 
 
+def test_graded_spectrum_blocks(z):
+    # many planes with newly significant coefficients (the coder's per-plane
+    # bookkeeping beyond its first ten such planes), 3 warps of blocks + tail
+    x = fieldgen.graded_blocks(100, 9)
+    n = (x.shape[2], 4, 4)
+    for rate in (8, 16):
+        out = torch.zeros(z.zfpx_stream_bytes(3, rate, n), dtype=torch.uint8, device="cuda")
+        z.zfpx_encode(3, rate, dev(x), out)
+        ref = oc.encode_array(3, rate, x)
+        assert host(out).tobytes() == ref.tobytes()
+        dec = torch.empty_like(dev(x))
+        z.zfpx_decode(3, rate, out, dec)
+        rdec = np.empty_like(x)
+        oc.decode_array(3, rate, ref, rdec)
+        same_bits(host(dec), rdec)
+
+
 def test_random_streams_decode_like_oracle(z):
     # the decoder is defined on any byte stream
     rng = np.random.default_rng(11)
