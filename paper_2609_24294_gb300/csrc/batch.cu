@@ -157,8 +157,7 @@ __device__ __forceinline__ void scatter_quad(const FieldDevB &f, const GridDev &
 
 template <int RATE>
 __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                           int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint16_t *wax,
-                                           uint8_t *out)
+                                           int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint8_t *out)
 {
     if (lane < nact) {
         const int64_t bg = b0 + lane + f.b0;
@@ -168,8 +167,7 @@ __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g,
         gather_quad(f, g, q, bxi, it.z0, it.nz, x);
         SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
         SmemPlanes pl{wpl, lane};
-        SmemAux aux{wax, lane};
-        encode_block3<RATE>(x, wr, pl, aux);
+        encode_block3<RATE>(x, wr, pl);
     }
     __syncwarp();
     uint64_t *dst = reinterpret_cast<uint64_t *>(out + it.out_off) + b0 * RATE;
@@ -208,9 +206,8 @@ template <int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
 batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
 {
-    __shared__ uint64_t sout[WARPS][16 * 32];
+    __shared__ uint64_t sout[WARPS][(16 + 2) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
-    __shared__ uint16_t saux[WARPS][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * WARPS;
     const int64_t gw = (int64_t)blockIdx.x * WARPS + wid;
@@ -226,8 +223,8 @@ batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
         const int64_t b0 = (c - it.unit0) * 32;
         const int nact = (int)min((int64_t)32, it.nblocks - b0);
         if (f.dims == 3) {
-            if (f.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], saux[wid], out);
-            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], saux[wid], out);
+            if (f.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
+            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
         } else {
             if (f.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
             else enc1_chunk<16>(f, bg.grid, it, b0, nact, lane, out);

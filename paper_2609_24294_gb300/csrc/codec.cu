@@ -74,13 +74,11 @@ template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
 {
-    __shared__ uint64_t smem[kWarps][RATE * 32];
+    __shared__ uint64_t smem[kWarps][(RATE + 2) * 32];
     __shared__ uint64_t splanes[kWarps][32 * 32];
-    __shared__ uint16_t saux[kWarps][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
     SmemPlanes pl{splanes[wid], lane};
-    SmemAux aux{saux[wid], lane};
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
     int64_t c = gw * g.nunits / W;
@@ -131,7 +129,7 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
                 for (int r = 0; r < 64; r++) x[r] = t[r];
             }
             SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
-            encode_block3<RATE>(x, wr, pl, aux);
+            encode_block3<RATE>(x, wr, pl);
         }
         __syncwarp();
         uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * RATE;

@@ -345,12 +345,12 @@ ZFPX_HD uint64_t decode_plane(Reader &rd, int &n, int &R)
 // start + 1 + p + t, with its group bit right after; pass 2 ORs those bits
 // into the stream.
 //
-// Writer: put(bits, len) for 1 <= len <= 64, zeros(len), finish() (flush and
-// zero-fill to RATE words), orw(i, v) (OR v into 64-bit word i after finish).
-// Planes: store(k, X) / load(k), 32 slots.  Aux: set(e, v) / get(e), 32
-// slots of at least 16 bits.
-template <int RATE, class Writer, class Planes, class Aux>
-ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl, Aux &aux)
+// Writer: RATE + 2 64-bit words, the last two slack that the caller drops;
+// put(bits, len) for 1 <= len <= 64, zeros(len), finish() (flush and
+// zero-fill to RATE words), orw(i, v) (OR v into word i after finish).
+// Planes: store(k, X) / load(k), store_half(k, h, w), 32 slots.
+template <int RATE, class Writer, class Planes>
+ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
 {
     constexpr int kSeq[64] = ZFPX_SEQ3;
     constexpr int END = 64 * RATE;
@@ -374,56 +374,67 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl, Aux &au
         lo[t] = to_negabinary(q[kSeq[t]]);
         hi[t] = to_negabinary(q[kSeq[32 + t]]);
     }
-    transpose32(lo);
-    transpose32(hi);
+    // one transpose body for both halves keeps the kernel's code compact
+#pragma unroll 1
+    for (int half = 0; half < 2; half++) {
+        if (half) {
 #pragma unroll
-    for (int k = 0; k < 32; k++) pl.store(k, ((uint64_t)hi[k] << 32) | lo[k]);
+            for (int t = 0; t < 32; t++) lo[t] = hi[t];
+        }
+        transpose32(lo);
+#pragma unroll
+        for (int k = 0; k < 32; k++) pl.store_half(k, half, lo[k]);
+    }
     wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    // pass 1: plane costs, verbatim bits, first group bits
-    int n = 0, pos = 9, ne = 0;
+    // pass 1: plane costs, verbatim bits, first group bits.  The last plane
+    // may run past the budget: its excess lands in the writer's two slack
+    // words, so no bit count is clipped here.  A plane with new ones keeps
+    // them in its own slot (already read) and is flagged in evm.
+    int n = 0, pos = 9;
+    uint32_t evm = 0;
+    uint64_t lm = 0;                                             // low_mask(n)
 #pragma unroll 1
     for (int k = 31; k >= 0 && pos < END; k--) {
         const uint64_t X = pl.load(k);
-        const int room = END - pos;
         if (n >= 64) {                                           // every coefficient significant
-            if (room < 64) wr.put(X & low_mask(room), room);
-            else wr.put(X, 64);
+            wr.put(X, 64);
             pos += 64;
             continue;
         }
-        const uint64_t lm = low_mask(n);
         const uint64_t Y = X & ~lm;                              // candidates for significance
-        uint64_t bits = (X & lm) | (Y ? lm + 1ull : 0ull);       // verbatim bits, group bit
-        int len = n + 1, L = n + 1;
-        int h = 0;
+        wr.put((X & lm) | (Y ? lm + 1ull : 0ull), n + 1);        // verbatim bits, group bit
+        int L = n + 1;
         if (Y) {
-            h = highest_set64(Y);
-            const int c = popc64(Y);
-            L = h < 63 ? h + 2 + c : h + c;
-        }
-        if (room < len) { bits &= low_mask(room); len = room; }
-        wr.put(bits, len);
-        const int more = (L < room ? L : room) - len;
-        if (more > 0) wr.zeros(more);
-        if (Y) {
-            pl.store(31 - ne, Y);           // slot 31 - ne >= k: already read
-            aux.set(ne, (uint32_t)(pos + 1));
-            ne++;
+            const int h = highest_set64(Y);
+            L = h < 63 ? h + 2 + popc64(Y) : h + popc64(Y);
+            wr.zeros(L - n - 1);
+            pl.store(k, Y);
+            evm |= 1u << k;
             n = h + 1;
+            lm = low_mask(n);
         }
         pos += L;
     }
     wr.finish();
-    // pass 2: the bits of each newly significant coefficient, in stream order
+    // pass 2: the bits of each newly significant coefficient, in stream
+    // order.  A flagged plane's start follows from the previous one's: that
+    // plane's cost, then one bit more than the significant count for each
+    // plane without new ones in between.
     uint64_t rest = 0, cacc = 0;
-    int ap = 0, t = 0, e = 0, cw = 0;
+    int ap = 0, t = 0, cw = 0, kp = 32, endp = 9, np = 0;
 #pragma unroll 1
     for (;;) {
         if (!rest) {
-            if (e >= ne) break;
-            rest = pl.load(31 - e);
-            ap = (int)aux.get(e);
-            e++;
+            if (!evm) break;
+            const int k = highest_set32(evm);
+            evm &= ~(1u << k);
+            rest = pl.load(k);
+            const int start = endp + (kp - 1 - k) * (np + 1);
+            ap = start + 1;
+            const int h = highest_set64(rest), c = popc64(rest);
+            endp = start + (h < 63 ? h + 2 + c : h + c);
+            np = h + 1;
+            kp = k;
             t = 0;
         }
         const int p = lowest_set(rest);
@@ -431,8 +442,9 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl, Aux &au
         const int A = ap + p + t;
         t++;
         if (A >= END) break;                                     // positions only grow
-        uint64_t b = p != 63 ? 1ull : 0ull;                      // coefficient 63's one is implied
-        if (rest && A + 1 < END) b |= 2ull;                      // group bit: more ones follow
+        // coefficient 63's one is implied; the group bit (more ones follow)
+        // may fall at END, in a slack word
+        const uint64_t b = (p != 63 ? 1ull : 0ull) | (rest ? 2ull : 0ull);
         const int w = A >> 6, s = A & 63;
         if (w != cw) {
             if (cacc) wr.orw(cw, cacc);
@@ -527,9 +539,8 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
     uint32_t lo[32], hi[32];
 #pragma unroll
     for (int kk = 0; kk < 32; kk++) {
-        const uint64_t P = pl.load(kk);
-        lo[kk] = (uint32_t)P;
-        hi[kk] = (uint32_t)(P >> 32);
+        lo[kk] = pl.load_half(kk, 0);
+        hi[kk] = pl.load_half(kk, 1);
     }
     transpose32(lo);
     transpose32(hi);
@@ -545,13 +556,14 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
 #pragma unroll
         for (int i = 0; i < 64; i++) x[i] = dequantize_fast(q[i], sc);
     } else {
-        uint32_t *wd = pl.words();
+        // tiny exponents (rare): a rolled loop over a local copy
+        int32_t t[64];
 #pragma unroll
-        for (int i = 0; i < 64; i++) wd[pl.word_index(i)] = (uint32_t)q[i];
+        for (int i = 0; i < 64; i++) t[i] = q[i];
 #pragma unroll 1
-        for (int i = 0; i < 64; i++) wd[pl.word_index(i)] = f2u(dequantize_small((int32_t)wd[pl.word_index(i)], e));
+        for (int i = 0; i < 64; i++) t[i] = (int32_t)f2u(dequantize_small(t[i], e));
 #pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = u2f(wd[pl.word_index(i)]);
+        for (int i = 0; i < 64; i++) x[i] = u2f((uint32_t)t[i]);
     }
 }
 

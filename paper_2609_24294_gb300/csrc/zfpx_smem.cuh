@@ -7,8 +7,8 @@
 
 namespace zfpx {
 
-// Writer into this lane's column of a [word][lane] tile of RATE 64-bit words,
-// XOR-swizzled (word w of lane l at w * 32 + (l ^ w)) so that both the
+// Writer into this lane's column of a [word][lane] tile of RATE + 2 64-bit
+// words (RATE stream words, two slack words past the budget), XOR-swizzled (word w of lane l at w * 32 + (l ^ w)) so that both the
 // per-lane writes and the warp's coalesced copy-out spread over the banks.
 // put(bits, len): 1 <= len <= 64, bits < 2^len; zeros(len): len >= 0;
 // finish(): flush and zero-fill to RATE words; orw(i, v): OR v into word i
@@ -57,17 +57,15 @@ struct SmemPlanes {
     int lane;
     __device__ __forceinline__ void store(int k, uint64_t X) { sm[k * 32 + lane] = X; }
     __device__ __forceinline__ uint64_t load(int k) const { return sm[k * 32 + lane]; }
-    // the same tile seen as 64 32-bit words per lane
-    __device__ __forceinline__ uint32_t *words() { return reinterpret_cast<uint32_t *>(sm); }
-    __device__ __forceinline__ int word_index(int i) const { return (i >> 1) * 64 + 2 * lane + (i & 1); }
-};
-
-// 32 16-bit slots per lane ([slot][lane]).
-struct SmemAux {
-    uint16_t *sm;
-    int lane;
-    __device__ __forceinline__ void set(int e, uint32_t v) { sm[e * 32 + lane] = (uint16_t)v; }
-    __device__ __forceinline__ uint32_t get(int e) const { return sm[e * 32 + lane]; }
+    // the low (half 0) or high (half 1) 32 bits of plane k
+    __device__ __forceinline__ void store_half(int k, int half, uint32_t v)
+    {
+        reinterpret_cast<uint32_t *>(sm)[2 * (k * 32 + lane) + half] = v;
+    }
+    __device__ __forceinline__ uint32_t load_half(int k, int half) const
+    {
+        return reinterpret_cast<const uint32_t *>(sm)[2 * (k * 32 + lane) + half];
+    }
 };
 
 // Stream tile of one warp: 32-bit words in a [word][lane] layout (word i of
