@@ -462,10 +462,7 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
 }
 
 // ----------------------------------------------------------------- 3-D decoder over a stream tile
-// Decoder: one loop over "steps" -- the start of a plane (verbatim bits and
-// a group bit) or one newly significant coefficient (zeros, its 1, the next
-// group bit) -- so lanes that are in different planes still run the same
-// iteration.  Reads are 64-bit windows funnel-shifted out of three tile words.
+// Reads are 64-bit windows funnel-shifted out of three tile words.
 template <class Tile>
 ZFPX_HD uint64_t tile_peek(const Tile &t, int pos)
 {
@@ -480,6 +477,30 @@ ZFPX_HD uint64_t tile_peek(const Tile &t, int pos)
     return ((uint64_t)hi << 32) | lo;
 }
 
+// The group-tested part of a plane, read from the window W that starts
+// right after its first (set) group bit.  The part is a run of tokens: "0"
+// (a coefficient that stays insignificant) or "1g" (a newly significant one
+// and the group bit after it); it ends at the first g = 0, or without a
+// closing bit where coefficient 63 is reached, whose one is implied.  Inside
+// the part every run of ones starts on a value bit and alternates value,
+// group, value, ...; a run of odd length ends on a value bit, and the 0
+// after it closes the part.  Returns the value ones of W read that way
+// (exact below the part's end) and in `term` the closing-0 candidates.
+ZFPX_HD uint64_t group_values(uint64_t W, uint64_t &term)
+{
+    constexpr uint64_t kEven = 0x5555555555555555ull;
+    const uint64_t starts = W & ~(W << 1);
+    const uint64_t even_runs = W & ~(W + (starts & kEven));     // the carry clears runs that start even
+    const uint64_t val = (even_runs & kEven) | (W & ~even_runs & ~kEven);
+    const uint64_t ends = W & ~(W >> 1) & ~(1ull << 63);         // a run at bit 63 may go on
+    term = (ends & val) << 1;
+    return val;
+}
+
+// Decodes one block from this lane's stream tile: plane by plane, each
+// plane's group-tested part in one step when it closes inside a 64-bit
+// window, below coefficient 63 and inside the budget; otherwise (rare) one
+// newly significant coefficient per step.
 template <int RATE, class Tile, class Planes>
 ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
 {
@@ -494,48 +515,89 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
     const int e = (int)((head >> 1) & 0xffu);
 #pragma unroll
     for (int k = 0; k < 32; k++) pl.store(k, 0ull);
-    int pos = 9, n = 0, k = 31;
-    bool start = true;
-    uint64_t X = 0;
+    int pos = 9, n = 0;
+    uint64_t lm = 0;                                             // low_mask(n)
 #pragma unroll 1
-    while (k >= 0 && (pos < END || (!start && n == 63))) {
+    for (int k = 31; k >= 0 && pos < END; k--) {
         const int rem = END - pos;
         const uint64_t w = tile_peek(tile, pos);
-        if (start) {
-            if (n >= 64) {
-                const int take = rem < 64 ? rem : 64;
-                pl.store(k, w & low_mask(take));
-                pos += take;
-                k--;
+        if (n >= 64) {                                           // verbatim plane
+            pl.store(k, rem < 64 ? w & low_mask(rem) : w);
+            pos += 64;
+            continue;
+        }
+        uint64_t X = w & lm;
+        if (rem <= n) { pl.store(k, w & low_mask(rem)); break; }     // budget ends in the verbatim bits
+        pos += n + 1;
+        if (!((w >> n) & 1ull)) { pl.store(k, X); continue; }       // group empty
+        {
+            // The whole part from one window.  The tile is zero past the
+            // budget, so no one and no closing 0 can be read there: a part
+            // cut by the budget shows as one that runs on, and only the
+            // implied one needs the check that its zeros fit (B bits left).
+            uint64_t term;
+            uint64_t V = group_values(tile_peek(tile, pos), term);
+            const int T = term ? lowest_set(term) : 64;          // offset of the closing 0
+            const int lim = 62 - n;                              // offset - rank of coefficient 62
+            const int B = END - pos;
+            int t = 0;
+            uint64_t nw = 0;
+            bool over = false;                                   // a one past coefficient 62
+            V &= low_mask(T);
+            while (V) {                                          // the t-th one, at offset p, is coefficient n + p - t
+                const int p = lowest_set(V);
+                if (p - t > lim) { over = true; break; }
+                nw |= 1ull << (p - t);
+                V &= V - 1;
+                t++;
+            }
+            X |= nw << n;
+            const int E = 63 - n + t;                            // end of the part if it ends at the implied one
+            if (!over && term) {                                 // closed by a 0 below coefficient 63
+                pl.store(k, X);
+                n += T - t + 1;
+                lm = low_mask(n);
+                pos += T + 1;
                 continue;
             }
-            X = w & low_mask(rem < n ? rem : n);
-            if (rem <= n) { pl.store(k, X); break; }             // budget ends in the verbatim bits
-            pos += n + 1;
-            if ((w >> n) & 1ull) start = false;
-            else { pl.store(k, X); k--; }
-        } else {
+            if (E <= 64) {                                       // ends at the implied one
+                if (E > B) { pl.store(k, X); break; }
+                X |= 1ull << 63;
+                pl.store(k, X);
+                pos += E;
+                n = 64;
+                lm = ~0ull;
+                continue;
+            }
+            // else: the part runs past the window; X's low bits are reread below
+            X = w & lm;
+        }
+        // one coefficient per step, with the budget and the implied last one
+        bool cut = false;
+#pragma unroll 1
+        for (;;) {
+            const int r = END - pos;
+            const uint64_t v = tile_peek(tile, pos);
             const int lim = 63 - n;
-            const int tz = w ? lowest_set(w) : 64;
+            const int tz = v ? lowest_set(v) : 64;
             if (tz >= lim) {                                     // only the implied one is left
-                if (rem < lim) { pl.store(k, X); break; }
+                if (r < lim) { cut = true; break; }
                 pos += lim;
                 X |= 1ull << 63;
                 n = 64;
-                pl.store(k, X);
-                k--;
-                start = true;
-            } else {
-                if (rem < tz + 1) { pl.store(k, X); break; }
-                X |= 1ull << (n + tz);
-                n += tz + 1;
-                if (rem == tz + 1) { pl.store(k, X); break; }    // budget ends before the group bit
-                pos += tz + 2;
-                if (!((w >> (tz + 1)) & 1ull)) { pl.store(k, X); k--; start = true; }
+                break;
             }
+            if (r < tz + 1) { cut = true; break; }
+            X |= 1ull << (n + tz);
+            n += tz + 1;
+            if (r == tz + 1) { cut = true; break; }              // budget ends before the group bit
+            pos += tz + 2;
+            if (!((v >> (tz + 1)) & 1ull)) break;                // group empty: plane done
         }
+        pl.store(k, X);
+        if (cut) break;
+        lm = low_mask(n);
     }
-    if (!start && k >= 0) pl.store(k, X);                        // budget ended inside a plane
     uint32_t lo[32], hi[32];
 #pragma unroll
     for (int kk = 0; kk < 32; kk++) {

@@ -138,6 +138,36 @@ def test_graded_spectrum_blocks(z):
         same_bits(host(dec), rdec)
 
 
+def _stream_budget_on_group_bit(rate):
+    """A 3-D stream whose budget ends exactly on a set group bit while 63
+    coefficients are significant: only coefficient 63 is left, and its one
+    is implied without another bit.  Built plane by plane: 5 empty planes,
+    one making coefficients 0..49 significant, one making 50..62
+    significant, planes of 63 verbatim bits and an empty group, and a last
+    plane whose group bit is the stream's final bit."""
+    rng = np.random.default_rng(rate)
+    bits = [1] + [int(b) for b in np.binary_repr(130, 8)[::-1]]          # block flag, exponent
+    bits += [0] * 5
+    bits += [1] + [1, 1] * 49 + [1, 0]                                    # coefficients 0..49
+    bits += list(rng.integers(0, 2, 50)) + [1] + [1, 1] * 12 + [1, 0]     # 50..62
+    m = (64 * rate - 64 - len(bits)) // 64
+    for _ in range(m):
+        bits += list(rng.integers(0, 2, 63)) + [0]
+    bits += list(rng.integers(0, 2, 63)) + [1]
+    assert len(bits) == 64 * rate
+    return np.packbits(np.array(bits, dtype=np.uint8), bitorder="little")
+
+
+def test_budget_ends_on_group_bit_with_implied_one(z):
+    for rate in (8, 16):
+        s = _stream_budget_on_group_bit(rate)
+        dec = torch.empty((4, 4, 4), device="cuda")
+        z.zfpx_decode(3, rate, dev(s), dec)
+        rdec = np.empty((4, 4, 4), dtype=np.float32)
+        oc.decode_array(3, rate, s, rdec)
+        same_bits(host(dec), rdec)
+
+
 def test_random_streams_decode_like_oracle(z):
     # the decoder is defined on any byte stream
     rng = np.random.default_rng(11)
