@@ -241,39 +241,77 @@ ZFPX_HD int32_t from_negabinary(uint32_t u) { return (int32_t)((u ^ 0xAAAAAAAAu)
 // In-place transpose of a 32x32 bit matrix: afterwards bit i of w[k] is
 // what bit k of w[i] was.  Off-diagonal blocks are swapped at sizes 16, 8,
 // 4, 2, 1; the 16- and 8-bit swaps are single byte permutes.
-ZFPX_HD void transpose32(uint32_t (&w)[32])
+//
+// The five stages swap one bit of the row index with the same bit of the
+// column index each, so they commute and may run in any order; a stage of
+// size S < L keeps each L-aligned group of words to itself.
+// tstage<S, B, E>: the stage of size S on the pairs (i, i + S), B <= i < E.
+template <int S, int B, int E>
+ZFPX_HD void tstage(uint32_t (&w)[32])
 {
 #pragma unroll
-    for (int i = 0; i < 16; i++) {
-        const uint32_t a = w[i], b = w[i + 16];
-        w[i] = byte_perm(a, b, 0x5410);
-        w[i + 16] = byte_perm(a, b, 0x7632);
+    for (int i = B; i < E; i++) {
+        if (i & S) continue;
+        const uint32_t a = w[i], b = w[i + S];
+        if (S == 16) {
+            w[i] = byte_perm(a, b, 0x5410);
+            w[i + S] = byte_perm(a, b, 0x7632);
+        } else if (S == 8) {
+            w[i] = byte_perm(a, b, 0x6240);
+            w[i + S] = byte_perm(a, b, 0x7351);
+        } else {
+            constexpr uint32_t m = S == 4 ? 0x0F0F0F0Fu : S == 2 ? 0x33333333u : 0x55555555u;
+            const uint32_t t = ((a >> S) ^ b) & m;
+            w[i + S] = b ^ t;
+            w[i] = a ^ (t << S);
+        }
     }
+}
+
+ZFPX_HD void transpose32(uint32_t (&w)[32])
+{
+    tstage<16, 0, 32>(w);
+    tstage<8, 0, 32>(w);
+    tstage<4, 0, 32>(w);
+    tstage<2, 0, 32>(w);
+    tstage<1, 0, 32>(w);
+}
+
+// The transpose in two parts, for coding planes from the top: part 1
+// finishes output words L..31 (L = 8 or 16) and leaves words 0..L-1 halfway;
+// part 2 finishes those.
+template <int L>
+ZFPX_HD void transpose32_part1(uint32_t (&w)[32])
+{
+    tstage<16, 0, 32>(w);
+    if (L == 8) tstage<8, 0, 32>(w);
+    else tstage<8, 16, 32>(w);
+    tstage<4, L, 32>(w);
+    tstage<2, L, 32>(w);
+    tstage<1, L, 32>(w);
+}
+template <int L>
+ZFPX_HD void transpose32_part2(uint32_t (&w)[32])
+{
+    if (L == 16) tstage<8, 0, 16>(w);
+    tstage<4, 0, L>(w);
+    tstage<2, 0, L>(w);
+    tstage<1, 0, L>(w);
+}
+
+// The transpose of a matrix whose words 0..L-1 are zero (L = 8 or 16): the
+// stages smaller than L only touch words L..31.
+template <int L>
+ZFPX_HD void transpose32_zero_low(uint32_t (&w)[32])
+{
 #pragma unroll
-    for (int i = 0; i < 32; i++) {
-        if (i & 8) continue;
-        const uint32_t a = w[i], b = w[i + 8];
-        w[i] = byte_perm(a, b, 0x6240);
-        w[i + 8] = byte_perm(a, b, 0x7351);
-    }
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        if (i & 4) continue;
-        const uint32_t t = ((w[i] >> 4) ^ w[i + 4]) & 0x0F0F0F0Fu;
-        w[i + 4] ^= t; w[i] ^= t << 4;
-    }
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        if (i & 2) continue;
-        const uint32_t t = ((w[i] >> 2) ^ w[i + 2]) & 0x33333333u;
-        w[i + 2] ^= t; w[i] ^= t << 2;
-    }
-#pragma unroll
-    for (int i = 0; i < 32; i++) {
-        if (i & 1) continue;
-        const uint32_t t = ((w[i] >> 1) ^ w[i + 1]) & 0x55555555u;
-        w[i + 1] ^= t; w[i] ^= t << 1;
-    }
+    for (int i = 0; i < L; i++) w[i] = 0u;
+    if (L == 16) tstage<8, 16, 32>(w);
+    tstage<4, L, 32>(w);
+    tstage<2, L, 32>(w);
+    tstage<1, L, 32>(w);
+    if (L == 8) tstage<8, 0, 32>(w);
+    tstage<16, 0, 32>(w);
 }
 
 // ----------------------------------------------------------------- coder
@@ -374,14 +412,18 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
         lo[t] = to_negabinary(q[kSeq[t]]);
         hi[t] = to_negabinary(q[kSeq[32 + t]]);
     }
-    // one transpose body for both halves keeps the kernel's code compact
+    // One transpose body for both halves keeps the kernel's code compact.
+    // The budget rarely reaches below plane 16 at rate 8 (plane 8 at rate
+    // 16): the planes above are finished here, and the words below wait
+    // half-transposed in their slots until the coder first needs them.
+    constexpr int kLow = RATE == 8 ? 16 : 8;
 #pragma unroll 1
     for (int half = 0; half < 2; half++) {
         if (half) {
 #pragma unroll
             for (int t = 0; t < 32; t++) lo[t] = hi[t];
         }
-        transpose32(lo);
+        transpose32_part1<kLow>(lo);
 #pragma unroll
         for (int k = 0; k < 32; k++) pl.store_half(k, half, lo[k]);
     }
@@ -395,6 +437,18 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
     uint64_t lm = 0;                                             // low_mask(n)
 #pragma unroll 1
     for (int k = 31; k >= 0 && pos < END; k--) {
+        if (k == kLow - 1) {                                     // finish planes 0..kLow-1
+            uint32_t a[32], b[32];
+#pragma unroll
+            for (int i = 0; i < kLow; i++) {
+                a[i] = pl.load_half(i, 0);
+                b[i] = pl.load_half(i, 1);
+            }
+            transpose32_part2<kLow>(a);
+            transpose32_part2<kLow>(b);
+#pragma unroll
+            for (int i = 0; i < kLow; i++) pl.store(i, ((uint64_t)b[i] << 32) | a[i]);
+        }
         const uint64_t X = pl.load(k);
         if (n >= 64) {                                           // every coefficient significant
             wr.put(X, 64);
@@ -513,12 +567,11 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
         return;
     }
     const int e = (int)((head >> 1) & 0xffu);
-#pragma unroll
-    for (int k = 0; k < 32; k++) pl.store(k, 0ull);
-    int pos = 9, n = 0;
+    int pos = 9, n = 0, kmin = 32;                               // planes below kmin stay zero
     uint64_t lm = 0;                                             // low_mask(n)
 #pragma unroll 1
     for (int k = 31; k >= 0 && pos < END; k--) {
+        kmin = k;                                                // every pass stores plane k
         const int rem = END - pos;
         const uint64_t w = tile_peek(tile, pos);
         if (n >= 64) {                                           // verbatim plane
@@ -599,13 +652,31 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
         lm = low_mask(n);
     }
     uint32_t lo[32], hi[32];
+    // Planes below kmin are zero; when that holds for planes 0..kLow-1 in
+    // every lane of the warp, the stages smaller than kLow skip them.
+    constexpr int kLow = RATE == 8 ? 16 : 8;
+#ifdef __CUDA_ARCH__
+    const bool low_zero = __all_sync(__activemask(), kmin >= kLow);
+#else
+    const bool low_zero = kmin >= kLow;
+#endif
+    if (low_zero) {
 #pragma unroll
-    for (int kk = 0; kk < 32; kk++) {
-        lo[kk] = pl.load_half(kk, 0);
-        hi[kk] = pl.load_half(kk, 1);
+        for (int kk = kLow; kk < 32; kk++) {
+            lo[kk] = kk >= kmin ? pl.load_half(kk, 0) : 0u;
+            hi[kk] = kk >= kmin ? pl.load_half(kk, 1) : 0u;
+        }
+        transpose32_zero_low<kLow>(lo);
+        transpose32_zero_low<kLow>(hi);
+    } else {
+#pragma unroll
+        for (int kk = 0; kk < 32; kk++) {
+            lo[kk] = kk >= kmin ? pl.load_half(kk, 0) : 0u;
+            hi[kk] = kk >= kmin ? pl.load_half(kk, 1) : 0u;
+        }
+        transpose32(lo);
+        transpose32(hi);
     }
-    transpose32(lo);
-    transpose32(hi);
     int32_t q[64];
 #pragma unroll
     for (int t = 0; t < 32; t++) {
