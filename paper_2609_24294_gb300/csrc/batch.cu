@@ -61,13 +61,70 @@ struct GridDev {
     int32_t nrows, nq;
 };
 
+// Items of one (dims, rate) kind: units [u0, u0 + n).  cum1 is the share of
+// all work up to and including this group, which picks the SMs for which it
+// is the home group.
+struct GroupDev {
+    int64_t u0, n;
+    int32_t dims, rate;
+    float cum1;
+    int32_t pad;
+};
+constexpr int kMaxGroups = 4;
+
 struct BatchGeom {
     const ItemDevB *items;
     const FieldDevB *fields;
     GridDev grid;
     int nitems;
     int64_t nunits;
+    GroupDev groups[kMaxGroups];
+    int ngroups;
+    uint32_t *ctr;        // ngroups work counters, zero at launch
 };
+
+__device__ __forceinline__ int item_of_unit(const ItemDevB *items, int n, int64_t u)
+{
+    int lo = 0, hi = n - 1;   // last item with unit0 <= u
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(&items[mid].unit0) <= u) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Work distribution of the batch kernels: each (dims, rate) group is a queue
+// of 32-block units claimed one at a time by whole warps.  A CTA starts on
+// its home group -- the SMs are split between groups in proportion to their
+// work, so an SM mostly runs one kind's code and keeps it in its instruction
+// cache -- and then helps the other groups until every queue is empty.
+template <class Fn>
+__device__ __forceinline__ void for_each_unit(const BatchGeom &bg, int lane, Fn &&fn)
+{
+    uint32_t smid, nsmid;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const float x = ((float)smid + 0.5f) / (float)nsmid;
+    int home = 0;
+    while (home + 1 < bg.ngroups && x >= bg.groups[home].cum1) home++;
+    for (int t = 0; t < bg.ngroups; t++) {
+        const int gi = (home + t) % bg.ngroups;
+        const GroupDev G = bg.groups[gi];
+        uint32_t *ctr = bg.ctr + gi;
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(ctr, 1u);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        while ((int64_t)u < G.n) {
+            uint32_t next = 0;                                   // claimed ahead: its latency hides behind fn
+            if (lane == 0) next = atomicAdd(ctr, 1u);
+            next = __shfl_sync(0xffffffffu, next, 0);
+            const int64_t c = G.u0 + u;
+            const int ii = item_of_unit(bg.items, bg.nitems, c);
+            fn(G, c, ii);
+            u = next;
+        }
+    }
+}
 
 __device__ __forceinline__ int upper_index(const int64_t *pre, int n, int64_t b)
 {
@@ -78,30 +135,6 @@ __device__ __forceinline__ int upper_index(const int64_t *pre, int n, int64_t b)
     }
     return lo;
 }
-
-struct ItemWalk {
-    const ItemDevB *items;
-    int n, i;
-    int64_t next0;
-    __device__ __forceinline__ void start(const ItemDevB *it, int cnt, int64_t u)
-    {
-        items = it; n = cnt;
-        int lo = 0, hi = cnt - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (it[mid].unit0 <= u) lo = mid; else hi = mid - 1;
-        }
-        i = lo;
-        next0 = i + 1 < cnt ? it[i + 1].unit0 : LLONG_MAX;
-    }
-    __device__ __forceinline__ void advance(int64_t u)
-    {
-        while (u >= next0) {
-            i++;
-            next0 = i + 1 < n ? items[i + 1].unit0 : LLONG_MAX;
-        }
-    }
-};
 
 // 64 values of a 3-D block of row-quad q, x block bxi, levels z0.. (rows
 // past the field's row range, points past a row's end and levels past nz
@@ -240,27 +273,19 @@ batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
     __shared__ uint64_t sout[WARPS][(16 + 2) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t W = (int64_t)gridDim.x * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + wid;
-    int64_t c = gw * bg.nunits / W;
-    const int64_t c1 = (gw + 1) * bg.nunits / W;
-    if (c >= c1) return;
-    ItemWalk walk;
-    walk.start(bg.items, bg.nitems, c);
-    for (; c < c1; c++) {
-        walk.advance(c);
-        const ItemDevB it = bg.items[walk.i];
+    for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
+        const ItemDevB it = bg.items[ii];
         const FieldDevB f = bg.fields[it.field];
         const int64_t b0 = (c - it.unit0) * 32;
         const int nact = (int)min((int64_t)32, it.nblocks - b0);
-        if (f.dims == 3) {
-            if (f.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
+        if (G.dims == 3) {
+            if (G.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
             else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
         } else {
-            if (f.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
+            if (G.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
             else enc1_chunk<16>(f, bg.grid, it, b0, nact, lane, out);
         }
-    }
+    });
 }
 
 template <int RATE>
@@ -318,29 +343,23 @@ batch_decode_kernel(BatchGeom bg, const uint8_t *__restrict__ in)
     __shared__ uint32_t stile[WARPS][(2 * 16 + 3) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t W = (int64_t)gridDim.x * WARPS;
-    const int64_t gw = (int64_t)blockIdx.x * WARPS + wid;
-    int64_t c = gw * bg.nunits / W;
-    const int64_t c1 = (gw + 1) * bg.nunits / W;
-    if (c >= c1) return;
-    ItemWalk walk;
-    walk.start(bg.items, bg.nitems, c);
-    for (; c < c1; c++) {
-        walk.advance(c);
-        const ItemDevB it = bg.items[walk.i];
+    for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
+        const ItemDevB it = bg.items[ii];
         const FieldDevB f = bg.fields[it.field];
         const int64_t b0 = (c - it.unit0) * 32;
         const int nact = (int)min((int64_t)32, it.nblocks - b0);
-        if (lane >= nact) continue;
-        const int64_t b = b0 + lane;
-        if (f.dims == 3) {
-            if (f.rate == 8) dec3_lane<8>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
-            else dec3_lane<16>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
-        } else {
-            if (f.rate == 8) dec1_lane<8>(f, bg.grid, it, b, in);
-            else dec1_lane<16>(f, bg.grid, it, b, in);
+        if (lane < nact) {
+            const int64_t b = b0 + lane;
+            if (G.dims == 3) {
+                if (G.rate == 8) dec3_lane<8>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
+                else dec3_lane<16>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
+            } else {
+                if (G.rate == 8) dec1_lane<8>(f, bg.grid, it, b, in);
+                else dec1_lane<16>(f, bg.grid, it, b, in);
+            }
         }
-    }
+        __syncwarp();
+    });
 }
 
 }  // namespace
@@ -438,7 +457,8 @@ int64_t field_stream_bytes(const GridHost &g, const zfpx_field &F, int r0, int r
 // Field and item descriptors of a set of fields whose streams start at the
 // given byte offsets; items grouped by (dims, rate) class.
 void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stream_off, int nfields,
-                std::vector<FieldDevB> &fd, std::vector<ItemDevB> &items, int64_t &units)
+                std::vector<FieldDevB> &fd, std::vector<ItemDevB> &items, int64_t &units,
+                std::vector<GroupDev> &groups)
 {
     fd.resize(nfields);
     for (int f = 0; f < nfields; f++) {
@@ -487,6 +507,43 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
             ioff += blocks * per_block;
         }
     }
+    // one group per (dims, rate) run of items; work share by values coded
+    // (a rate-16 value costs about 15 % more than a rate-8 one)
+    groups.clear();
+    std::vector<double> work;
+    for (const ItemDevB &it : items) {
+        const FieldDevB &F = fd[it.field];
+        const int64_t n = (it.nblocks + 31) / 32;
+        if (groups.empty() || groups.back().dims != F.dims || groups.back().rate != F.rate) {
+            GroupDev G;
+            G.u0 = it.unit0; G.n = 0; G.dims = F.dims; G.rate = F.rate; G.cum1 = 1.0f; G.pad = 0;
+            groups.push_back(G);
+            work.push_back(0.0);
+        }
+        groups.back().n += n;
+        work.back() += (double)n * (F.dims == 3 ? 2048.0 : 128.0) * (F.rate == 16 ? 1.15 : 1.0);
+    }
+    double total = 0.0, acc = 0.0;
+    for (double w : work) total += w;
+    for (size_t i = 0; i < groups.size(); i++) {
+        acc += work[i];
+        groups[i].cum1 = i + 1 == groups.size() ? 2.0f : (float)(acc / total);
+    }
+}
+
+BatchGeom make_geom(const FieldDevB *d_fields, const ItemDevB *d_items, const GridDev &grid, int nitems,
+                    int64_t nunits, const std::vector<GroupDev> &groups, uint32_t *d_ctr)
+{
+    BatchGeom g;
+    g.items = d_items;
+    g.fields = d_fields;
+    g.grid = grid;
+    g.nitems = nitems;
+    g.nunits = nunits;
+    g.ngroups = (int)groups.size();
+    for (int i = 0; i < g.ngroups; i++) g.groups[i] = groups[i];
+    g.ctr = d_ctr;
+    return g;
 }
 
 int launch_batch(const BatchGeom &g, int warps, int ctas_per_sm, bool encode, const uint8_t *in, uint8_t *out,
@@ -524,6 +581,8 @@ struct zfpx_batch_s {
     int warps = 4, ctas_per_sm = 0;     // 0 = as many as fit
     zfpx::FieldDevB *d_fields = nullptr;
     zfpx::ItemDevB *d_items = nullptr;
+    std::vector<zfpx::GroupDev> groups;
+    uint32_t *d_ctr = nullptr;          // work counters: encode 0..3, decode 4..7
 };
 
 using namespace zfpx;
@@ -536,6 +595,7 @@ void zfpx_batch_destroy(zfpx_batch b)
     b->grid.free_dev();
     cudaFree(b->d_fields);
     cudaFree(b->d_items);
+    cudaFree(b->d_ctr);
     delete b;
 }
 
@@ -563,11 +623,12 @@ int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const 
     b->total = off;
     std::vector<FieldDevB> fd;
     std::vector<ItemDevB> items;
-    build_work(b->grid, fields, b->field_off.data(), nfields, fd, items, b->nunits);
+    build_work(b->grid, fields, b->field_off.data(), nfields, fd, items, b->nunits, b->groups);
     b->nitems = (int)items.size();
     rc = upload_grid(b->grid);
     if (!rc) rc = upload(&b->d_fields, fd);
     if (!rc) rc = upload(&b->d_items, items);
+    if (!rc && cudaMalloc((void **)&b->d_ctr, 2 * kMaxGroups * sizeof(uint32_t)) != cudaSuccess) rc = ZFPX_ENOMEM;
     if (rc) { zfpx_batch_destroy(b); return rc; }
     *out = b;
     return ZFPX_OK;
@@ -595,15 +656,13 @@ int zfpx_batch_set_launch(zfpx_batch b, int warps_per_cta, int ctas_per_sm)
     return ZFPX_OK;
 }
 
-static BatchGeom batch_geom(zfpx_batch b)
+// Geometry for one launch; its work counters are zeroed on the stream first.
+static int batch_geom(zfpx_batch b, bool encode, cudaStream_t st, BatchGeom &g)
 {
-    BatchGeom g;
-    g.items = b->d_items;
-    g.fields = b->d_fields;
-    g.grid = b->grid.dev();
-    g.nitems = b->nitems;
-    g.nunits = b->nunits;
-    return g;
+    uint32_t *ctr = b->d_ctr + (encode ? 0 : kMaxGroups);
+    if (cudaMemsetAsync(ctr, 0, kMaxGroups * sizeof(uint32_t), st) != cudaSuccess) return ZFPX_ECUDA;
+    g = make_geom(b->d_fields, b->d_items, b->grid.dev(), b->nitems, b->nunits, b->groups, ctr);
+    return ZFPX_OK;
 }
 
 int zfpx_batch_encode(zfpx_batch b, uint8_t *d_out, size_t cap, void *stream)
@@ -612,7 +671,9 @@ int zfpx_batch_encode(zfpx_batch b, uint8_t *d_out, size_t cap, void *stream)
     if ((int64_t)cap < b->total) return ZFPX_ESIZE;
     for (const zfpx_field &F : b->fields)
         if (!F.d_src || ((uintptr_t)F.d_src & 3u)) return ZFPX_EINVAL;
-    return launch_batch(batch_geom(b), b->warps, b->ctas_per_sm, true, nullptr, d_out, (cudaStream_t)stream);
+    BatchGeom g;
+    const int rc = batch_geom(b, true, (cudaStream_t)stream, g);
+    return rc ? rc : launch_batch(g, b->warps, b->ctas_per_sm, true, nullptr, d_out, (cudaStream_t)stream);
 }
 
 int zfpx_batch_decode(zfpx_batch b, const uint8_t *d_in, size_t len, void *stream)
@@ -621,7 +682,9 @@ int zfpx_batch_decode(zfpx_batch b, const uint8_t *d_in, size_t len, void *strea
     if ((int64_t)len < b->total) return ZFPX_ESIZE;
     for (const zfpx_field &F : b->fields)
         if (!F.d_dst || ((uintptr_t)F.d_dst & 3u)) return ZFPX_EINVAL;
-    return launch_batch(batch_geom(b), b->warps, b->ctas_per_sm, false, d_in, nullptr, (cudaStream_t)stream);
+    BatchGeom g;
+    const int rc = batch_geom(b, false, (cudaStream_t)stream, g);
+    return rc ? rc : launch_batch(g, b->warps, b->ctas_per_sm, false, d_in, nullptr, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -748,7 +811,7 @@ int zfpx_server_create(zfpx_server *out, const int64_t *row_len, int nrows, size
     if (!rc && cudaMalloc((void **)&s->d_arena, arena_bytes) != cudaSuccess) rc = ZFPX_ENOMEM;
     s->arena.init((int64_t)arena_bytes / 256 * 256);
     s->max_batch = max_batch;
-    const size_t cap = (size_t)max_batch * (sizeof(FieldDevB) + kItemsPerRequest * sizeof(ItemDevB)) + 256;
+    const size_t cap = (size_t)max_batch * (sizeof(FieldDevB) + kItemsPerRequest * sizeof(ItemDevB)) + 768;
     s->slots.resize(nstreams);
     for (auto &sl : s->slots) {
         if (rc) break;
@@ -845,24 +908,27 @@ int zfpx_server_pump(zfpx_server s, int *launched)
     }
     std::vector<FieldDevB> fd;
     std::vector<ItemDevB> items;
+    std::vector<GroupDev> groups;
     int64_t units = 0;
-    build_work(s->grid, fields.data(), soff.data(), (int)fields.size(), fd, items, units);
+    build_work(s->grid, fields.data(), soff.data(), (int)fields.size(), fd, items, units, groups);
+    // descriptors: fields, items, then zeroed work counters (encode, decode)
     const size_t fbytes = fd.size() * sizeof(FieldDevB);
     const size_t ioff = (fbytes + 255) / 256 * 256;
-    const size_t total = ioff + items.size() * sizeof(ItemDevB);
+    const size_t coff = (ioff + items.size() * sizeof(ItemDevB) + 255) / 256 * 256;
+    const size_t total = coff + 2 * kMaxGroups * sizeof(uint32_t);
     if (total > sl.cap) return ZFPX_ESIZE;
     std::memcpy(sl.h_stage, fd.data(), fbytes);
     std::memcpy(sl.h_stage + ioff, items.data(), items.size() * sizeof(ItemDevB));
+    std::memset(sl.h_stage + coff, 0, 2 * kMaxGroups * sizeof(uint32_t));
     if (cudaMemcpyAsync(sl.d_desc, sl.h_stage, total, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         return ZFPX_ECUDA;
-    BatchGeom g;
-    g.fields = reinterpret_cast<const FieldDevB *>(sl.d_desc);
-    g.items = reinterpret_cast<const ItemDevB *>(sl.d_desc + ioff);
-    g.grid = s->grid.dev();
-    g.nitems = (int)items.size();
-    g.nunits = units;
-    int rc = launch_batch(g, s->warps, s->ctas_per_sm, true, nullptr, s->d_arena, sl.stream);
-    if (!rc) rc = launch_batch(g, s->warps, s->ctas_per_sm, false, s->d_arena, nullptr, sl.stream);
+    uint32_t *ctr = reinterpret_cast<uint32_t *>(sl.d_desc + coff);
+    const FieldDevB *dfd = reinterpret_cast<const FieldDevB *>(sl.d_desc);
+    const ItemDevB *dit = reinterpret_cast<const ItemDevB *>(sl.d_desc + ioff);
+    const BatchGeom ge = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, ctr);
+    const BatchGeom gd = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, ctr + kMaxGroups);
+    int rc = launch_batch(ge, s->warps, s->ctas_per_sm, true, nullptr, s->d_arena, sl.stream);
+    if (!rc) rc = launch_batch(gd, s->warps, s->ctas_per_sm, false, s->d_arena, nullptr, sl.stream);
     if (!rc && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = ZFPX_ECUDA;
     if (rc) return rc;
     sl.ids = ids;
