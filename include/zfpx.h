@@ -147,7 +147,17 @@ ZFPX_API int zfpx_pack_compress(zfpx_plan plan, int rate, const float *d_src, ui
 /* zfpx_decompress_unpack (Sec. I: the receiver expands the streams before it
  * computes on them): decodes every message of d_in (len bytes, the
  * chosen layout) and scatters the values into d_dst through the plan's dst
- * view; padding values are dropped.  Errors as above. */
+ * view; padding values are dropped.  Errors as above.
+ *
+ * For dims = 3 the kernels hand out work through counters kept with the
+ * plan's device table of that rate (one pair for compression, one for
+ * decompression), which each launch leaves at zero when it ends.  So calls
+ * with the same plan, rate and direction must not overlap on the GPU (use
+ * one stream, or order the streams); different plans, rates or directions
+ * may run concurrently.  The same holds for zfpx_encode / zfpx_decode with
+ * the same extents, strides and rate, and the counters are never reset by
+ * the host: a launch that fails mid-kernel leaves the context unusable
+ * anyway. */
 ZFPX_API int zfpx_decompress_unpack(zfpx_plan plan, int rate, const uint8_t *d_in, size_t len,
                            float *d_dst, int layout, void *stream);
 
@@ -260,10 +270,11 @@ ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
  * allocator, in loops that must not pay for an allocation, with a fixed
  * device memory map.  It does what zfpx_pack_compress (ZFPX_LAYOUT_RECV)
  * followed by zfpx_decompress_unpack do, d_src -> d_dst through the plan at
- * `rate` (8 or 16), with the same result, but it keeps the plan's message
- * table and the compressed messages in one library-owned device array of
- * ZFPX_NOALLOC_SCRATCH_BYTES (64 MiB), reserved on every GPU that loads the
- * library until the process exits, and calls no allocation routine; the plan
+ * `rate` (8 or 16), with the same result, but it keeps its work counters,
+ * the plan's message table and the compressed messages in one library-owned
+ * device array of ZFPX_NOALLOC_SCRATCH_BYTES (64 MiB), reserved on every GPU
+ * that loads the library until the process exits, and calls no allocation
+ * routine; the plan
  * needs no zfpx_plan_prepare.  The first call on each device looks the array
  * up with that device current.  Every call shares the array, so calls that
  * overlap on the GPU (other streams, other host threads) race; calls in order

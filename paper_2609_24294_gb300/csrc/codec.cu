@@ -69,6 +69,30 @@ struct MsgWalk {
     }
 };
 
+// Dynamic work split of the 3-D kernels: whole warps claim 32-block units
+// from a counter, issuing the next claim before coding the current unit so
+// that its latency hides.  The last warp to run dry resets the counters for
+// the next launch, so no launch needs a memset; two launches that share
+// counters must not overlap on the GPU.
+struct UnitClaim {
+    uint32_t *ctr;                                   // [claim, done]
+    int lane;
+    __device__ __forceinline__ uint32_t next() const
+    {
+        uint32_t u = 0;
+        if (lane == 0) u = atomicAdd(ctr, 1u);
+        return __shfl_sync(0xffffffffu, u, 0);
+    }
+    __device__ __forceinline__ void finish() const
+    {
+        const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+        if (lane == 0 && atomicAdd(ctr + 1, 1u) == nwarps - 1) {
+            ctr[0] = 0u;
+            ctr[1] = 0u;
+        }
+    }
+};
+
 // ================================================================= 3-D kernels
 template <int RATE>
 __global__ void __launch_bounds__(kThreads)
@@ -79,16 +103,11 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
     SmemPlanes pl{splanes[wid], lane};
-    const int64_t W = (int64_t)gridDim.x * kWarps;
-    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
-    int64_t c = gw * g.nunits / W;
-    const int64_t c1 = (gw + 1) * g.nunits / W;
-    if (c >= c1) return;
-    MsgWalk walk;
-    walk.start(g.msgs, g.nmsg, c);
-    for (; c < c1; c++) {
-        walk.advance(c);
-        const MsgDev &m = g.msgs[walk.mi];
+    const UnitClaim cl{g.ctr, lane};
+    for (uint32_t u = cl.next(); (int64_t)u < g.nunits;) {
+        const int64_t c = u;
+        u = cl.next();
+        const MsgDev &m = g.msgs[find_msg(g.msgs, g.nmsg, c)];
         const int64_t unit0 = m.unit0, nblocks = m.nblocks, src_off = m.src_off;
         const int64_t boff = layout ? m.off[1] : m.off[0];
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
@@ -139,6 +158,7 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         }
         __syncwarp();
     }
+    cl.finish();
 }
 
 template <int RATE>
@@ -153,62 +173,60 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
     const StreamTile tile{t32, lane};
 #pragma unroll
     for (int r = 0; r < 3; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
-    const int64_t W = (int64_t)gridDim.x * kWarps;
-    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
-    int64_t c = gw * g.nunits / W;
-    const int64_t c1 = (gw + 1) * g.nunits / W;
-    if (c >= c1) return;
-    MsgWalk walk;
-    walk.start(g.msgs, g.nmsg, c);
-    for (; c < c1; c++) {
-        walk.advance(c);
-        const MsgDev &m = g.msgs[walk.mi];
+    const UnitClaim cl{g.ctr + 2, lane};
+    for (uint32_t u = cl.next(); (int64_t)u < g.nunits;) {
+        const int64_t c = u;
+        u = cl.next();
+        const MsgDev &m = g.msgs[find_msg(g.msgs, g.nmsg, c)];
         const int64_t unit0 = m.unit0, nblocks = m.nblocks, dst_off = m.dst_off;
         const int64_t boff = layout ? m.off[1] : m.off[0];
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
         const int64_t b0 = (c - unit0) * 32;
         const int nact = (int)min((int64_t)32, nblocks - b0);
-        if (lane >= nact) continue;
-        const int b = (int)b0 + lane;
-        // this lane's block: RATE / 2 16-byte loads into its own tile column
-        const uint4 *src4 = reinterpret_cast<const uint4 *>(in + boff) + (int64_t)b * (RATE / 2);
+        if (lane < nact) {
+            const int b = (int)b0 + lane;
+            // this lane's block: RATE / 2 16-byte loads into its own tile column
+            const uint4 *src4 = reinterpret_cast<const uint4 *>(in + boff) + (int64_t)b * (RATE / 2);
 #pragma unroll
-        for (int i = 0; i < RATE / 2; i++) {
-            const uint4 v = __ldg(src4 + i);
-            t32[(4 * i) * 32 + lane] = v.x;
-            t32[(4 * i + 1) * 32 + lane] = v.y;
-            t32[(4 * i + 2) * 32 + lane] = v.z;
-            t32[(4 * i + 3) * 32 + lane] = v.w;
-        }
-        const int bxi = b % bxn, t = b / bxn;
-        const int byi = t % byn, bzi = t / byn;
-        const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
-        float v[64];
-        decode_block3_tile<RATE>(tile, v, pl);
-        float *base = dstf + dst_off;
-        if (vec && x0 + 4 <= nx) {
+            for (int i = 0; i < RATE / 2; i++) {
+                const uint4 v = __ldg(src4 + i);
+                t32[(4 * i) * 32 + lane] = v.x;
+                t32[(4 * i + 1) * 32 + lane] = v.y;
+                t32[(4 * i + 2) * 32 + lane] = v.z;
+                t32[(4 * i + 3) * 32 + lane] = v.w;
+            }
+            const int bxi = b % bxn, t = b / bxn;
+            const int byi = t % byn, bzi = t / byn;
+            const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
+            float v[64];
+            decode_block3_tile<RATE>(tile, v, pl);
+            float *base = dstf + dst_off;
+            if (vec && x0 + 4 <= nx) {
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+                for (int k = 0; k < 4; k++) {
 #pragma unroll
-                for (int j = 0; j < 4; j++) {
-                    float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + x0;
-                    if (z0 + k < nz && y0 + j < ny)
-                        *reinterpret_cast<float4 *>(row) = make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1],
-                                                                       v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+                    for (int j = 0; j < 4; j++) {
+                        float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + x0;
+                        if (z0 + k < nz && y0 + j < ny)
+                            *reinterpret_cast<float4 *>(row) = make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1],
+                                                                           v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+                    }
+                }
+            } else {
+                float t[64];
+#pragma unroll
+                for (int r = 0; r < 64; r++) t[r] = v[r];
+#pragma unroll 1
+                for (int r = 0; r < 64; r++) {
+                    const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                    if (x0 + i < nx && y0 + j < ny && z0 + k < nz)
+                        base[(int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + (int64_t)(x0 + i) * g.ds[0]] = t[r];
                 }
             }
-        } else {
-            float t[64];
-#pragma unroll
-            for (int r = 0; r < 64; r++) t[r] = v[r];
-#pragma unroll 1
-            for (int r = 0; r < 64; r++) {
-                const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
-                if (x0 + i < nx && y0 + j < ny && z0 + k < nz)
-                    base[(int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + (int64_t)(x0 + i) * g.ds[0]] = t[r];
-            }
         }
+        __syncwarp();
     }
+    cl.finish();
 }
 
 // ================================================================= 1-D kernels
@@ -363,7 +381,7 @@ int zfpx_pack_compress(zfpx_plan p, int rate, const float *d_src, uint8_t *d_out
     int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
     if (rc) return rc;
     LaunchGeom g{};
-    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits; g.ctr = t->d_ctr;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
     const int vec = vec_ok(d_src, p->ss, p, 0) ? 1 : 0;
     return launch_encode(p->dims, rate, d_src, d_out, g, layout, vec, (cudaStream_t)stream);
@@ -380,7 +398,7 @@ int zfpx_decompress_unpack(zfpx_plan p, int rate, const uint8_t *d_in, size_t le
     int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
     if (rc) return rc;
     LaunchGeom g{};
-    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits; g.ctr = t->d_ctr;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
     const int vec = vec_ok(d_dst, p->ds, p, 1) ? 1 : 0;
     return launch_decode(p->dims, rate, d_in, d_dst, g, layout, vec, (cudaStream_t)stream);
@@ -539,18 +557,23 @@ extern "C" int zfpx_transpose_noalloc(zfpx_plan p, int rate, const float *d_src,
     }
     const size_t table_bytes = (M * sizeof(MsgDev) + 255) / 256 * 256;
     const size_t stream_bytes = (size_t)ro;
-    if (table_bytes + stream_bytes > ZFPX_NOALLOC_SCRATCH_BYTES) return ZFPX_ESIZE;
+    // layout of the array: 256 bytes of work counters (zero between calls),
+    // the message table, the compressed messages
+    constexpr size_t kCtrBytes = 256;
+    if (kCtrBytes + table_bytes + stream_bytes > ZFPX_NOALLOC_SCRATCH_BYTES) return ZFPX_ESIZE;
     void *scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     if (units == 0) return ZFPX_OK;
     cudaStream_t st = (cudaStream_t)stream;
     // pageable source: the copy has read h before this call returns
-    if (cudaMemcpyAsync(scratch, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    uint8_t *base = static_cast<uint8_t *>(scratch);
+    if (cudaMemcpyAsync(base + kCtrBytes, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return ZFPX_ECUDA;
-    uint8_t *buf = static_cast<uint8_t *>(scratch) + table_bytes;
+    uint8_t *buf = base + kCtrBytes + table_bytes;
     LaunchGeom g{};
-    g.msgs = static_cast<const MsgDev *>(scratch);
+    g.msgs = reinterpret_cast<const MsgDev *>(base + kCtrBytes);
+    g.ctr = reinterpret_cast<uint32_t *>(base);
     g.nmsg = (int)M;
     g.nunits = units;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }

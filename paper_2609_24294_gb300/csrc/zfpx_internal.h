@@ -32,6 +32,7 @@ struct LaunchGeom {
     int64_t nunits;     // total work units
     int64_t ss[3];      // source strides (elements)
     int64_t ds[3];      // destination strides (elements)
+    uint32_t *ctr;      // 3-D codec work counters: encode claim / done, decode claim / done (zero between launches)
 };
 
 struct HostMsg {
@@ -41,7 +42,8 @@ struct HostMsg {
 
 // Device tables of one (rate, unit kind, device) for a plan.
 struct DevTable {
-    MsgDev *d_msgs = nullptr;
+    MsgDev *d_msgs = nullptr;   // one allocation: the table, then 4 work counters (zeroed)
+    uint32_t *d_ctr = nullptr;
     int64_t nunits = 0;
 };
 

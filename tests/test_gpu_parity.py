@@ -183,6 +183,31 @@ def test_random_streams_decode_like_oracle(z):
             same_bits(host(dec), rdec)
 
 
+def test_repeated_launches_reuse_work_counters(z):
+    # the 3-D kernels hand out work through counters that each launch leaves
+    # at zero: every launch of a run must code every block
+    x = smooth_field((24, 40, 72), 3, offset=250.0)
+    nz, ny, nx = x.shape
+    xd = dev(x)
+    plan = z.Plan.for_fields(xd, 2, 3, 0, 3)
+    for rate in (8, 16):
+        outs = []
+        for _ in range(4):
+            buf = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+            z.zfpx_pack_compress(plan, rate, xd, buf)
+            outs.append(buf)
+        for buf in outs[1:]:
+            assert torch.equal(buf, outs[0])
+        decs = []
+        for _ in range(4):
+            d = torch.full_like(xd, float("nan"))
+            z.zfpx_decompress_unpack(plan, rate, outs[0], d, layout=z.LAYOUT_SEND)
+            decs.append(d)
+        for d in decs[1:]:
+            same_bits(host(d), host(decs[0]))
+        assert not torch.isnan(decs[0]).any()                       # every value written
+
+
 # ---------------------------------------------------------------- plans
 PLANS = [((17, 23, 37), 3, 2), ((8, 32, 64), 2, 2), ((5, 9, 11), 2, 3), ((20, 16, 48), 1, 4)]
 
