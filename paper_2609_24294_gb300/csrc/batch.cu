@@ -302,7 +302,7 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
         t32[(4 * i + 3) * 32 + lane] = v.w;
     }
 #pragma unroll
-    for (int r = 0; r < 3; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
+    for (int r = 0; r < kTileZeroRows<RATE>; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
     const int64_t bg = b + f.b0;
     const int q = upper_index(g.qpre, g.nq + 1, bg);
     const int bxi = (int)(bg - __ldg(g.qpre + q));
@@ -340,7 +340,7 @@ template <int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
 batch_decode_kernel(BatchGeom bg, const uint8_t *__restrict__ in)
 {
-    __shared__ uint32_t stile[WARPS][(2 * 16 + 3) * 32];
+    __shared__ uint32_t stile[WARPS][(2 * 16 + 2) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {

@@ -33,11 +33,17 @@ using namespace blk;
 
 constexpr int kWarps = 4;
 constexpr int kThreads = 32 * kWarps;
-// Resident CTAs per SM the 3-D decoder is compiled for: at rate 8 its shared
-// memory leaves room for five, and capping registers to fit them pays; at
-// rate 16 shared memory allows four whatever the registers.
+// Launch shapes of the 3-D kernels, chosen by measurement on GB300: 4 warps
+// per CTA, except the rate-16 decoder, whose 3-warp CTAs fit six to an SM
+// (two zero rows after its stream tile make the shared memory fit); the
+// rate-8 decoder is compiled for five resident CTAs, which its shared memory
+// allows and capping its registers to match pays for.
 template <int RATE>
-constexpr int dec3_min_blocks() { return RATE == 8 ? 5 : 1; }
+constexpr int kEnc3Warps = 4;
+template <int RATE>
+constexpr int kDec3Warps = RATE == 16 ? 3 : 4;
+template <int RATE>
+constexpr int kDec3MinBlocks = RATE == 8 ? 5 : 6;
 
 // ----------------------------------------------------------------- message walk
 __device__ __forceinline__ int find_msg(const MsgDev *msgs, int nmsg, int64_t u)
@@ -95,11 +101,11 @@ struct UnitClaim {
 
 // ================================================================= 3-D kernels
 template <int RATE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(32 * kEnc3Warps<RATE>)
 encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
 {
-    __shared__ uint64_t smem[kWarps][(RATE + 2) * 32];
-    __shared__ uint64_t splanes[kWarps][32 * 32];
+    __shared__ uint64_t smem[kEnc3Warps<RATE>][(RATE + 2) * 32];
+    __shared__ uint64_t splanes[kEnc3Warps<RATE>][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
     SmemPlanes pl{splanes[wid], lane};
@@ -162,17 +168,17 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
 }
 
 template <int RATE>
-__global__ void __launch_bounds__(kThreads, dec3_min_blocks<RATE>())
+__global__ void __launch_bounds__(32 * kDec3Warps<RATE>, kDec3MinBlocks<RATE>)
 decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
-    __shared__ uint32_t stile[kWarps][(2 * RATE + 3) * 32];
-    __shared__ uint64_t splanes[kWarps][32 * 32];
+    __shared__ uint32_t stile[kDec3Warps<RATE>][(2 * RATE + kTileZeroRows<RATE>) * 32];
+    __shared__ uint64_t splanes[kDec3Warps<RATE>][32 * 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t *t32 = stile[wid];
     SmemPlanes pl{splanes[wid], lane};
     const StreamTile tile{t32, lane};
 #pragma unroll
-    for (int r = 0; r < 3; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
+    for (int r = 0; r < kTileZeroRows<RATE>; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
     const UnitClaim cl{g.ctr + 2, lane};
     for (uint32_t u = cl.next(); (int64_t)u < g.nunits;) {
         const int64_t c = u;
@@ -313,10 +319,10 @@ decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
 
 // ================================================================= launch
 template <class K>
-int grid_for(K kernel, int64_t nunits)
+int grid_for(K kernel, int64_t nunits, int warps = kWarps)
 {
-    const int occ = occupancy((const void *)kernel, kThreads);
-    const int64_t want = (nunits + kWarps - 1) / kWarps;
+    const int occ = occupancy((const void *)kernel, 32 * warps);
+    const int64_t want = (nunits + warps - 1) / warps;
     const int64_t cap = (int64_t)num_sms() * occ;
     return (int)std::max<int64_t>(1, std::min(want, cap));
 }
@@ -338,8 +344,12 @@ int launch_encode(int dims, int rate, const float *src, uint8_t *out, const Laun
 {
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
-        if (rate == 8) encode3_kernel<8><<<grid_for(encode3_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
-        else encode3_kernel<16><<<grid_for(encode3_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+        if (rate == 8)
+            encode3_kernel<8><<<grid_for(encode3_kernel<8>, g.nunits, kEnc3Warps<8>), 32 * kEnc3Warps<8>, 0, st>>>(
+                src, out, g, layout, vec);
+        else
+            encode3_kernel<16><<<grid_for(encode3_kernel<16>, g.nunits, kEnc3Warps<16>), 32 * kEnc3Warps<16>, 0,
+                                 st>>>(src, out, g, layout, vec);
     } else {
         if (rate == 8) encode1_kernel<8><<<grid_for(encode1_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
         else encode1_kernel<16><<<grid_for(encode1_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
@@ -353,8 +363,12 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
 {
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
-        if (rate == 8) decode3_kernel<8><<<grid_for(decode3_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
-        else decode3_kernel<16><<<grid_for(decode3_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+        if (rate == 8)
+            decode3_kernel<8><<<grid_for(decode3_kernel<8>, g.nunits, kDec3Warps<8>), 32 * kDec3Warps<8>, 0, st>>>(
+                in, dst, g, layout, vec);
+        else
+            decode3_kernel<16><<<grid_for(decode3_kernel<16>, g.nunits, kDec3Warps<16>), 32 * kDec3Warps<16>, 0,
+                                 st>>>(in, dst, g, layout, vec);
     } else {
         if (rate == 8) decode1_kernel<8><<<grid_for(decode1_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
         else decode1_kernel<16><<<grid_for(decode1_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);

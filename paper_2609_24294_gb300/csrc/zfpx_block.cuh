@@ -516,7 +516,13 @@ ZFPX_HD void encode_block3(const float (&x)[64], Writer &wr, Planes &pl)
 }
 
 // ----------------------------------------------------------------- 3-D decoder over a stream tile
-// Reads are 64-bit windows funnel-shifted out of three tile words.
+// Reads are 64-bit windows funnel-shifted out of three tile words.  The tile
+// holds the 2 RATE stream words and kTileZeroRows<RATE> zero words after
+// them: three let the decoder read a window at the stream's end without a
+// test; at rate 16 the decoder tests instead and two suffice, which is what
+// lets six 3-warp CTAs share an SM.
+template <int RATE>
+constexpr int kTileZeroRows = RATE == 16 ? 2 : 3;
 template <class Tile>
 ZFPX_HD uint64_t tile_peek(const Tile &t, int pos)
 {
@@ -589,7 +595,7 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
             // cut by the budget shows as one that runs on, and only the
             // implied one needs the check that its zeros fit (B bits left).
             uint64_t term;
-            uint64_t V = group_values(tile_peek(tile, pos), term);
+            uint64_t V = group_values(kTileZeroRows<RATE> >= 3 || pos < END ? tile_peek(tile, pos) : 0ull, term);
             const int T = term ? lowest_set(term) : 64;          // offset of the closing 0
             const int lim = 62 - n;                              // offset - rank of coefficient 62
             const int B = END - pos;
@@ -630,7 +636,7 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
 #pragma unroll 1
         for (;;) {
             const int r = END - pos;
-            const uint64_t v = tile_peek(tile, pos);
+            const uint64_t v = kTileZeroRows<RATE> >= 3 || pos < END ? tile_peek(tile, pos) : 0ull;
             const int lim = 63 - n;
             const int tz = v ? lowest_set(v) : 64;
             if (tz >= lim) {                                     // only the implied one is left

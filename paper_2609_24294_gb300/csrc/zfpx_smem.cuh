@@ -70,7 +70,8 @@ struct SmemPlanes {
 
 // Stream tile of one warp: 32-bit words in a [word][lane] layout (word i of
 // lane l at i * 32 + l), so every lane reads its own column without bank
-// conflicts; three zero rows follow the stream for the 64-bit read window.
+// conflicts; two zero rows follow the stream, so the 64-bit window read at
+// any position before the stream's end stays inside the tile.
 struct StreamTile {
     const uint32_t *sm;
     int lane;
