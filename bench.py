@@ -543,27 +543,57 @@ def run_gpu(args):
         err["r%d" % r] = {"rel_l2": float(np.linalg.norm(d - x64) / np.linalg.norm(x64)),
                           "max_abs": float(np.max(np.abs(d - x64)))}
 
-    # end to end through the public API: pinned host field in, decoded fields out
+    # end to end through the public API: pinned host field in, decoded fields out.  Every step
+    # copies its field in and both decoded fields out; the copies run on their own streams,
+    # double-buffered, so step i+1's input and step i's outputs cross the host link while the
+    # codec works.
     hx = torch.from_numpy(x).pin_memory()
     hout = {r: torch.empty(SHAPE, dtype=torch.float32).pin_memory() for r in RATES}
-    xin = torch.empty_like(xd)
+    xin = [torch.empty_like(xd) for _ in range(2)]
+    dout = {r: [torch.empty_like(xd) for _ in range(2)] for r in RATES}
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ev_in = [torch.cuda.Event() for _ in range(2)]                 # input b is on the device
+    ev_used = [torch.cuda.Event() for _ in range(2)]               # the codec has read input b
+    ev_done = {r: [torch.cuda.Event() for _ in range(2)] for r in RATES}   # output (r, b) written
+    ev_read = {r: [torch.cuda.Event() for _ in range(2)] for r in RATES}   # output (r, b) copied out
+    for e in ev_used + [ev_read[r][k] for r in RATES for k in range(2)]:
+        e.record(stream)
 
-    def e2e_step():
-        xin.copy_(hx, non_blocking=True)
-        for r in RATES:
-            z.zfpx_pack_compress(plan, r, xin, send[r])
-            z.zfpx_permute(plan, r, send[r], recv[r])
-            z.zfpx_decompress_unpack(plan, r, recv[r], outs[r])
-            hout[r].copy_(outs[r], non_blocking=True)
-    for _ in range(args.warmup):
-        e2e_step()
+    def e2e_steps(n):
+        for i in range(n):
+            k = i % 2
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(ev_used[k])
+                xin[k].copy_(hx, non_blocking=True)
+                ev_in[k].record(s_in)
+            stream.wait_event(ev_in[k])
+            for j, r in enumerate(RATES):
+                stream.wait_event(ev_read[r][k])
+                z.zfpx_pack_compress(plan, r, xin[k], send[r])
+                if j == len(RATES) - 1:
+                    ev_used[k].record(stream)
+                z.zfpx_permute(plan, r, send[r], recv[r])
+                z.zfpx_decompress_unpack(plan, r, recv[r], dout[r][k])
+                ev_done[r][k].record(stream)
+                with torch.cuda.stream(s_out):
+                    s_out.wait_event(ev_done[r][k])
+                    hout[r].copy_(dout[r][k], non_blocking=True)
+                    ev_read[r][k].record(s_out)
+        tail = torch.cuda.Event()
+        tail.record(s_out)
+        stream.wait_event(tail)
+        tail_in = torch.cuda.Event()
+        tail_in.record(s_in)
+        stream.wait_event(tail_in)
+    e2e_steps(args.warmup)
     torch.cuda.synchronize()
     barrier()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for _ in range(args.steps):
-        e2e_step()
+    s_in.wait_stream(stream)
+    s_out.wait_stream(stream)
+    e2e_steps(args.steps)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = multirank.max_over_ranks(a.elapsed_time(b), device="cuda")
