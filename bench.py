@@ -25,7 +25,7 @@ import subprocess
 import sys
 import threading
 import time
-from concurrent.futures import ThreadPoolExecutor
+from concurrent.futures import FIRST_COMPLETED, ThreadPoolExecutor, wait
 
 import numpy as np
 
@@ -137,16 +137,16 @@ def recorded_traffic(kernel_key, sha):
 
 
 # ------------------------------------------------------------------ CPU oracle leg
-def oracle_sample(x, max_seconds, max_messages=None):
+def oracle_sample(x, max_seconds, max_messages=None, threads=None):
     """Runs the oracle over messages of the same plan (both rates, compress and
-    decompress) on all host cores until max_seconds or the whole field is
-    done.  Returns (f32 bytes processed, seconds, threads, messages)."""
+    decompress) on `threads` host cores (default all) until max_seconds or the
+    whole field is done.  Returns (f32 bytes processed, seconds, threads, messages)."""
     from oracle import codec as oc
     from oracle import plan as opl
     nz, ny, nx = x.shape
     plan = opl.Plan(nx, ny, nz, PR, PC, 0, 3)
     msgs = plan.messages[: max_messages or len(plan.messages)]
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
 
     def one(m):
         box = x[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx]
@@ -166,15 +166,72 @@ def oracle_sample(x, max_seconds, max_messages=None):
             if m is not None:
                 pending.add(ex.submit(one, m))
         while pending:
-            f = next(iter(pending))
-            done_bytes += f.result()
-            done += 1
-            pending.discard(f)
-            if time.perf_counter() - t0 < max_seconds:
-                m = next(it, None)
-                if m is not None:
-                    pending.add(ex.submit(one, m))
+            finished, pending = wait(pending, return_when=FIRST_COMPLETED)
+            for f in finished:                   # refill as soon as any message is done
+                done_bytes += f.result()
+                done += 1
+                if time.perf_counter() - t0 < max_seconds:
+                    m = next(it, None)
+                    if m is not None:
+                        pending.add(ex.submit(one, m))
     return done_bytes, time.perf_counter() - t0, threads, done
+
+
+def field_errors(x, y):
+    """Errors of y against x (float32 tensors on the device), in FP64: global relative L2,
+    max |error|, mean |error| / |x| over x != 0, and the relative L2 error of each 4x4x4
+    block (lon, lat, lev; levels past the last multiple of 4 left out; blocks of zeros
+    skipped): mean and quantiles."""
+    import torch
+    x64 = x.double()
+    d = y.double() - x64
+    ax = x64.abs()
+    nz = ax > 0
+    res = {"rel_l2": float(d.norm() / x64.norm()), "max_abs": float(d.abs().max()),
+           "mean_rel": float((d.abs()[nz] / ax[nz]).mean())}
+    L = (x.shape[0] // 4) * 4
+
+    def blocks(t):
+        t = t[:L]
+        Z, Y, X = t.shape
+        return t.reshape(Z // 4, 4, Y // 4, 4, X // 4, 4).permute(0, 2, 4, 1, 3, 5).reshape(-1, 64)
+    bx = blocks(x64).norm(dim=1)
+    bd = blocks(d).norm(dim=1)
+    keep = bx > 0
+    eb = bd[keep] / bx[keep]
+    qs = torch.quantile(eb, torch.tensor([0.5, 0.9, 0.99], dtype=torch.float64, device=eb.device))
+    res["block"] = {"mean": float(eb.mean()), "p50": float(qs[0]), "p90": float(qs[1]),
+                    "p99": float(qs[2]), "max": float(eb.max()), "blocks": int(keep.sum())}
+    del x64, d, ax, nz, bx, bd
+    return res
+
+
+def reconstruction_errors(z, plan, x, decoded=None):
+    """ZFP rates 8 and 16 (decoded[r] if given, else coded here) and the float16 cast,
+    round to nearest and toward zero, through the same plan."""
+    import torch
+    out = {}
+    y = torch.empty_like(x)
+    for r in RATES:
+        if decoded is not None:
+            out["r%d" % r] = field_errors(x, decoded[r])
+            continue
+        sb = torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        z.zfpx_pack_compress(plan, r, x, sb)
+        z.zfpx_permute(plan, r, sb, rb)
+        z.zfpx_decompress_unpack(plan, r, rb, y)
+        out["r%d" % r] = field_errors(x, y)
+        del sb, rb
+    for label, mode in (("fp16_rn", z.ROUND_NEAREST), ("fp16_rz", z.ROUND_ZERO)):
+        sb = torch.zeros(plan.buffer_bytes(z.RATE_F16), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        z.zfpx_cast_fp16_pack(plan, mode, x, sb)
+        z.zfpx_permute(plan, z.RATE_F16, sb, rb)
+        z.zfpx_fp16_unpack(plan, rb, y)
+        out[label] = field_errors(x, y)
+        del sb, rb
+    return out
 
 
 def make_field():
@@ -234,6 +291,40 @@ def _octahedral_fields():
         src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
         fields.append((src, torch.empty_like(src), dims, rate))
     return og.row_lengths(1280), fields
+
+
+def extra_small_latency(z):
+    """The 64 x 32 x 8 T21 field (64 KiB, 256 blocks) over 2 x 2 ranks: latency of one
+    pack+compress -> all-to-all -> decompress+unpack at rates 16 and 8 (median of 50)."""
+    import torch
+    import fieldgen
+    x = torch.from_numpy(fieldgen.config1_field()).cuda()
+    plan = z.Plan.for_fields(x, 2, 2, 0, 3)
+    res = {"workload": "64x32x8 f32 (64 KiB) T21, 2x2 ranks"}
+    st = torch.cuda.current_stream()
+    for r in (16, 8):
+        plan.prepare(r)
+        sb = torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        y = torch.empty_like(x)
+
+        def once():
+            z.zfpx_pack_compress(plan, r, x, sb)
+            z.zfpx_permute(plan, r, sb, rb)
+            z.zfpx_decompress_unpack(plan, r, rb, y)
+        for _ in range(5):
+            once()
+        ts = []
+        for _ in range(50):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(st)
+            once()
+            b.record(st)
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        res["r%d_us" % r] = 1e3 * float(np.median(ts))
+    return res
 
 
 def extra_batched(z, reps, peak, lens, fields):
@@ -535,13 +626,10 @@ def run_gpu(args):
                        "roundtrip_ms": sum(ms) / args.steps, "message_bytes_total": bb}
         del sb, rb, o
 
-    # reconstruction error of the timed outputs (FP64, off the timed path)
-    x64 = x.astype(np.float64)
-    err = {}
-    for r in RATES:
-        d = outs[r].cpu().numpy().astype(np.float64)
-        err["r%d" % r] = {"rel_l2": float(np.linalg.norm(d - x64) / np.linalg.norm(x64)),
-                          "max_abs": float(np.max(np.abs(d - x64)))}
+    # reconstruction error (FP64 against the float32 input, off the timed path): the timed
+    # outputs, the float16 cast both ways, and the same for the temperature-like field
+    err = {"unit_rms_field": reconstruction_errors(z, plan, xd, outs),
+           "temperature_like": reconstruction_errors(z, plan, (250.0 + 20.0 * xd.double()).float())}
 
     # end to end through the public API: pinned host field in, decoded fields out.  Every step
     # copies its field in and both decoded fields out; the copies run on their own streams,
@@ -603,6 +691,10 @@ def run_gpu(args):
     if not args.no_extras:
         reps = max(3, args.steps // 2)
         try:
+            extras["small_field_latency"] = extra_small_latency(z)
+        except Exception as e:
+            extras["small_field_latency"] = {"error": repr(e)}
+        try:
             extras["transposition_pair"] = extra_pair(z, reps, peak)
         except Exception as e:              # reported, never silently dropped
             extras["transposition_pair"] = {"error": repr(e)}
@@ -625,9 +717,12 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         b_, s_, threads, done = oracle_sample(x, args.cpu_seconds)
+        b1, s1, _, done1 = oracle_sample(x, max(1.0, args.cpu_seconds / 4), threads=1)
         cpu = {"value": b_ / s_ / 1e9, "unit": "GB/s", "cores": threads, "kind": "oracle",
                "sample": "%d of 512 messages of this plan, each through r8 and r16 compress+decompress "
-                         "(%.1f s on %d threads)" % (done, s_, threads)}
+                         "(%.1f s on %d threads)" % (done, s_, threads),
+               "single_thread": {"value": b1 / s1 / 1e9, "unit": "GB/s",
+                                 "sample": "%d messages in %.1f s on 1 thread" % (done1, s1)}}
 
     if rank == 0:
         line = {
