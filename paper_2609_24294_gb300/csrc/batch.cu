@@ -136,46 +136,33 @@ __device__ __forceinline__ int upper_index(const int64_t *pre, int n, int64_t b)
     return lo;
 }
 
-// 64 values of a 3-D block of row-quad q, x block bxi, levels z0.. (rows
-// past the field's row range, points past a row's end and levels past nz
-// repeat the last one).  Blocks inside all four rows take 16-byte row loads;
-// the few at a row's end take a rolled element path.
+// 64 values of a 3-D block of row-quad q, x block bxi, levels z0.. (rows past
+// the field's row range, points past a row's end and levels past nz repeat
+// the last one).  Row by row: each row's loads can start as soon as its own
+// offset has arrived, which keeps the latency of a lone small batch low (a
+// variant testing all four rows first was a little faster on big batches and
+// a quarter slower on small ones).
 __device__ __forceinline__ void gather_quad(const FieldDevB &f, const GridDev &g, int q, int bxi, int z0, int nz,
                                             float (&x)[64])
 {
     const int x0 = 4 * bxi;
-    int64_t roff[4];
-    int len[4];
-    int minlen = INT_MAX;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
         const int r = min(4 * q + j, f.row1 - 1);
-        roff[j] = __ldg(g.row_off + r) - f.roff0;
-        len[j] = __ldg(g.row_len + r);
-        minlen = min(minlen, len[j]);
-    }
-    if (f.vec && x0 + 4 <= minlen) {
+        const int64_t roff = __ldg(g.row_off + r) - f.roff0;
+        const int len = __ldg(g.row_len + r);
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            const float *lev = f.src + (int64_t)(z0 + min(k, nz - 1)) * f.src_ls + x0;
-#pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const float4 v = __ldg(reinterpret_cast<const float4 *>(lev + roff[j]));
+            const float *row = f.src + (int64_t)(z0 + min(k, nz - 1)) * f.src_ls + roff;
+            if (f.vec && x0 + 4 <= len) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x0));
                 x[16 * k + 4 * j] = v.x; x[16 * k + 4 * j + 1] = v.y;
                 x[16 * k + 4 * j + 2] = v.z; x[16 * k + 4 * j + 3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) x[16 * k + 4 * j + i] = __ldg(row + min(x0 + i, len - 1));
             }
         }
-    } else {
-        float t[64];
-#pragma unroll 1
-        for (int e = 0; e < 64; e++) {
-            const int i = e & 3, j = (e >> 2) & 3, k = e >> 4;
-            const int64_t ro = j == 0 ? roff[0] : j == 1 ? roff[1] : j == 2 ? roff[2] : roff[3];
-            const int l = j == 0 ? len[0] : j == 1 ? len[1] : j == 2 ? len[2] : len[3];
-            t[e] = __ldg(f.src + (int64_t)(z0 + min(k, nz - 1)) * f.src_ls + ro + min(x0 + i, l - 1));
-        }
-#pragma unroll
-        for (int e = 0; e < 64; e++) x[e] = t[e];
     }
 }
 
@@ -185,36 +172,25 @@ __device__ __forceinline__ void scatter_quad(const FieldDevB &f, const GridDev &
                                              const float (&x)[64])
 {
     const int x0 = 4 * bxi;
-    int64_t roff[4];
-    int len[4];
-    int minlen = INT_MAX;
 #pragma unroll
     for (int j = 0; j < 4; j++) {
-        const int r = min(4 * q + j, f.row1 - 1);
-        roff[j] = __ldg(g.row_off + r) - f.roff0;
-        len[j] = 4 * q + j < f.row1 ? __ldg(g.row_len + r) : 0;
-        minlen = min(minlen, len[j]);
-    }
-    if (f.vec && x0 + 4 <= minlen) {
+        const int r = 4 * q + j;
+        if (r >= f.row1) continue;
+        const int64_t roff = __ldg(g.row_off + r) - f.roff0;
+        const int len = __ldg(g.row_len + r);
+        if (x0 >= len) continue;
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            float *lev = f.dst + (int64_t)(z0 + k) * f.dst_ls + x0;
+            if (k >= nz) continue;
+            float *row = f.dst + (int64_t)(z0 + k) * f.dst_ls + roff;
+            if (f.vec && x0 + 4 <= len) {
+                *reinterpret_cast<float4 *>(row + x0) =
+                    make_float4(x[16 * k + 4 * j], x[16 * k + 4 * j + 1], x[16 * k + 4 * j + 2], x[16 * k + 4 * j + 3]);
+            } else {
 #pragma unroll
-            for (int j = 0; j < 4; j++)
-                if (k < nz)
-                    *reinterpret_cast<float4 *>(lev + roff[j]) = make_float4(
-                        x[16 * k + 4 * j], x[16 * k + 4 * j + 1], x[16 * k + 4 * j + 2], x[16 * k + 4 * j + 3]);
-        }
-    } else {
-        float t[64];
-#pragma unroll
-        for (int e = 0; e < 64; e++) t[e] = x[e];
-#pragma unroll 1
-        for (int e = 0; e < 64; e++) {
-            const int i = e & 3, j = (e >> 2) & 3, k = e >> 4;
-            const int64_t ro = j == 0 ? roff[0] : j == 1 ? roff[1] : j == 2 ? roff[2] : roff[3];
-            const int l = j == 0 ? len[0] : j == 1 ? len[1] : j == 2 ? len[2] : len[3];
-            if (k < nz && x0 + i < l) f.dst[(int64_t)(z0 + k) * f.dst_ls + ro + x0 + i] = t[e];
+                for (int i = 0; i < 4; i++)
+                    if (x0 + i < len) row[x0 + i] = x[16 * k + 4 * j + i];
+            }
         }
     }
 }
