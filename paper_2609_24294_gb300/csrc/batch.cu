@@ -93,14 +93,25 @@ __device__ __forceinline__ int item_of_unit(const ItemDevB *items, int n, int64_
     return lo;
 }
 
-// Work distribution of the batch kernels: each (dims, rate) group is a queue
-// of 32-block units claimed one at a time by whole warps.  A CTA starts on
+// Work distribution of the batch kernels.  A batch with no more units than
+// the grid has warps gives each warp one unit.  Otherwise each (dims, rate)
+// group is a queue of 32-block units claimed one at a time by whole warps.  A CTA starts on
 // its home group -- the SMs are split between groups in proportion to their
 // work, so an SM mostly runs one kind's code and keeps it in its instruction
 // cache -- and then helps the other groups until every queue is empty.
 template <class Fn>
 __device__ __forceinline__ void for_each_unit(const BatchGeom &bg, int lane, Fn &&fn)
 {
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    if (bg.nunits <= nwarps) {                                   // a small batch: one unit per warp, no claims
+        const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+        if (c < bg.nunits) {
+            int gi = 0;
+            while (gi + 1 < bg.ngroups && c >= bg.groups[gi + 1].u0) gi++;
+            fn(bg.groups[gi], c, item_of_unit(bg.items, bg.nitems, c));
+        }
+        return;
+    }
     uint32_t smid, nsmid;
     asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
     asm volatile("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
