@@ -46,32 +46,39 @@ struct LaneWalk {
     }
 };
 
-// Position of one quad: element offset in the view and index inside the message.
-struct Quad {
-    int64_t view_off;   // element offset (view) of the quad's first value
-    int64_t e;          // index of that value inside the message (raster order)
-    int cnt;            // valid values (1..4)
+// A lane's position among the quads (4 consecutive values along x) of one
+// message: quad index in its row, row (y) and level (z).  Found by division
+// when the lane enters a message, then stepped forward 32 quads at a time
+// without dividing.
+struct QuadPos {
+    int quad, y, z;
+    __device__ __forceinline__ void set(const MsgDev &m, int64_t rel)
+    {
+        const int qpr = (m.nx + 3) >> 2;
+        const int row = (int)(rel / qpr);
+        quad = (int)(rel - (int64_t)row * qpr);
+        y = row % m.ny;
+        z = row / m.ny;
+    }
+    __device__ __forceinline__ void step32(const MsgDev &m)
+    {
+        const int qpr = (m.nx + 3) >> 2;
+        quad += 32;
+        if (quad < qpr) return;
+        int d = 1;
+        if (qpr >= 32) quad -= qpr;
+        else { d = quad / qpr; quad -= d * qpr; }
+        y += d;
+        while (y >= m.ny) { y -= m.ny; z++; }
+    }
 };
-
-__device__ __forceinline__ Quad locate(const MsgDev &m, int64_t rel, const int64_t s[3], int64_t base)
-{
-    const int qpr = (m.nx + 3) >> 2;
-    const int64_t row = rel / qpr;
-    const int quad = (int)(rel - row * qpr);
-    const int y = (int)(row % m.ny), z = (int)(row / m.ny);
-    const int x = 4 * quad;
-    Quad q;
-    q.view_off = base + (int64_t)x * s[0] + (int64_t)y * s[1] + (int64_t)z * s[2];
-    q.e = row * m.nx + x;
-    q.cnt = min(4, m.nx - x);
-    return q;
-}
 
 // MODE 0: f32 pack, 1: f32 unpack, 2: f16 pack RN, 3: f16 pack RZ, 4: f16 unpack
 template <int MODE>
 __global__ void __launch_bounds__(kThreads)
 quad_kernel(const void *__restrict__ in, void *__restrict__ out, LaunchGeom g, int layout, int view_vec)
 {
+    constexpr bool pack = (MODE == 0 || MODE == 2 || MODE == 3);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
@@ -79,55 +86,63 @@ quad_kernel(const void *__restrict__ in, void *__restrict__ out, LaunchGeom g, i
     if (u0 + lane >= u1) return;
     LaneWalk walk;
     walk.start(g.msgs, g.nmsg, u0 + lane);
+    int mi = -1;
+    QuadPos qp;
+    const int64_t *s = pack ? g.ss : g.ds;
     for (int64_t u = u0 + lane; u < u1; u += 32) {
         walk.advance(u);
         const MsgDev &m = g.msgs[walk.mi];
-        const bool pack = (MODE == 0 || MODE == 2 || MODE == 3);
-        const Quad q = locate(m, u - m.unit0, pack ? g.ss : g.ds, pack ? m.src_off : m.dst_off);
-        const int64_t vs = pack ? g.ss[0] : g.ds[0];
-        const bool vview = view_vec && q.cnt == 4 && (q.view_off & 3) == 0;
-        const bool vbuf = q.cnt == 4 && (q.e & 3) == 0;
+        if (walk.mi != mi) { mi = walk.mi; qp.set(m, u - m.unit0); }
+        const int x = 4 * qp.quad;
+        const int cnt = min(4, m.nx - x);
+        const int64_t view_off = (pack ? m.src_off : m.dst_off) + (int64_t)x * s[0] + (int64_t)qp.y * s[1] +
+                                 (int64_t)qp.z * s[2];
+        const int64_t e = ((int64_t)qp.z * m.ny + qp.y) * m.nx + x;   // index inside the message
+        const int64_t vs = s[0];
+        const bool vview = view_vec && cnt == 4 && (view_off & 3) == 0;
+        const bool vbuf = cnt == 4 && (e & 3) == 0;
+        qp.step32(m);
         float v[4];
         if (pack) {
-            const float *src = reinterpret_cast<const float *>(in) + q.view_off;
+            const float *src = reinterpret_cast<const float *>(in) + view_off;
             if (vview) {
                 const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
                 v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
             } else {
 #pragma unroll
-                for (int i = 0; i < 4; i++) v[i] = i < q.cnt ? __ldg(src + i * vs) : 0.0f;
+                for (int i = 0; i < 4; i++) v[i] = i < cnt ? __ldg(src + i * vs) : 0.0f;
             }
             if (MODE == 0) {
-                float *dst = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(out) + m.off[layout]) + q.e;
+                float *dst = reinterpret_cast<float *>(reinterpret_cast<uint8_t *>(out) + m.off[layout]) + e;
                 if (vbuf) *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
                 else
-                    for (int i = 0; i < q.cnt; i++) dst[i] = v[i];
+                    for (int i = 0; i < cnt; i++) dst[i] = v[i];
             } else {
                 __half h[4];
 #pragma unroll
                 for (int i = 0; i < 4; i++) h[i] = MODE == 2 ? __float2half_rn(v[i]) : __float2half_rz(v[i]);
-                __half *dst = reinterpret_cast<__half *>(reinterpret_cast<uint8_t *>(out) + m.off[layout]) + q.e;
+                __half *dst = reinterpret_cast<__half *>(reinterpret_cast<uint8_t *>(out) + m.off[layout]) + e;
                 if (vbuf) {
                     uint2 w;
                     w.x = (uint32_t)__half_as_ushort(h[0]) | ((uint32_t)__half_as_ushort(h[1]) << 16);
                     w.y = (uint32_t)__half_as_ushort(h[2]) | ((uint32_t)__half_as_ushort(h[3]) << 16);
                     *reinterpret_cast<uint2 *>(dst) = w;
                 } else {
-                    for (int i = 0; i < q.cnt; i++) dst[i] = h[i];
+                    for (int i = 0; i < cnt; i++) dst[i] = h[i];
                 }
             }
         } else {
             if (MODE == 1) {
-                const float *src = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(in) + m.off[layout]) + q.e;
+                const float *src = reinterpret_cast<const float *>(reinterpret_cast<const uint8_t *>(in) + m.off[layout]) + e;
                 if (vbuf) {
                     const float4 f = __ldg(reinterpret_cast<const float4 *>(src));
                     v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; i++) v[i] = i < q.cnt ? __ldg(src + i) : 0.0f;
+                    for (int i = 0; i < 4; i++) v[i] = i < cnt ? __ldg(src + i) : 0.0f;
                 }
             } else {
-                const __half *src = reinterpret_cast<const __half *>(reinterpret_cast<const uint8_t *>(in) + m.off[layout]) + q.e;
+                const __half *src = reinterpret_cast<const __half *>(reinterpret_cast<const uint8_t *>(in) + m.off[layout]) + e;
                 if (vbuf) {
                     const uint2 w = __ldg(reinterpret_cast<const uint2 *>(src));
                     v[0] = __half2float(__ushort_as_half((unsigned short)(w.x & 0xffffu)));
@@ -136,13 +151,13 @@ quad_kernel(const void *__restrict__ in, void *__restrict__ out, LaunchGeom g, i
                     v[3] = __half2float(__ushort_as_half((unsigned short)(w.y >> 16)));
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; i++) v[i] = i < q.cnt ? __half2float(src[i]) : 0.0f;
+                    for (int i = 0; i < 4; i++) v[i] = i < cnt ? __half2float(src[i]) : 0.0f;
                 }
             }
-            float *dst = reinterpret_cast<float *>(out) + q.view_off;
+            float *dst = reinterpret_cast<float *>(out) + view_off;
             if (vview) *reinterpret_cast<float4 *>(dst) = make_float4(v[0], v[1], v[2], v[3]);
             else
-                for (int i = 0; i < q.cnt; i++) dst[i * vs] = v[i];
+                for (int i = 0; i < cnt; i++) dst[i * vs] = v[i];
         }
     }
 }
