@@ -126,6 +126,20 @@ def kernel_source_sha():
     return h.hexdigest()[:16]
 
 
+def recorded_pipes(kernel_key, sha):
+    """ALU-pipe, issue-slot and DRAM utilisation (% of peak) from a committed ncu summary
+    of the same sources: the codec kernels' limiting unit."""
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
+        for line in open(f):
+            m = re.match(r"^pipes:\s*kernel=(\S+)\s+alu_pct=([\d.]+)\s+issue_pct=([\d.]+)\s+dram_pct=([\d.]+)"
+                         r"\s+source_sha=(\w+)", line.strip())
+            if m and m.group(1) == kernel_key and m.group(5) == sha:
+                return {"unit": "alu pipe (integer)", "alu_pct_of_peak": float(m.group(2)),
+                        "issue_slots_pct": float(m.group(3)), "dram_pct_of_peak": float(m.group(4)),
+                        "source": "ncu --set full, profiles/" + os.path.basename(f)}
+    return None
+
+
 def recorded_traffic(kernel_key, sha):
     """DRAM bytes per launch from a committed ncu summary of the same sources."""
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")):
@@ -486,6 +500,78 @@ def extra_pair(z, reps, peak):
     return res
 
 
+def _flushed_ms(fn, reps, flush):
+    """Mean device time of fn, each repetition after an L2 flush (a write larger
+    than L2), timed with events around fn alone."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush.fill_(1)
+        a.record()
+        fn()
+        b.record()
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
+def extra_network_model(z, xd, reps):
+    """The row transposition of the 2560 x 1280 x 137 grid at the node counts of
+    Table 1: one rank's pack-side and unpack-side kernels timed on this GPU on
+    that rank's z-pencil (lon/p x lat/p x 137, cut from the benchmark field, rows
+    padded to a multiple of 4 values, L2 flushed before each launch), the Table 1 message sizes from the plan, and
+    the communication-time model of netmodel (Dragonfly, 200 Gb/s, 1 us per
+    hop), serial as in the paper and pipelined per piece."""
+    import torch
+    from paper_2609_24294_gb300 import netmodel as nm
+    sizes = nm.message_sizes()
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")     # 256 MB > L2
+    per_rank = {}
+    for N in nm.TABLE1_N:
+        p = nm.grid_side(N)
+        nlat, nlon = 1280 // p, 2560 // p
+        pitch = (nlon + 3) // 4 * 4                  # rows start on 16 bytes, as an FFT-ready pencil would
+        pen = torch.empty(137, nlat, pitch, device="cuda")[:, :, :nlon]
+        pen.copy_(xd[:, :nlat, :nlon])
+        out = torch.empty(137, nlat, pitch, device="cuda")[:, :, :nlon]
+        plan = z.Plan.for_fields(pen, 1, 1, 0, 3)
+        t = {}
+        for s in nm.STRATEGIES:
+            r = nm.RATE_OF[s]
+            plan.prepare(r)
+            buf = torch.empty(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+            if s == "float32":
+                fp, fu = (lambda: z.zfpx_pack(plan, pen, buf)), (lambda: z.zfpx_unpack(plan, buf, out))
+            elif s == "float16":
+                fp = lambda: z.zfpx_cast_fp16_pack(plan, z.ROUND_NEAREST, pen, buf)
+                fu = lambda: z.zfpx_fp16_unpack(plan, buf, out)
+            else:
+                fp = lambda: z.zfpx_pack_compress(plan, r, pen, buf)
+                fu = lambda: z.zfpx_decompress_unpack(plan, r, buf, out)
+            t[s] = (_flushed_ms(fp, reps, flush) / 1e3, _flushed_ms(fu, reps, flush) / 1e3)
+            del buf
+        per_rank[N] = t
+        plan.close()
+        del pen, out
+    del flush
+    res = nm.model(nm.TABLE1_N, sizes, per_rank)
+    table = {}
+    for N in nm.TABLE1_N:
+        table[N] = {s: {"MiB": round(res[N][s]["message_bytes"] / 2 ** 20, 2),
+                        "pack_us": round(1e6 * res[N][s]["pack_s"], 1),
+                        "comm_us": round(1e6 * res[N][s]["comm_s"], 1),
+                        "unpack_us": round(1e6 * res[N][s]["unpack_s"], 1),
+                        "speedup_serial": round(res[N][s]["speedup_serial"], 3),
+                        "speedup_pipelined": round(res[N][s]["speedup_pipelined"], 3),
+                        "pieces": res[N][s]["pieces"]} for s in nm.STRATEGIES}
+    return {"workload": "row transposition of 2560x1280x137 f32 at N = 4..121 (p x p ranks); per-rank "
+                        "kernels timed on one rank's lon/p x lat/p x 137 pencil (row pitch a multiple of 4), L2 flushed; alpha-beta "
+                        "Dragonfly model (200 Gb/s links, 1 us/hop, injection-bound, no contention)",
+            "per_N": table,
+            "paper_speedup_N121": nm.PAPER_SPEEDUP_N121}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -580,7 +666,8 @@ def run_gpu(args):
             "decompress_r16": "decode3_r16"}[dom]
     roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["GBps"], "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": kern[dom]["GBps"] / peak,
-                "traffic": recorded_traffic(kkey, sha), "source_sha": sha}
+                "traffic": recorded_traffic(kkey, sha), "source_sha": sha,
+                "limiter": recorded_pipes(kkey, sha)}
 
     # comparators on the same field: float32 and float16 (RN) pack -> all-to-all -> unpack
     comp = {}
@@ -698,6 +785,10 @@ def run_gpu(args):
             extras["transposition_pair"] = extra_pair(z, reps, peak)
         except Exception as e:              # reported, never silently dropped
             extras["transposition_pair"] = {"error": repr(e)}
+        try:
+            extras["network_model"] = extra_network_model(z, xd, reps)
+        except Exception as e:
+            extras["network_model"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()

@@ -1,0 +1,117 @@
+"""The communication-time model of the row transposition (Sec. III-E, Sec. V-B;
+Table 1 message sizes): closed forms, limits and the pipelining bound.  Host
+only: the message sizes come from the library's plan, no kernel runs."""
+import math
+
+import pytest
+
+from paper_2609_24294_gb300 import netmodel as nm
+
+
+@pytest.fixture(scope="module")
+def sizes():
+    from paper_2609_24294_gb300 import build
+    build.build()
+    return nm.message_sizes()
+
+
+def test_machine_matches_the_paper():
+    t = nm.Dragonfly()
+    # 27 groups x 16 chassis x 4 routers x 1 node; the paper's total of 6480 nodes
+    # does not follow from these counts (only the first two groups hold N <= 121)
+    assert t.nodes == 1728
+    assert t.link_bytes_s == 25e9                       # 200 Gb/s
+    assert t.hop_s == 1e-6
+
+
+def test_hops_symmetric_and_ordered_by_distance():
+    t = nm.Dragonfly()
+    assert t.hops(5, 5) == 0
+    assert t.hops(0, 1) == 3                            # same chassis
+    assert t.hops(0, 4) == 5                            # next chassis, same group
+    assert t.hops(0, 64) == 7                           # next group
+    for a, b in ((0, 1), (3, 60), (10, 700), (1727, 0)):
+        assert t.hops(a, b) == t.hops(b, a)
+    with pytest.raises(ValueError):
+        t.hops(0, 1728)
+    t2 = nm.Dragonfly(nodes_per_router=2)
+    assert t2.hops(0, 1) == 2
+
+
+def test_table1_sizes_from_the_plan(sizes):
+    # Table 1 in MB (MiB): float32, float16, rate-16, rate-8; the two printed ties
+    # (53.125, 1.625 ...) are accepted either way.
+    table1 = {4: (212.50, 106.25, 106.25, 53.13), 9: (62.38, 31.19, 33.54, 16.77),
+              16: (26.56, 13.28, 14.06, 7.03), 25: (13.50, 6.75, 7.00, 3.50),
+              36: (7.62, 3.81, 4.23, 2.12), 49: (4.81, 2.41, 2.58, 1.29),
+              64: (3.32, 1.66, 1.95, 0.98), 81: (2.31, 1.15, 1.25, 0.62),
+              100: (1.62, 0.81, 1.00, 0.50), 121: (1.23, 0.62, 0.62, 0.31)}
+    for N, row in table1.items():
+        for s, mb in zip(nm.STRATEGIES, row):
+            assert abs(sizes[N][s] / 2 ** 20 - mb) <= 0.0051, (N, s)
+
+
+def test_alltoall_is_rounds_of_latency_plus_link_time():
+    t = nm.Dragonfly()
+    m = 1 << 20
+    # 4 ranks on one chassis: 3 rounds of (3 hops x 1 us + m / 25 GB/s)
+    assert nm.alltoall_time([0, 1, 2, 3], m, t) == pytest.approx(3 * (3e-6 + m / 25e9), rel=1e-12)
+    # without latency the exchange is (p - 1) m / beta, for any placement
+    t0 = nm.Dragonfly(hop_s=0.0)
+    for N in nm.TABLE1_N:
+        p = nm.grid_side(N)
+        assert nm.exchange_time(N, m, t0) == pytest.approx((p - 1) * m / 25e9, rel=1e-12)
+    # pieces only add latency
+    assert nm.alltoall_time([0, 1, 2, 3], m, t, pieces=4) == pytest.approx(3 * (4 * 3e-6 + m / 25e9), rel=1e-12)
+    assert nm.alltoall_time([7], m, t) == 0.0
+    with pytest.raises(ValueError):
+        nm.grid_side(8)
+
+
+def test_rows_that_cross_a_group_are_the_slowest():
+    t = nm.Dragonfly()
+    # N = 121: rows of 11 consecutive nodes; row 5 spans nodes 55..65 (groups 0 and 1)
+    slow = nm.alltoall_time(nm.row_nodes(121, 5), 1 << 20, t)
+    fast = nm.alltoall_time(nm.row_nodes(121, 0), 1 << 20, t)
+    assert slow > fast
+    assert nm.exchange_time(121, 1 << 20, t) == pytest.approx(max(
+        nm.alltoall_time(nm.row_nodes(121, r), 1 << 20, t) for r in range(11)))
+
+
+def test_pipeline_bounds():
+    for tp, tc, tu in ((1.0, 2.0, 0.5), (3.0, 0.2, 3.0), (0.0, 1.0, 0.0)):
+        ser = nm.serial_total(tp, tc, tu)
+        assert nm.pipelined_total(tp, tc, tu, 1) == pytest.approx(ser)
+        prev = ser
+        for k in (2, 4, 8, 64, 4096):
+            t = nm.pipelined_total(tp, tc, tu, k)
+            assert max(tp, tc, tu) - 1e-12 <= t <= prev + 1e-12      # never below the slowest stage
+            prev = t
+        assert nm.pipelined_total(tp, tc, tu, 10 ** 7) == pytest.approx(max(tp, tc, tu), rel=1e-5)
+
+
+def test_speedups_reduce_to_size_ratios_without_overheads(sizes):
+    zero = {N: {s: (0.0, 0.0) for s in nm.STRATEGIES} for N in nm.TABLE1_N}
+    res = nm.model(nm.TABLE1_N, sizes, zero, nm.Dragonfly(hop_s=0.0), pieces=(1,))
+    for N in nm.TABLE1_N:
+        for s in nm.STRATEGIES:
+            want = sizes[N]["float32"] / sizes[N][s]
+            assert res[N][s]["speedup_serial"] == pytest.approx(want, rel=1e-12)
+        assert res[N]["float16"]["speedup_serial"] == pytest.approx(2.0, rel=1e-12)
+    # at N = 121 the model's ceiling for rate 8 is the size ratio, 4x (Table 1: 1.23 / 0.31)
+    assert res[121]["zfp8"]["speedup_serial"] == pytest.approx(4.0, rel=1e-2)
+
+
+def test_codec_time_is_added_in_series_and_pipelining_helps(sizes):
+    per = {N: {"float32": (0.0, 0.0), "float16": (0.0, 0.0), "zfp16": (50e-6, 50e-6), "zfp8": (40e-6, 40e-6)}
+           for N in nm.TABLE1_N}
+    res = nm.model(nm.TABLE1_N, sizes, per)
+    for N in nm.TABLE1_N:
+        r = res[N]["zfp8"]
+        assert r["serial_s"] == pytest.approx(r["pack_s"] + r["comm_s"] + r["unpack_s"])
+        assert r["pipelined_s"] <= r["serial_s"]
+        assert res[N]["zfp8"]["speedup_serial"] < sizes[N]["float32"] / sizes[N]["zfp8"]
+    # with codec time on the ZFP side only, rate 16 trails float16 at every N
+    # (its messages are as large or larger, Table 1)
+    assert all(res[N]["float16"]["speedup_serial"] > res[N]["zfp16"]["speedup_serial"] for N in nm.TABLE1_N)
+    assert math.isfinite(res[121]["zfp8"]["speedup_pipelined"])
