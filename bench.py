@@ -838,6 +838,35 @@ def run_gpu(args):
     return 0
 
 
+def run_profile_case(args):
+    """A reduced workload for an ncu capture of kernels whose benchmark workload is too
+    large to capture in full: `batch` = the ten O1280 fields with every level count
+    divided by 16 (at least 1; 51 levels, 337 M values, 1.35 GB of float32), one batch
+    encode and one decode launch per repetition.  Prints one line; times nothing."""
+    import torch
+    from paper_2609_24294_gb300 import build, zfpx as z
+    from fieldgen import octahedral as og
+    build.build()
+    z.lib()
+    fields = []
+    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+        lev = max(1, nlev // 16)
+        src = og.octahedral_field(1280, lev, 300 + i, kind=kind, device="cuda")
+        fields.append((src, torch.empty_like(src), dims if lev > 1 else 1, rate))
+    lens = og.row_lengths(1280)
+    batch = z.Batch(lens, fields)
+    out = torch.empty(batch.nbytes(), dtype=torch.uint8, device="cuda")
+    for _ in range(max(1, args.steps)):
+        batch.encode(out)
+        batch.decode(out)
+    torch.cuda.synchronize()
+    nvals = sum(f[0].numel() for f in fields)
+    print(json.dumps({"profile_case": args.profile_case, "values": nvals, "stream_bytes": batch.nbytes(),
+                      "launches": 2 * max(1, args.steps)}))
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -848,7 +877,11 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-case", choices=["batch"], default=None,
+                    help="run a reduced workload for an ncu capture and exit")
     args = ap.parse_args()
+    if args.profile_case:
+        return run_profile_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
