@@ -113,7 +113,7 @@ def xform_inverse(dims, q):
 
 
 def sequency_order(dims):
-    S = 4 if dims == 1 else 64
+    S = 4 ** dims
     a = np.zeros(S, dtype=np.int32)
     lib().zfpo_sequency_order(dims, _ptr(a))
     return a

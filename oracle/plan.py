@@ -79,6 +79,8 @@ def message_bytes(m: Message, rate: int, dims: int = 3) -> int:
         return 2 * m.nvals
     if dims == 3:
         return _ceil4(m.nx) * _ceil4(m.ny) * _ceil4(m.nz) * 8 * rate
+    if dims == 2:
+        return _ceil4(m.nx) * _ceil4(m.ny) * m.nz * 2 * rate
     return (_ceil4(m.nx) * m.ny * m.nz * 4 * rate + 7) // 8
 
 

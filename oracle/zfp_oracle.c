@@ -7,7 +7,7 @@
  * transform and then reduced in precision; fixed-rate mode spends exactly r
  * bits per value, Sec. II-C and Sec. IV-B, ZFP 1.0.1) and from the cited published method
  * (Lindstrom 2014, the paper's reference for ZFP).  Where both are silent the
- * readings used are listed in the design doc and repeated at the step below.
+ * reading used is stated at the step below.
  *
  * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline / reference
  * leg may load this library.  It shares no code, header, table or constant
@@ -21,8 +21,8 @@
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * (closed forms, the published transform matrix, hand-derived golden
  * streams, brute force and invariants).  Byte compatibility with the zfp
- * 1.0.1 library itself is NOT pinned (no zfp build is available); see the
- * readings in the design doc.
+ * 1.0.1 library itself is NOT pinned (no zfp build is available); the
+ * readings at the steps below decide where the method leaves a choice.
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -144,10 +144,16 @@ void zfpo_lift_forward(int32_t v[4]) { lift_forward_int(v, 1); }
 void zfpo_lift_inverse(int32_t v[4]) { lift_inverse_int(v, 1); }
 
 /* Separable transform of a block q[i + 4j + 16k]: along axis 0 (i) for every
- * line, then axis 1 (j), then axis 2 (k).  The inverse runs axes 2, 1, 0. */
+ * line, then axis 1 (j), then axis 2 (k).  The inverse runs axes 2, 1, 0.
+ * A 2-D block q[i + 4j] has the first two axes only. */
 void zfpo_xform_forward(int dims, int32_t *q)
 {
     if (dims == 1) { lift_forward_int(q, 1); return; }
+    if (dims == 2) {
+        for (int j = 0; j < 4; j++) lift_forward_int(q + 4 * j, 1);
+        for (int i = 0; i < 4; i++) lift_forward_int(q + i, 4);
+        return;
+    }
     for (int k = 0; k < 4; k++)
         for (int j = 0; j < 4; j++) lift_forward_int(q + 4 * j + 16 * k, 1);
     for (int k = 0; k < 4; k++)
@@ -158,6 +164,11 @@ void zfpo_xform_forward(int dims, int32_t *q)
 void zfpo_xform_inverse(int dims, int32_t *q)
 {
     if (dims == 1) { lift_inverse_int(q, 1); return; }
+    if (dims == 2) {
+        for (int i = 0; i < 4; i++) lift_inverse_int(q + i, 4);
+        for (int j = 0; j < 4; j++) lift_inverse_int(q + 4 * j, 1);
+        return;
+    }
     for (int j = 0; j < 4; j++)
         for (int i = 0; i < 4; i++) lift_inverse_int(q + i + 4 * j, 16);
     for (int k = 0; k < 4; k++)
@@ -169,11 +180,11 @@ void zfpo_xform_inverse(int dims, int32_t *q)
 /* ------------------------------------------------------------------------ */
 /* Step 5: sequency order.  Coefficient (i,j,k) of a 3-D block is ranked by  */
 /* total sequency i+j+k; ties by i*i+j*j+k*k; then by i + 4j + 16k (reading). */
-/* 1-D blocks keep their natural order.                                      */
+/* A 2-D block is the same rule with k = 0.  1-D blocks keep their order.    */
 /* ------------------------------------------------------------------------ */
 void zfpo_sequency_order(int dims, int *order /* [4^dims] */)
 {
-    int S = dims == 1 ? 4 : 64;
+    int S = 1 << (2 * dims);
     for (int t = 0; t < S; t++) order[t] = t;
     if (dims == 1) return;
     /* insertion sort on the key; plain and small */
@@ -329,7 +340,7 @@ uint64_t zfpo_decode_planes(int S, const uint8_t *in, uint64_t budget, uint32_t 
 /* ------------------------------------------------------------------------ */
 static int valid_rate(int dims, int rate)
 {
-    if (dims != 1 && dims != 3) return 0;
+    if (dims < 1 || dims > 3) return 0;
     if (rate < 1 || rate > 32) return 0;
     if (dims == 1 && rate < 3) return 0;   /* 4*rate must exceed the 9-bit header */
     return 1;
@@ -337,7 +348,7 @@ static int valid_rate(int dims, int rate)
 
 static void encode_block(bitw *w, int dims, int rate, const float *v)
 {
-    const int S = dims == 1 ? 4 : 64;
+    const int S = 1 << (2 * dims);
     const uint64_t maxbits = (uint64_t)S * (uint64_t)rate;   /* step 1 */
     const uint64_t start = w->pos;
 
@@ -383,7 +394,7 @@ static void encode_block(bitw *w, int dims, int rate, const float *v)
 
 static void decode_block(bitr *r, int dims, int rate, float *v)
 {
-    const int S = dims == 1 ? 4 : 64;
+    const int S = 1 << (2 * dims);
     const uint64_t maxbits = (uint64_t)S * (uint64_t)rate;
     const uint64_t start = r->pos;
     if (!get_bit(r)) {
@@ -424,7 +435,8 @@ int zfpo_decode_block(int dims, int rate, const uint8_t *in, float *v)
 
 /* ------------------------------------------------------------------------ */
 /* Arrays.  A box of extent n[0] x n[1] x n[2] (axis 0 fastest) is read      */
-/* through element strides s[0..2].  dims == 3: 4x4x4 blocks; dims == 1:      */
+/* through element strides s[0..2].  dims == 3: 4x4x4 blocks; dims == 2: 4x4 */
+/* blocks over axes 0 and 1, each axis-2 slice on its own; dims == 1:        */
 /* 4-value blocks along axis 0.  Blocks are stored back to back in raster    */
 /* order of block indices, axis 0 fastest.  A partial block is completed by  */
 /* repeating the last value along each short axis (reading); the repeated    */
@@ -435,11 +447,12 @@ static int64_t imin64(int64_t a, int64_t b) { return a < b ? a : b; }
 int64_t zfpo_block_count(int dims, const int64_t n[3])
 {
     if (dims == 1) return ((n[0] + 3) / 4) * n[1] * n[2];
+    if (dims == 2) return ((n[0] + 3) / 4) * ((n[1] + 3) / 4) * n[2];
     return ((n[0] + 3) / 4) * ((n[1] + 3) / 4) * ((n[2] + 3) / 4);
 }
 int64_t zfpo_stream_bytes(int dims, int rate, const int64_t n[3])
 {
-    int S = dims == 1 ? 4 : 64;
+    int S = 1 << (2 * dims);
     int64_t bits = zfpo_block_count(dims, n) * S * rate;
     return (bits + 7) / 8;
 }
@@ -468,6 +481,19 @@ int zfpo_encode_array(int dims, int rate, const float *base, const int64_t n[3],
                                 v[i + 4 * j + 16 * k] = base[x * s[0] + y * s[1] + z * s[2]];
                             }
                     encode_block(&w, 3, rate, v);
+                }
+    } else if (dims == 2) {
+        int64_t by = (n[1] + 3) / 4;
+        for (int64_t z = 0; z < n[2]; z++)
+            for (int64_t yb = 0; yb < by; yb++)
+                for (int64_t xb = 0; xb < bx; xb++) {
+                    for (int j = 0; j < 4; j++)
+                        for (int i = 0; i < 4; i++) {
+                            int64_t x = imin64(4 * xb + i, n[0] - 1);
+                            int64_t y = imin64(4 * yb + j, n[1] - 1);
+                            v[i + 4 * j] = base[x * s[0] + y * s[1] + z * s[2]];
+                        }
+                    encode_block(&w, 2, rate, v);
                 }
     } else {
         for (int64_t z = 0; z < n[2]; z++)
@@ -504,6 +530,18 @@ int zfpo_decode_array(int dims, int rate, const uint8_t *in, const int64_t n[3],
                                 if (x < n[0] && y < n[1] && z < n[2])
                                     base[x * s[0] + y * s[1] + z * s[2]] = v[i + 4 * j + 16 * k];
                             }
+                }
+    } else if (dims == 2) {
+        int64_t by = (n[1] + 3) / 4;
+        for (int64_t z = 0; z < n[2]; z++)
+            for (int64_t yb = 0; yb < by; yb++)
+                for (int64_t xb = 0; xb < bx; xb++) {
+                    decode_block(&r, 2, rate, v);
+                    for (int j = 0; j < 4; j++)
+                        for (int i = 0; i < 4; i++) {
+                            int64_t x = 4 * xb + i, y = 4 * yb + j;
+                            if (x < n[0] && y < n[1]) base[x * s[0] + y * s[1] + z * s[2]] = v[i + 4 * j];
+                        }
                 }
     } else {
         for (int64_t z = 0; z < n[2]; z++)

@@ -57,10 +57,11 @@ def _lines(dims):
     """Index lines of a block along axis 0, then 1, then 2 (index i + 4j + 16k)."""
     if dims == 1:
         return [[[0, 1, 2, 3]]]
+    size = 4 ** dims
     axes = []
-    for stride in (1, 4, 16):
+    for stride in (1, 4, 16)[:dims]:
         lines = []
-        for base in range(64):
+        for base in range(size):
             if (base // stride) % 4 == 0:
                 lines.append([base + stride * t for t in range(4)])
         axes.append(lines)
@@ -68,11 +69,11 @@ def _lines(dims):
 
 
 def _order(dims):
-    """Coefficients by total sequency, then i^2+j^2+k^2, then index."""
+    """Coefficients by total sequency, then i^2+j^2+k^2, then index (k = 0 in 2-D)."""
     if dims == 1:
         return [0, 1, 2, 3]
     keys = []
-    for idx in range(64):
+    for idx in range(4 ** dims):
         i, j, k = idx % 4, (idx // 4) % 4, idx // 16
         keys.append((i + j + k, i * i + j * j + k * k, idx))
     return [key[2] for key in sorted(keys)]
@@ -192,6 +193,8 @@ def _blocks(dims, shape):
     nz, ny, nx = shape
     if dims == 1:
         return [(z, y, x) for z in range(nz) for y in range(ny) for x in range(0, nx, 4)]
+    if dims == 2:
+        return [(z, y, x) for z in range(nz) for y in range(0, ny, 4) for x in range(0, nx, 4)]
     return [(z, y, x) for z in range(0, nz, 4) for y in range(0, ny, 4) for x in range(0, nx, 4)]
 
 
@@ -199,6 +202,8 @@ def _gather(dims, a, z, y, x):
     nz, ny, nx = a.shape
     if dims == 1:
         return [a[z, y, min(x + i, nx - 1)] for i in range(4)]
+    if dims == 2:
+        return [a[z, min(y + j, ny - 1), min(x + i, nx - 1)] for j in range(4) for i in range(4)]
     return [a[min(z + k, nz - 1), min(y + j, ny - 1), min(x + i, nx - 1)]
             for k in range(4) for j in range(4) for i in range(4)]
 
@@ -224,6 +229,11 @@ def decode_array(dims, rate, stream, shape):
             for i in range(4):
                 if x + i < nx:
                     out[z, y, x + i] = vals[i]
+        elif dims == 2:
+            for j in range(4):
+                for i in range(4):
+                    if y + j < ny and x + i < nx:
+                        out[z, y + j, x + i] = vals[4 * j + i]
         else:
             for k in range(4):
                 for j in range(4):
