@@ -500,6 +500,33 @@ def extra_pair(z, reps, peak):
     return res
 
 
+def extra_blocks_2d(z, xd, reps, peak):
+    """The benchmark field and plan (1280 x 640 x 137, 8 x 8 ranks, z->lambda) coded
+    with 2-D blocks (4 x 4 values of one level, the block shape for single-level
+    fields) instead of 3-D blocks: per-kernel time, throughput and error."""
+    import torch
+    plan = z.Plan.for_fields(xd, PR, PC, 0, 2)
+    fbytes = 4 * xd.numel()
+    x64 = xd.double()
+    res = {"workload": "1280x640x137 f32, 8x8 ranks, z->lambda, 2-D blocks (each level on its own)"}
+    for r in RATES:
+        plan.prepare(r)
+        send = torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        out = torch.empty_like(xd)
+        tc = _events_ms(lambda: z.zfpx_pack_compress(plan, r, xd, send), reps)
+        td = _events_ms(lambda: z.zfpx_decompress_unpack(plan, r, send, out, layout=z.LAYOUT_SEND), reps)
+        moved = fbytes + plan.buffer_bytes(r)
+        res["r%d" % r] = {"compress_ms": tc, "decompress_ms": td,
+                          "compress_f32_GBps": fbytes / (tc / 1e3) / 1e9,
+                          "decompress_f32_GBps": fbytes / (td / 1e3) / 1e9,
+                          "compress_frac_of_measured_hbm": moved / (tc / 1e3) / 1e9 / peak,
+                          "decompress_frac_of_measured_hbm": moved / (td / 1e3) / 1e9 / peak,
+                          "rel_l2": float((out.double() - x64).norm() / x64.norm())}
+        del send, out
+    plan.close()
+    return res
+
+
 def _flushed_ms(fn, reps, flush):
     """Mean device time of fn, each repetition after an L2 flush (a write larger
     than L2), timed with events around fn alone."""
@@ -789,6 +816,10 @@ def run_gpu(args):
             extras["network_model"] = extra_network_model(z, xd, reps)
         except Exception as e:
             extras["network_model"] = {"error": repr(e)}
+        try:
+            extras["blocks_2d"] = extra_blocks_2d(z, xd, reps, peak)
+        except Exception as e:
+            extras["blocks_2d"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()

@@ -111,8 +111,10 @@ ZFPX_API uint64_t zfpx_launch_count(void);
  *     lon_l (lon split in p_r) x lat_j x lev_k.
  * `src` describes the field the packs read (all simulated ranks' pencils
  * together, as one array); `dst` the field the unpacks write; their
- * extents must be equal, strides may differ.  dims = 3 (4x4x4 blocks) or 1
- * (4 values along longitude).  Every message starts at a multiple of 256
+ * extents must be equal, strides may differ.  dims = 3 (4x4x4 blocks), 2
+ * (4x4 blocks over longitude and latitude, every level on its own: the block
+ * shape for single-level fields, coded like the 3-D blocks with one axis
+ * fewer, 16 r bits each) or 1 (4 values along longitude).  Every message starts at a multiple of 256
  * bytes in both layouts.  The plan is host-side; device tables are built on
  * first use per rate (or by zfpx_plan_prepare, which should precede any
  * stream capture).  *out receives a plan owned by the caller, freed with
@@ -181,8 +183,10 @@ ZFPX_API int zfpx_permute(zfpx_plan plan, int rate, const void *d_send, void *d_
 
 /* ---- raw codec on one array (Sec. II-C) ------------------------------------
  * Encodes the array of extents n[] read through element strides stride[]
- * into d_out (cap bytes, at least zfpx_stream_bytes).  dims 1 or 3,
- * rate 8 or 16.  Errors: ZFPX_EINVAL, ZFPX_ESIZE, ZFPX_ECUDA. */
+ * into d_out (cap bytes, at least zfpx_stream_bytes).  dims 1, 2 or 3,
+ * rate 8 or 16; blocks back to back in raster order of block indices (axis 0
+ * fastest; for dims 2 each level's blocks in turn).  Errors: ZFPX_EINVAL,
+ * ZFPX_ESIZE, ZFPX_ECUDA. */
 ZFPX_API size_t zfpx_stream_bytes(int dims, int rate, const int64_t n[3]);
 ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3],
                 const int64_t stride[3], uint8_t *d_out, size_t cap, void *stream);

@@ -3,7 +3,7 @@
 // The codec is ZFP's fixed-rate mode as the paper uses it (Sec. II-C: 4^d
 // blocks coded independently by a lifting transform and precision
 // reduction; Sec. IV-B: rate 8 and 16, fixed message size), in the readings
-// stated in include/zfpx.h and the design doc:
+// stated in include/zfpx.h:
 //   e_max = frexp exponent of max|x|; zero block if max|x| is 0, subnormal or
 //   non-finite; q = trunc(x 2^(30-e_max)); five-step integer lifting along
 //   x, y, z; coefficients in total-sequency order; negabinary; group-tested
@@ -317,6 +317,133 @@ decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
     }
 }
 
+// ================================================================= 2-D kernels
+// Blocks of 4 x 4 values over axes 0 and 1 of one level; one lane per block,
+// a warp takes 32 consecutive blocks of one message (units split statically
+// over the warps).  A block's stream is RATE / 4 64-bit words, staged in a
+// swizzled [word][lane] shared tile and moved with coalesced 8-byte accesses.
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+encode2_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
+{
+    constexpr int NW = RATE / 4;
+    __shared__ uint64_t smem[kWarps][(NW + 2) * 32];
+    __shared__ uint32_t splanes[kWarps][32 * 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint64_t *wsm = smem[wid];
+    SmemPlanes16 pl{splanes[wid], lane};
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t b0 = (c - m.unit0) * 32;
+        const int nact = (int)min((int64_t)32, m.nblocks - b0);
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        if (lane < nact) {
+            const int nx = m.nx, ny = m.ny, bxn = m.bx, byn = m.by;
+            const int b = (int)b0 + lane;
+            const int bxi = b % bxn, t = b / bxn;
+            const int byi = t % byn, z = t / byn;
+            const int x0 = 4 * bxi, y0 = 4 * byi;
+            const float *base = src + m.src_off + (int64_t)z * g.ss[2];
+            float x[16];
+            if (vec && x0 + 4 <= nx) {
+                // four 16-byte row loads (rows past the box repeat its last row)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(
+                        base + (int64_t)min(y0 + j, ny - 1) * g.ss[1] + x0));
+                    x[4 * j] = f.x; x[4 * j + 1] = f.y; x[4 * j + 2] = f.z; x[4 * j + 3] = f.w;
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < 16; r++) {
+                    const int i = r & 3, j = r >> 2;
+                    x[r] = __ldg(base + (int64_t)min(y0 + j, ny - 1) * g.ss[1] + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
+                }
+            }
+            SmemWriter<NW> wr{wsm, 0ull, 0, 0, lane};
+            encode_block2<RATE>(x, wr, pl);
+        }
+        __syncwarp();
+        uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * NW;
+        for (int idx = lane; idx < nact * NW; idx += 32) {
+            const int l = idx / NW, w = idx % NW;
+            dst[idx] = wsm[w * 32 + (l ^ w)];
+        }
+        __syncwarp();
+    }
+}
+
+template <int RATE>
+__global__ void __launch_bounds__(kThreads)
+decode2_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
+{
+    constexpr int NW = RATE / 4;              // 64-bit words per block
+    constexpr int ZR = 3;                     // zero rows after the stream
+    __shared__ uint32_t stile[kWarps][(2 * NW + ZR) * 32];
+    __shared__ uint32_t splanes[kWarps][32 * 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t *t32 = stile[wid];
+    SmemPlanes16 pl{splanes[wid], lane};
+    const StreamTile tile{t32, lane};
+#pragma unroll
+    for (int r = 0; r < ZR; r++) t32[(2 * NW + r) * 32 + lane] = 0u;
+    const int64_t W = (int64_t)gridDim.x * kWarps;
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
+    int64_t c = gw * g.nunits / W;
+    const int64_t c1 = (gw + 1) * g.nunits / W;
+    if (c >= c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, c);
+    for (; c < c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
+        const int64_t b0 = (c - m.unit0) * 32;
+        const int nact = (int)min((int64_t)32, m.nblocks - b0);
+        if (lane >= nact) continue;
+        const int nx = m.nx, ny = m.ny, bxn = m.bx, byn = m.by;
+        const int64_t boff = layout ? m.off[1] : m.off[0];
+        const int b = (int)b0 + lane;
+        // this lane's block: NW / 2 16-byte loads into its own tile column
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(in + boff) + (int64_t)b * (NW / 2);
+#pragma unroll
+        for (int i = 0; i < NW / 2; i++) {
+            const uint4 v = __ldg(src4 + i);
+            t32[(4 * i) * 32 + lane] = v.x;
+            t32[(4 * i + 1) * 32 + lane] = v.y;
+            t32[(4 * i + 2) * 32 + lane] = v.z;
+            t32[(4 * i + 3) * 32 + lane] = v.w;
+        }
+        float v[16];
+        decode_block2_tile<RATE>(tile, v, pl);
+        const int bxi = b % bxn, t = b / bxn;
+        const int byi = t % byn, z = t / byn;
+        const int x0 = 4 * bxi, y0 = 4 * byi;
+        float *base = dstf + m.dst_off + (int64_t)z * g.ds[2];
+        if (vec && x0 + 4 <= nx) {
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+                if (y0 + j < ny)
+                    *reinterpret_cast<float4 *>(base + (int64_t)(y0 + j) * g.ds[1] + x0) =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 16; r++) {
+                const int i = r & 3, j = r >> 2;
+                if (x0 + i < nx && y0 + j < ny)
+                    base[(int64_t)(y0 + j) * g.ds[1] + (int64_t)(x0 + i) * g.ds[0]] = v[r];
+            }
+        }
+    }
+}
+
 // ================================================================= launch
 template <class K>
 int grid_for(K kernel, int64_t nunits, int warps = kWarps)
@@ -350,6 +477,9 @@ int launch_encode(int dims, int rate, const float *src, uint8_t *out, const Laun
         else
             encode3_kernel<16><<<grid_for(encode3_kernel<16>, g.nunits, kEnc3Warps<16>), 32 * kEnc3Warps<16>, 0,
                                  st>>>(src, out, g, layout, vec);
+    } else if (dims == 2) {
+        if (rate == 8) encode2_kernel<8><<<grid_for(encode2_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
+        else encode2_kernel<16><<<grid_for(encode2_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
     } else {
         if (rate == 8) encode1_kernel<8><<<grid_for(encode1_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
         else encode1_kernel<16><<<grid_for(encode1_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
@@ -369,6 +499,9 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
         else
             decode3_kernel<16><<<grid_for(decode3_kernel<16>, g.nunits, kDec3Warps<16>), 32 * kDec3Warps<16>, 0,
                                  st>>>(in, dst, g, layout, vec);
+    } else if (dims == 2) {
+        if (rate == 8) decode2_kernel<8><<<grid_for(decode2_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
+        else decode2_kernel<16><<<grid_for(decode2_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
     } else {
         if (rate == 8) decode1_kernel<8><<<grid_for(decode1_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
         else decode1_kernel<16><<<grid_for(decode1_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
@@ -420,10 +553,11 @@ int zfpx_decompress_unpack(zfpx_plan p, int rate, const uint8_t *d_in, size_t le
 
 size_t zfpx_stream_bytes(int dims, int rate, const int64_t n[3])
 {
-    if (!n || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return 0;
+    if (!n || dims < 1 || dims > 3 || !valid_codec_rate(rate)) return 0;
     for (int a = 0; a < 3; a++) if (n[a] < 1) return 0;
     const int64_t bx = (n[0] + 3) / 4;
     if (dims == 3) return (size_t)(bx * ((n[1] + 3) / 4) * ((n[2] + 3) / 4) * 8 * rate);
+    if (dims == 2) return (size_t)(bx * ((n[1] + 3) / 4) * n[2] * 2 * rate);
     return (size_t)(bx * n[1] * n[2] * rate / 2);
 }
 
@@ -465,7 +599,7 @@ extern "C" {
 int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3], const int64_t stride[3],
                 uint8_t *d_out, size_t cap, void *stream)
 {
-    if (!d_in || !d_out || !n || !stride || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    if (!d_in || !d_out || !n || !stride || dims < 1 || dims > 3 || !valid_codec_rate(rate)) return ZFPX_EINVAL;
     for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
     if (cap < zfpx_stream_bytes(dims, rate, n)) return ZFPX_ESIZE;
     zfpx_plan p = nullptr;
@@ -477,7 +611,7 @@ int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3], const
 int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3], const int64_t stride[3],
                 float *d_out, void *stream)
 {
-    if (!d_in || !d_out || !n || !stride || (dims != 1 && dims != 3) || !valid_codec_rate(rate)) return ZFPX_EINVAL;
+    if (!d_in || !d_out || !n || !stride || dims < 1 || dims > 3 || !valid_codec_rate(rate)) return ZFPX_EINVAL;
     for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
     if (len < zfpx_stream_bytes(dims, rate, n)) return ZFPX_ESIZE;
     zfpx_plan p = nullptr;
@@ -556,7 +690,7 @@ extern "C" int zfpx_transpose_noalloc(zfpx_plan p, int rate, const float *d_src,
         const HostMsg &m = p->msgs[i];
         MsgDev &d = h[i];
         const int64_t bx = (m.nx + 3) / 4;
-        const int64_t by = p->dims == 3 ? (m.ny + 3) / 4 : m.ny;
+        const int64_t by = p->dims >= 2 ? (m.ny + 3) / 4 : m.ny;
         const int64_t bz = p->dims == 3 ? (m.nz + 3) / 4 : m.nz;
         d.src_off = m.x0 * p->ss[0] + m.y0 * p->ss[1] + m.z0 * p->ss[2];
         d.dst_off = m.x0 * p->ds[0] + m.y0 * p->ds[1] + m.z0 * p->ds[2];

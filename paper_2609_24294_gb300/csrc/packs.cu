@@ -179,7 +179,7 @@ permute_kernel(const uint8_t *__restrict__ send, uint8_t *__restrict__ recv, Lau
         const int64_t nv = (int64_t)m.nx * m.ny * m.nz;
         const int64_t bytes = rate == ZFPX_RATE_F32 ? 4 * nv
                             : rate == ZFPX_RATE_F16 ? 2 * nv
-                            : (dims == 3 ? m.nblocks * 8 * rate : m.nblocks * rate / 2);
+                            : (dims == 3 ? m.nblocks * 8 * rate : dims == 2 ? m.nblocks * 2 * rate : m.nblocks * rate / 2);
         const int64_t o = (u - m.unit0) * 16;
         const uint8_t *a = send + m.off[0] + o;
         uint8_t *b = recv + m.off[1] + o;

@@ -53,6 +53,7 @@ static void block_counts(int dims, const HostMsg &m, int64_t b[3])
 {
     b[0] = ceil4(m.nx);
     if (dims == 3) { b[1] = ceil4(m.ny); b[2] = ceil4(m.nz); }
+    else if (dims == 2) { b[1] = ceil4(m.ny); b[2] = m.nz; }
     else { b[1] = m.ny; b[2] = m.nz; }
 }
 
@@ -64,7 +65,7 @@ int64_t message_bytes(const zfpx_plan_s *p, const HostMsg &m, int rate)
     int64_t b[3];
     block_counts(p->dims, m, b);
     const int64_t nb = b[0] * b[1] * b[2];
-    return p->dims == 3 ? nb * 8 * rate : nb * rate / 2;
+    return p->dims == 3 ? nb * 8 * rate : p->dims == 2 ? nb * 2 * rate : nb * rate / 2;
 }
 
 // Offsets of every message (send order index) in the given layout.
@@ -190,7 +191,7 @@ int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *ds
     *out = nullptr;
     if (pr < 1 || pc < 1 || (long long)pr * pc > (1 << 20)) return ZFPX_EINVAL;
     if (transposition != 0 && transposition != 1) return ZFPX_EINVAL;
-    if (dims != 1 && dims != 3) return ZFPX_EINVAL;
+    if (dims < 1 || dims > 3) return ZFPX_EINVAL;
     if (split_mode != ZFPX_SPLIT_BALANCED && split_mode != ZFPX_SPLIT_TABLE1) return ZFPX_EINVAL;
     for (int a = 0; a < 3; a++) {
         if (src->n[a] < 1 || src->n[a] != dst->n[a] || src->n[a] > (int64_t)1 << 31) return ZFPX_EINVAL;

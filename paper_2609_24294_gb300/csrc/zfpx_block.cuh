@@ -706,6 +706,134 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
     }
 }
 
+// ----------------------------------------------------------------- 2-D block
+// A 2-D block is 4 x 4 values x[i + 4j] (i along axis 0, j along axis 1) of
+// one level, coded into exactly 16 RATE bits (128 at rate 8, 256 at rate 16).
+// Transform: the lifting along i for every j, then along j for every i.
+// Coefficient (i + 4j) coded at position t: total sequency i + j ascending,
+// ties by i^2 + j^2, then by the index (the 3-D rule with k = 0).
+#define ZFPX_SEQ2 {0, 1, 4, 5, 2, 8, 6, 9, 3, 12, 10, 7, 13, 11, 14, 15}
+
+ZFPX_HD void xform2_fwd(int32_t (&q)[16])
+{
+#pragma unroll
+    for (int j = 0; j < 4; j++) lift_fwd(q[4 * j], q[4 * j + 1], q[4 * j + 2], q[4 * j + 3]);
+#pragma unroll
+    for (int i = 0; i < 4; i++) lift_fwd(q[i], q[i + 4], q[i + 8], q[i + 12]);
+}
+
+ZFPX_HD void xform2_inv(int32_t (&q)[16])
+{
+#pragma unroll
+    for (int i = 0; i < 4; i++) lift_inv(q[i], q[i + 4], q[i + 8], q[i + 12]);
+#pragma unroll
+    for (int j = 0; j < 4; j++) lift_inv(q[4 * j], q[4 * j + 1], q[4 * j + 2], q[4 * j + 3]);
+}
+
+// Encodes x[i + 4j] into 16 RATE bits.  The 16 coefficients' bit planes come
+// from one 32x32 transpose whose lower 16 rows are zero (the coefficients sit
+// in rows 16..31, so plane k is the high 16 bits of word k and the stages
+// below 16 only touch the upper rows), parked in the lane's plane slots; then
+// one group-tested plane after another until the budget is spent.  Writer: put(bits, len),
+// finish() (flush and zero-fill).  Planes: store_half(k, 0, w) /
+// load_half(k, 0), 32 slots of 32 bits.
+template <int RATE, class Writer, class Planes>
+ZFPX_HD void encode_block2(const float (&x)[16], Writer &wr, Planes &pl)
+{
+    constexpr int kSeq[16] = ZFPX_SEQ2;
+    uint32_t amax = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) {
+        const uint32_t a = f2u(x[i]) & 0x7fffffffu;
+        amax = a > amax ? a : amax;
+    }
+    const int E = (int)(amax >> 23);
+    if (amax < 0x00400000u || E == 255) { wr.finish(); return; }
+    const QuantScale qs(E);
+    int32_t q[16];
+#pragma unroll
+    for (int i = 0; i < 16; i++) q[i] = qs(x[i]);
+    xform2_fwd(q);
+    uint32_t w[32];
+#pragma unroll
+    for (int t = 0; t < 16; t++) w[16 + t] = to_negabinary(q[kSeq[t]]);
+    transpose32_zero_low<16>(w);
+#pragma unroll
+    for (int k = 0; k < 32; k++) pl.store_half(k, 0, w[k] >> 16);
+    wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
+    int n = 0, R = 16 * RATE - 9;
+#pragma unroll 1
+    for (int k = 31; k >= 0 && R > 0; k--) code_plane<16>(wr, (uint64_t)pl.load_half(k, 0), n, R);
+    wr.finish();
+}
+
+// Reader over a stream tile: peek() = the 64 bits from the current position.
+template <class Tile>
+struct TileReader {
+    const Tile &t;
+    int pos;
+    ZFPX_HD uint64_t peek() const { return tile_peek(t, pos); }
+    ZFPX_HD void skip(int k) { pos += k; }
+};
+
+// Decodes one 2-D block from this lane's stream tile (2 RATE / 4 words of 32
+// bits, then at least two zero words).  Planes below the last one the budget
+// reached stay zero.
+template <int RATE, class Tile, class Planes>
+ZFPX_HD void decode_block2_tile(const Tile &tile, float (&x)[16], Planes &pl)
+{
+    constexpr int kSeq[16] = ZFPX_SEQ2;
+    const uint64_t head = tile_peek(tile, 0);
+    if (!(head & 1ull)) {
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = 0.0f;
+        return;
+    }
+    const int e = (int)((head >> 1) & 0xffu);
+    TileReader<Tile> rd{tile, 9};
+    int n = 0, R = 16 * RATE - 9, kmin = 32;
+#pragma unroll 1
+    for (int k = 31; k >= 0 && R > 0; k--) {
+        pl.store_half(k, 0, (uint32_t)decode_plane<16>(rd, n, R));
+        kmin = k;
+    }
+    // Planes below kmin are zero; when planes 0..15 are zero in every lane of
+    // the warp, the transpose stages below 16 skip them.
+    uint32_t w[32];
+#ifdef __CUDA_ARCH__
+    const bool low_zero = __all_sync(__activemask(), kmin >= 16);
+#else
+    const bool low_zero = kmin >= 16;
+#endif
+    if (low_zero) {
+#pragma unroll
+        for (int k = 16; k < 32; k++) w[k] = k >= kmin ? pl.load_half(k, 0) : 0u;
+        transpose32_zero_low<16>(w);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 32; k++) w[k] = k >= kmin ? pl.load_half(k, 0) : 0u;
+        transpose32(w);
+    }
+    int32_t q[16];
+#pragma unroll
+    for (int t = 0; t < 16; t++) q[kSeq[t]] = from_negabinary(w[t]);
+    xform2_inv(q);
+    if (e >= 31) {
+        const float sc = dequant_scale(e);
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = dequantize_fast(q[i], sc);
+    } else {
+        // tiny exponents (rare): a rolled loop over a local copy
+        int32_t t[16];
+#pragma unroll
+        for (int i = 0; i < 16; i++) t[i] = q[i];
+#pragma unroll 1
+        for (int i = 0; i < 16; i++) t[i] = (int32_t)f2u(dequantize_small(t[i], e));
+#pragma unroll
+        for (int i = 0; i < 16; i++) x[i] = u2f((uint32_t)t[i]);
+    }
+}
+
 // ----------------------------------------------------------------- 1-D block
 // A 1-D block is 4 RATE <= 64 bits, returned in one word (LSB = first bit).
 struct RegWriter {

@@ -68,6 +68,15 @@ struct SmemPlanes {
     }
 };
 
+// 32-bit bit planes (2-D blocks: 16 coefficients) in this lane's column of a
+// [plane][lane] tile; the same interface as the low half of SmemPlanes.
+struct SmemPlanes16 {
+    uint32_t *sm;
+    int lane;
+    __device__ __forceinline__ void store_half(int k, int, uint32_t v) { sm[k * 32 + lane] = v; }
+    __device__ __forceinline__ uint32_t load_half(int k, int) const { return sm[k * 32 + lane]; }
+};
+
 // Stream tile of one warp: 32-bit words in a [word][lane] layout (word i of
 // lane l at i * 32 + l), so every lane reads its own column without bank
 // conflicts; two zero rows follow the stream, so the 64-bit window read at

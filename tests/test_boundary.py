@@ -43,7 +43,7 @@ def test_library_plan_reproduces_table1(zfpx, N):
 
 
 @pytest.mark.parametrize("t", [0, 1])
-@pytest.mark.parametrize("dims", [1, 3])
+@pytest.mark.parametrize("dims", [1, 2, 3])
 @pytest.mark.parametrize("shape,pr,pc", [((37, 23, 17), 3, 2), ((64, 32, 8), 2, 2), ((5, 3, 1), 2, 3),
                                          ((1280, 640, 137), 8, 8)])
 def test_library_plan_matches_oracle_plan(zfpx, t, dims, shape, pr, pc):
@@ -65,7 +65,7 @@ def test_library_plan_matches_oracle_plan(zfpx, t, dims, shape, pr, pc):
 
 def test_plan_rejects_bad_arguments(zfpx):
     for args in [((0, 4, 4), 1, 1, 0, 3), ((4, 4, 4), 0, 1, 0, 3), ((4, 4, 4), 1, 1, 2, 3),
-                 ((4, 4, 4), 1, 1, 0, 2)]:
+                 ((4, 4, 4), 1, 1, 0, 4), ((4, 4, 4), 1, 1, 0, 0)]:
         with pytest.raises(zfpx.ZfpxError) as e:
             zfpx.Plan(*args)
         assert e.value.code == -1
@@ -89,8 +89,10 @@ def test_calls_reject_bad_arguments_before_any_launch(zfpx):
     assert L.zfpx_pack(h, ctypes.c_void_p(256), ctypes.c_void_p(4096), 16, 0, None) == -2
     n = (ctypes.c_int64 * 3)(8, 8, 8)
     s = (ctypes.c_int64 * 3)(1, 8, 64)
-    assert L.zfpx_encode(2, 8, ctypes.c_void_p(256), n, s, ctypes.c_void_p(4096), 1 << 20, None) == -1
+    assert L.zfpx_encode(4, 8, ctypes.c_void_p(256), n, s, ctypes.c_void_p(4096), 1 << 20, None) == -1
+    assert L.zfpx_encode(2, 8, ctypes.c_void_p(256), n, s, ctypes.c_void_p(4096), 10, None) == -2
     assert L.zfpx_encode(3, 8, ctypes.c_void_p(256), n, s, ctypes.c_void_p(4096), 10, None) == -2
     assert zfpx.zfpx_launch_count() == before
     assert zfpx.zfpx_stream_bytes(3, 8, (8, 8, 8)) == 8 * 64
     assert zfpx.zfpx_stream_bytes(1, 8, (9, 2, 3)) == 3 * 2 * 3 * 4
+    assert zfpx.zfpx_stream_bytes(2, 8, (9, 6, 3)) == 3 * 2 * 3 * 16

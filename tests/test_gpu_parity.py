@@ -52,7 +52,7 @@ def smooth_field(shape, seed, offset=0.0):
 
 
 # ---------------------------------------------------------------- raw arrays
-@pytest.mark.parametrize("dims", [3, 1])
+@pytest.mark.parametrize("dims", [3, 2, 1])
 @pytest.mark.parametrize("rate", [16, 8])
 def test_config1_raw_codec(z, dims, rate):
     f = fieldgen.config1_field()                   # 64 lon x 32 lat x 8 levels
@@ -71,7 +71,7 @@ def test_config1_raw_codec(z, dims, rate):
 
 
 @pytest.mark.parametrize("shape", [(1, 1, 1), (1, 3, 5), (7, 5, 3), (2, 9, 33), (17, 6, 130)])
-@pytest.mark.parametrize("dims", [3, 1])
+@pytest.mark.parametrize("dims", [3, 2, 1])
 def test_small_and_ragged_arrays(z, shape, dims):
     x = smooth_field(shape, 3, offset=10.0)
     n = tuple(reversed(shape))
@@ -108,7 +108,7 @@ def _special_values(shape, seed):
 def test_special_values(z):
     x = _special_values((8, 12, 16), 5)
     n = (16, 12, 8)
-    for dims in (3, 1):
+    for dims in (3, 2, 1):
         for rate in (8, 16):
             out = torch.zeros(z.zfpx_stream_bytes(dims, rate, n), dtype=torch.uint8, device="cuda")
             z.zfpx_encode(dims, rate, dev(x), out)
@@ -172,7 +172,7 @@ def test_random_streams_decode_like_oracle(z):
     # the decoder is defined on any byte stream
     rng = np.random.default_rng(11)
     n = (32, 8, 8)
-    for dims in (3, 1):
+    for dims in (3, 2, 1):
         for rate in (8, 16):
             nb = z.zfpx_stream_bytes(dims, rate, n)
             s = rng.integers(0, 256, nb, dtype=np.uint8)
@@ -213,7 +213,7 @@ PLANS = [((17, 23, 37), 3, 2), ((8, 32, 64), 2, 2), ((5, 9, 11), 2, 3), ((20, 16
 
 
 @pytest.mark.parametrize("t", [0, 1])
-@pytest.mark.parametrize("dims", [3, 1])
+@pytest.mark.parametrize("dims", [3, 2, 1])
 @pytest.mark.parametrize("shape,pr,pc", PLANS)
 def test_pack_compress_permute_decompress(z, t, dims, shape, pr, pc):
     x = smooth_field(shape, 7, offset=250.0)
@@ -292,12 +292,13 @@ def test_strided_sources(z):
     alt = alt_store.permute(0, 2, 1)
     for s in (src, alt):
         nz, ny, nx = x.shape
-        oplan = opl.Plan(nx, ny, nz, 2, 2, 0, 3)
-        plan = z.Plan.for_fields(s, 2, 2, 0, 3)
-        for rate in (8, 16):
-            send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
-            z.zfpx_pack_compress(plan, rate, s, send)
-            assert host(send).tobytes() == op.pack(oplan, rate, x).tobytes()
+        for dims in (3, 2):
+            oplan = opl.Plan(nx, ny, nz, 2, 2, 0, dims)
+            plan = z.Plan.for_fields(s, 2, 2, 0, dims)
+            for rate in (8, 16):
+                send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
+                z.zfpx_pack_compress(plan, rate, s, send)
+                assert host(send).tobytes() == op.pack(oplan, rate, x).tobytes()
     del rng
 
 
@@ -307,16 +308,17 @@ def config2():
     return fieldgen.config2_field()
 
 
+@pytest.mark.parametrize("dims", [3, 2])
 @pytest.mark.parametrize("rate", [8, 16])
-def test_config2_full_size_sampled(z, config2, rate):
+def test_config2_full_size_sampled(z, config2, rate, dims):
     """1280 x 640 x 137, 8 x 8 ranks, z->lambda: the launch the benchmark
     times, checked message by message on a sample (the oracle codes one
     message in well under a second) and as a whole by invariants."""
     x = config2
     xd = dev(x)
     nz, ny, nx = x.shape
-    plan = z.Plan.for_fields(xd, 8, 8, 0, 3)
-    oplan = opl.Plan(nx, ny, nz, 8, 8, 0, 3)
+    plan = z.Plan.for_fields(xd, 8, 8, 0, dims)
+    oplan = opl.Plan(nx, ny, nz, 8, 8, 0, dims)
     send = torch.zeros(plan.buffer_bytes(rate), dtype=torch.uint8, device="cuda")
     z.zfpx_pack_compress(plan, rate, xd, send)
     recv = torch.zeros_like(send)
@@ -333,14 +335,14 @@ def test_config2_full_size_sampled(z, config2, rate):
     sample = [oplan.messages[0], oplan.messages[-1]] + [oplan.messages[i] for i in
                                                         rng.choice(len(oplan.messages), 4, replace=False)]
     for m in sample:
-        nb = opl.message_bytes(m, rate, 3)
+        nb = opl.message_bytes(m, rate, dims)
         ref = op.message_stream(oplan, rate, x, m)
         o = so[(m.src, m.dst)]
         assert hs[o:o + nb].tobytes() == ref.tobytes(), (m.src, m.dst)
         box = np.empty((m.nz, m.ny, m.nx), dtype=np.float32)
-        oc.decode_array(3, rate, ref, box)
+        oc.decode_array(dims, rate, ref, box)
         same_bits(ho[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx], box)
     # whole field: every value written, finite, within the rate's accuracy
     assert np.isfinite(ho).all()
     rel = np.linalg.norm(ho.astype(np.float64) - x) / np.linalg.norm(x.astype(np.float64))
-    assert rel < (5e-3 if rate == 8 else 5e-5)
+    assert rel < ((5e-3 if rate == 8 else 5e-5) if dims == 3 else (2e-2 if rate == 8 else 2e-4))
