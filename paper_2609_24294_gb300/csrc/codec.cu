@@ -100,9 +100,14 @@ struct UnitClaim {
 };
 
 // ================================================================= 3-D kernels
-template <int RATE>
+// VEC: every block's rows start on 16 bytes (the view's row and level strides
+// and every message's x origin are multiples of 4 values, the base aligned),
+// so full rows move as 16-byte loads and stores.  Otherwise a separate
+// instantiation reads and writes the rows of x-complete blocks as four scalar
+// accesses each, unrolled, keeping the vector kernel's code as it is.
+template <int RATE, bool VEC>
 __global__ void __launch_bounds__(32 * kEnc3Warps<RATE>)
-encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
+encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout)
 {
     __shared__ uint64_t smem[kEnc3Warps<RATE>][(RATE + 2) * 32];
     __shared__ uint64_t splanes[kEnc3Warps<RATE>][32 * 32];
@@ -126,7 +131,7 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
             const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
             const float *base = src + src_off;
             float x[64];
-            if (vec && x0 + 4 <= nx) {
+            if (VEC && x0 + 4 <= nx) {
                 // the common case: sixteen 16-byte row loads (rows past the
                 // end of the box repeat its last row)
 #pragma unroll
@@ -140,8 +145,20 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
                         x[16 * k + 4 * j + 2] = f.z; x[16 * k + 4 * j + 3] = f.w;
                     }
                 }
+            } else if (!VEC && x0 + 4 <= nx) {
+                // rows not on 16 bytes: four scalar loads per row
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int64_t zo = (int64_t)min(z0 + k, nz - 1) * g.ss[2];
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const float *row = base + zo + (int64_t)min(y0 + j, ny - 1) * g.ss[1] + (int64_t)x0 * g.ss[0];
+#pragma unroll
+                        for (int i = 0; i < 4; i++) x[16 * k + 4 * j + i] = __ldg(row + (int64_t)i * g.ss[0]);
+                    }
+                }
             } else {
-                // partial in x or unaligned: element loads through a local
+                // partial in x: element loads through a local
                 // array, kept rolled so the hot path's code stays compact
                 float t[64];
 #pragma unroll 1
@@ -167,9 +184,9 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
     cl.finish();
 }
 
-template <int RATE>
+template <int RATE, bool VEC>
 __global__ void __launch_bounds__(32 * kDec3Warps<RATE>, kDec3MinBlocks<RATE>)
-decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
+decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout)
 {
     __shared__ uint32_t stile[kDec3Warps<RATE>][(2 * RATE + kTileZeroRows<RATE>) * 32];
     __shared__ uint64_t splanes[kDec3Warps<RATE>][32 * 32];
@@ -207,7 +224,7 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
             float v[64];
             decode_block3_tile<RATE>(tile, v, pl);
             float *base = dstf + dst_off;
-            if (vec && x0 + 4 <= nx) {
+            if (VEC && x0 + 4 <= nx) {
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
 #pragma unroll
@@ -216,6 +233,19 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
                         if (z0 + k < nz && y0 + j < ny)
                             *reinterpret_cast<float4 *>(row) = make_float4(v[16 * k + 4 * j], v[16 * k + 4 * j + 1],
                                                                            v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+                    }
+                }
+            } else if (!VEC && x0 + 4 <= nx) {
+                // rows not on 16 bytes: four scalar stores per row
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        float *row = base + (int64_t)(z0 + k) * g.ds[2] + (int64_t)(y0 + j) * g.ds[1] + (int64_t)x0 * g.ds[0];
+                        if (z0 + k < nz && y0 + j < ny) {
+#pragma unroll
+                            for (int i = 0; i < 4; i++) row[(int64_t)i * g.ds[0]] = v[16 * k + 4 * j + i];
+                        }
                     }
                 }
             } else {
@@ -456,6 +486,14 @@ int grid_for(K kernel, int64_t nunits, int warps = kWarps)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
+// One launch of a 3-D codec kernel (either alignment instantiation).
+template <class In, class Out>
+void launch3(void (*kernel)(In, Out, LaunchGeom, int), int warps, const LaunchGeom &g, cudaStream_t st, In in,
+             Out out, int layout)
+{
+    kernel<<<grid_for(kernel, g.nunits, warps), 32 * warps, 0, st>>>(in, out, g, layout);
+}
+
 // vec: rows start on 16 bytes wherever a block starts (x0 multiple of 4).
 bool vec_ok(const void *ptr, const int64_t s[3], const zfpx_plan_s *p, int which /*0 src,1 dst*/)
 {
@@ -472,11 +510,9 @@ int launch_encode(int dims, int rate, const float *src, uint8_t *out, const Laun
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
         if (rate == 8)
-            encode3_kernel<8><<<grid_for(encode3_kernel<8>, g.nunits, kEnc3Warps<8>), 32 * kEnc3Warps<8>, 0, st>>>(
-                src, out, g, layout, vec);
+            launch3(vec ? encode3_kernel<8, true> : encode3_kernel<8, false>, kEnc3Warps<8>, g, st, src, out, layout);
         else
-            encode3_kernel<16><<<grid_for(encode3_kernel<16>, g.nunits, kEnc3Warps<16>), 32 * kEnc3Warps<16>, 0,
-                                 st>>>(src, out, g, layout, vec);
+            launch3(vec ? encode3_kernel<16, true> : encode3_kernel<16, false>, kEnc3Warps<16>, g, st, src, out, layout);
     } else if (dims == 2) {
         if (rate == 8) encode2_kernel<8><<<grid_for(encode2_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
         else encode2_kernel<16><<<grid_for(encode2_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
@@ -494,11 +530,9 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
         if (rate == 8)
-            decode3_kernel<8><<<grid_for(decode3_kernel<8>, g.nunits, kDec3Warps<8>), 32 * kDec3Warps<8>, 0, st>>>(
-                in, dst, g, layout, vec);
+            launch3(vec ? decode3_kernel<8, true> : decode3_kernel<8, false>, kDec3Warps<8>, g, st, in, dst, layout);
         else
-            decode3_kernel<16><<<grid_for(decode3_kernel<16>, g.nunits, kDec3Warps<16>), 32 * kDec3Warps<16>, 0,
-                                 st>>>(in, dst, g, layout, vec);
+            launch3(vec ? decode3_kernel<16, true> : decode3_kernel<16, false>, kDec3Warps<16>, g, st, in, dst, layout);
     } else if (dims == 2) {
         if (rate == 8) decode2_kernel<8><<<grid_for(decode2_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
         else decode2_kernel<16><<<grid_for(decode2_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);

@@ -209,7 +209,9 @@ def test_repeated_launches_reuse_work_counters(z):
 
 
 # ---------------------------------------------------------------- plans
-PLANS = [((17, 23, 37), 3, 2), ((8, 32, 64), 2, 2), ((5, 9, 11), 2, 3), ((20, 16, 48), 1, 4)]
+# the last three leave messages empty (more ranks than levels, points or rows on an axis)
+PLANS = [((17, 23, 37), 3, 2), ((8, 32, 64), 2, 2), ((5, 9, 11), 2, 3), ((20, 16, 48), 1, 4),
+         ((3, 8, 8), 2, 4), ((1, 1, 1), 3, 3), ((2, 2, 5), 3, 3)]
 
 
 @pytest.mark.parametrize("t", [0, 1])
