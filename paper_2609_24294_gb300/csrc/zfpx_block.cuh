@@ -67,6 +67,22 @@ ZFPX_HD int lowest_set(uint64_t x)
     return __builtin_ctzll(x);
 #endif
 }
+ZFPX_HD int lowest_set32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __ffs((int)x) - 1;
+#else
+    return __builtin_ctz(x);
+#endif
+}
+ZFPX_HD int popc32(uint32_t x)
+{
+#ifdef __CUDA_ARCH__
+    return __popc(x);
+#else
+    return __builtin_popcount(x);
+#endif
+}
 ZFPX_HD int popc64(uint64_t x)
 {
 #ifdef __CUDA_ARCH__
@@ -733,10 +749,10 @@ ZFPX_HD void xform2_inv(int32_t (&q)[16])
 // Encodes x[i + 4j] into 16 RATE bits.  The 16 coefficients' bit planes come
 // from one 32x32 transpose whose lower 16 rows are zero (the coefficients sit
 // in rows 16..31, so plane k is the high 16 bits of word k and the stages
-// below 16 only touch the upper rows), parked in the lane's plane slots; then
-// one group-tested plane after another until the budget is spent.  Writer: put(bits, len),
-// finish() (flush and zero-fill).  Planes: store_half(k, 0, w) /
-// load_half(k, 0), 32 slots of 32 bits.
+// below 16 only touch the upper rows), parked in the lane's plane slots;
+// the planes are coded in the two passes of encode_block3.  Writer: as for
+// encode_block3 (put, zeros, finish, orw; two slack words past 16 RATE
+// bits).  Planes: store_half(k, 0, w) / load_half(k, 0), 32 slots of 32 bits.
 template <int RATE, class Writer, class Planes>
 ZFPX_HD void encode_block2(const float (&x)[16], Writer &wr, Planes &pl)
 {
@@ -761,10 +777,77 @@ ZFPX_HD void encode_block2(const float (&x)[16], Writer &wr, Planes &pl)
 #pragma unroll
     for (int k = 0; k < 32; k++) pl.store_half(k, 0, w[k] >> 16);
     wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    int n = 0, R = 16 * RATE - 9;
+    // The two passes of encode_block3 with 16 coefficients: pass 1 writes each
+    // plane's verbatim bits and first group bit and leaves zeros for its
+    // group-tested part (the last plane may run into the writer's slack
+    // words); planes with new ones keep them in their slot, flagged in evm.
+    constexpr int END = 16 * RATE;
+    int n = 0, pos = 9;
+    uint32_t evm = 0, lm = 0;                                    // lm = low_mask(n)
 #pragma unroll 1
-    for (int k = 31; k >= 0 && R > 0; k--) code_plane<16>(wr, (uint64_t)pl.load_half(k, 0), n, R);
+    for (int k = 31; k >= 0 && pos < END; k--) {
+        const uint32_t X = pl.load_half(k, 0);
+        if (n >= 16) {                                           // every coefficient significant
+            wr.put(X, 16);
+            pos += 16;
+            continue;
+        }
+        const uint32_t Y = X & ~lm;
+        wr.put((X & lm) | (Y ? lm + 1u : 0u), n + 1);
+        int L = n + 1;
+        if (Y) {
+            const int h = highest_set32(Y), c = popc32(Y);
+            L = h < 15 ? h + 2 + c : h + c;
+            wr.zeros(L - n - 1);
+            pl.store_half(k, 0, Y);
+            evm |= 1u << k;
+            n = h + 1;
+            lm = (2u << h) - 1u;
+        }
+        pos += L;
+    }
     wr.finish();
+    // pass 2: the bits of each newly significant coefficient (the t-th one of
+    // a plane, at coefficient p, sits at plane start + 1 + p + t, its group
+    // bit right after; coefficient 15's one is implied)
+    uint32_t rest = 0;
+    uint64_t cacc = 0;
+    int ap = 0, t = 0, cw = 0, kp = 32, endp = 9, np = 0;
+#pragma unroll 1
+    for (;;) {
+        if (!rest) {
+            if (!evm) break;
+            const int k = highest_set32(evm);
+            evm &= ~(1u << k);
+            rest = pl.load_half(k, 0);
+            const int start = endp + (kp - 1 - k) * (np + 1);
+            ap = start + 1;
+            const int h = highest_set32(rest), c = popc32(rest);
+            endp = start + (h < 15 ? h + 2 + c : h + c);
+            np = h + 1;
+            kp = k;
+            t = 0;
+        }
+        const int p = lowest_set32(rest);
+        rest &= rest - 1u;
+        const int A = ap + p + t;
+        t++;
+        if (A >= END) break;                                     // positions only grow
+        const uint64_t b = (p != 15 ? 1ull : 0ull) | (rest ? 2ull : 0ull);
+        const int w = A >> 6, sh = A & 63;
+        if (w != cw) {
+            if (cacc) wr.orw(cw, cacc);
+            cw = w;
+            cacc = 0;
+        }
+        cacc |= b << sh;
+        if (sh == 63 && (b & 2ull)) {
+            wr.orw(cw, cacc);
+            cw = w + 1;
+            cacc = 1ull;
+        }
+    }
+    if (cacc) wr.orw(cw, cacc);
 }
 
 // Reader over a stream tile: peek() = the 64 bits from the current position.
