@@ -304,6 +304,36 @@ def test_strided_sources(z):
     del rng
 
 
+def test_random_views_fuzz(z):
+    """Random small fields, views of larger arrays (offsets, padded pitches,
+    longitude not always fastest), block shapes 1-D / 2-D / 3-D and both rates,
+    raw codec against the oracle; the decoder on the oracle's stream."""
+    rng = np.random.default_rng(31)
+    for it in range(40):
+        nz, ny, nx = (int(v) for v in rng.integers(1, 19, 3))
+        big = (rng.standard_normal((nz + 3, ny + 5, nx + 9)) * 10.0 ** rng.uniform(-20, 20)).astype(np.float32)
+        if it % 4 == 0:
+            big += np.float32(rng.uniform(-300, 300))
+        oz, oy, ox = (int(rng.integers(0, m)) for m in (3, 5, 9))
+        x = big[oz:oz + nz, oy:oy + ny, ox:ox + nx]
+        bd = dev(big)
+        src = bd[oz:oz + nz, oy:oy + ny, ox:ox + nx]
+        if it % 3 == 1:                                   # [lev][lon][lat] storage viewed as [lev][lat][lon]
+            alt = dev(np.ascontiguousarray(np.transpose(x, (0, 2, 1))))
+            src = alt.permute(0, 2, 1)
+        dims, rate = (1, 2, 3)[it % 3], (8, 16)[(it // 3) % 2]
+        n = (nx, ny, nz)
+        out = torch.zeros(z.zfpx_stream_bytes(dims, rate, n), dtype=torch.uint8, device="cuda")
+        z.zfpx_encode(dims, rate, src, out)
+        ref = oc.encode_array(dims, rate, np.ascontiguousarray(x))
+        assert host(out).tobytes() == ref.tobytes(), (it, dims, rate, x.shape)
+        dec = torch.full((nz, ny, nx), float("nan"), device="cuda")
+        z.zfpx_decode(dims, rate, out, dec)
+        rdec = np.empty_like(x)
+        oc.decode_array(dims, rate, ref, rdec)
+        same_bits(host(dec), rdec)
+
+
 # ---------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
 def config2():

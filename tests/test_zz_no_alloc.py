@@ -40,10 +40,11 @@ def _allocating_path(z, plan, rate, src):
 
 
 def test_noalloc_matches_allocating_path_two_calls(z):
-    cases = [((20, 36, 52), 2, 3, 0, 16, 250.0, 1), ((17, 26, 37), 3, 2, 1, 8, 0.0, 2)]
-    for shape, pr, pc, t, rate, offset, seed in cases:     # two calls in a row, different plans and rates
+    cases = [((20, 36, 52), 2, 3, 0, 16, 250.0, 1, 3), ((17, 26, 37), 3, 2, 1, 8, 0.0, 2, 3),
+             ((9, 30, 44), 2, 2, 0, 8, 5.0, 3, 2)]
+    for shape, pr, pc, t, rate, offset, seed, dims in cases:     # calls in a row, different plans and rates
         src = _field(shape, seed, offset)
-        plan = z.Plan.for_fields(src, pr, pc, t, 3)
+        plan = z.Plan.for_fields(src, pr, pc, t, dims)
         ref = _allocating_path(z, plan, rate, src)
         got = torch.full_like(src, float("nan"))
         z.zfpx_transpose_noalloc(plan, rate, src, got)
