@@ -879,15 +879,34 @@ def run_gpu(args):
 
 
 def run_profile_case(args):
-    """A reduced workload for an ncu capture of kernels whose benchmark workload is too
-    large to capture in full: `batch` = the ten O1280 fields with every level count
-    divided by 16 (at least 1; 51 levels, 337 M values, 1.35 GB of float32), one batch
-    encode and one decode launch per repetition.  Prints one line; times nothing."""
+    """A workload for an ncu capture of kernels the headline step does not run, or whose
+    benchmark workload is too large to capture in full.  `batch`: the ten O1280 fields
+    with every level count divided by 16 (at least 1; 51 levels, 337 M values, 1.35 GB
+    of float32), one batch encode and one decode launch per repetition.  `blocks12`: the
+    benchmark field and plan (1280 x 640 x 137, 8 x 8 ranks) coded with 2-D and then
+    1-D blocks, rates 8 and 16, pack+compress and decompress+unpack per repetition.
+    Prints one line; times nothing."""
     import torch
     from paper_2609_24294_gb300 import build, zfpx as z
-    from fieldgen import octahedral as og
     build.build()
     z.lib()
+    if args.profile_case == "blocks12":
+        xd = torch.from_numpy(make_field()).cuda()
+        n = 0
+        for _ in range(max(1, args.steps)):
+            for dims in (2, 1):
+                plan = z.Plan.for_fields(xd, PR, PC, 0, dims)
+                for r in RATES:
+                    send = torch.zeros(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+                    out = torch.empty_like(xd)
+                    z.zfpx_pack_compress(plan, r, xd, send)
+                    z.zfpx_decompress_unpack(plan, r, send, out, layout=z.LAYOUT_SEND)
+                    n += 2
+                plan.close()
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": n}))
+        return 0
+    from fieldgen import octahedral as og
     fields = []
     for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
         lev = max(1, nlev // 16)
@@ -917,7 +936,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--profile-case", choices=["batch"], default=None,
+    ap.add_argument("--profile-case", choices=["batch", "blocks12"], default=None,
                     help="run a reduced workload for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -30,16 +30,17 @@ def _field(shape, seed):
 
 
 @pytest.mark.parametrize("fold", [False, True])
-@pytest.mark.parametrize("shape,pr,pc", [((20, 40, 48), 2, 2), ((17, 26, 37), 3, 2)])
+@pytest.mark.parametrize("shape,pr,pc,dims", [((20, 40, 48), 2, 2, 3), ((17, 26, 37), 3, 2, 3),
+                                              ((9, 30, 44), 2, 3, 2)])
 @pytest.mark.parametrize("rate", [8, 16])
-def test_pair_graph_matches_oracle(z, shape, pr, pc, rate, fold):
+def test_pair_graph_matches_oracle(z, shape, pr, pc, dims, rate, fold):
     x = _field(shape, 1)
     nz, ny, nx = shape
     src = torch.from_numpy(x).cuda()
     mid = torch.full_like(src, float("nan"))
     dst = torch.full_like(src, float("nan"))
-    p1 = z.Plan.for_fields(src, pr, pc, 0, 3, dst=mid)
-    p2 = z.Plan.for_fields(mid, pr, pc, 1, 3, dst=dst)
+    p1 = z.Plan.for_fields(src, pr, pc, 0, dims, dst=mid)
+    p2 = z.Plan.for_fields(mid, pr, pc, 1, dims, dst=dst)
     nbuf = max(p1.buffer_bytes(rate), p2.buffer_bytes(rate))
     send = torch.zeros(nbuf, dtype=torch.uint8, device="cuda")
     recv = torch.zeros(nbuf, dtype=torch.uint8, device="cuda")
@@ -50,8 +51,8 @@ def test_pair_graph_matches_oracle(z, shape, pr, pc, rate, fold):
     torch.cuda.synchronize()
     assert z.zfpx_launch_count() - before == g.num_kernels()
     # oracle: the two transpositions in turn
-    o1 = opl.Plan(nx, ny, nz, pr, pc, 0, 3)
-    o2 = opl.Plan(nx, ny, nz, pr, pc, 1, 3)
+    o1 = opl.Plan(nx, ny, nz, pr, pc, 0, dims)
+    o2 = opl.Plan(nx, ny, nz, pr, pc, 1, dims)
     ymid = np.full_like(x, np.nan)
     op.unpack(o1, rate, op.permute(o1, rate, op.pack(o1, rate, x)), ymid)
     zout = np.full_like(x, np.nan)
