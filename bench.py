@@ -37,7 +37,7 @@ METRIC = "fused pack+ZFP rate-8/16 GB/s (fp32 in) vs HBM roofline & fp16-cast pa
 SHAPE = (137, 640, 1280)                    # [lev][lat][lon]
 PR = PC = 8
 RATES = (8, 16)
-WORKLOAD = ("config2: 1280x640x137 float32 T639 (l+1)^-1.5 field + 0.01 noise (seed 1), "
+WORKLOAD = ("1280x640x137 float32 T639 (l+1)^-1.5 field + 0.01 noise (seed 1), "
             "z->lambda over 8x8 simulated ranks (512 messages), ZFP 3-D rates 8 and 16: "
             "pack+compress, device-local all-to-all, decompress+unpack")
 FALLBACK_HBM = 6800.0
@@ -250,7 +250,7 @@ def reconstruction_errors(z, plan, x, decoded=None):
 
 def make_field():
     import fieldgen
-    return fieldgen.config2_field()
+    return fieldgen.t639_field()
 
 
 # ------------------------------------------------------------------ reference arm
@@ -312,7 +312,7 @@ def extra_small_latency(z):
     pack+compress -> all-to-all -> decompress+unpack at rates 16 and 8 (median of 50)."""
     import torch
     import fieldgen
-    x = torch.from_numpy(fieldgen.config1_field()).cuda()
+    x = torch.from_numpy(fieldgen.t21_field()).cuda()
     plan = z.Plan.for_fields(x, 2, 2, 0, 3)
     res = {"workload": "64x32x8 f32 (64 KiB) T21, 2x2 ranks"}
     st = torch.cuda.current_stream()

@@ -9,4 +9,4 @@ spherical-harmonic transforms of seeded power-law spectra on Gauss-Legendre
 latitudes (Sec. II-A describes the grid and the transform).
 """
 from .sht import gaussian_latitudes, sht_field  # noqa: F401
-from .workloads import config1_field, config2_field, graded_blocks, temperature_like  # noqa: F401
+from .workloads import t21_field, t639_field, graded_blocks, temperature_like  # noqa: F401

@@ -1,8 +1,8 @@
 """The seeded workloads (stand-ins for the paper's DYAMOND fields, Sec. IV-A).
 
-* ``config1_field``: 64 lon x 32 Gaussian lat x 8 levels, T21 spectrum with
+* ``t21_field``: 64 lon x 32 Gaussian lat x 8 levels, T21 spectrum with
   complex N(0,1) (l+1)^-1.5 amplitudes, one draw per level, seed 0.
-* ``config2_field``: 1280 x 640 x 137, T639 (l+1)^-1.5 spectrum, one draw per
+* ``t639_field``: 1280 x 640 x 137, T639 (l+1)^-1.5 spectrum, one draw per
   level, each level scaled to unit RMS, plus N(0, 0.01^2) white noise, seed 1.
 * ``temperature_like``: 250 + 20 * field -- the paper's temperature has a
   large mean offset, which is what makes its relative error small.
@@ -14,7 +14,7 @@ import numpy as np
 from .sht import sht_field
 
 
-def config1_field():
+def t21_field():
     return sht_field(64, 32, 8, T=21, slope=-1.5, seed=0)
 
 
@@ -27,7 +27,7 @@ def unit_rms_plus_noise(f, noise, seed):
     return f.astype(np.float32)
 
 
-def config2_field(nlon=1280, nlat=640, nlev=137, T=639, seed=1, noise=0.01):
+def t639_field(nlon=1280, nlat=640, nlev=137, T=639, seed=1, noise=0.01):
     f = sht_field(nlon, nlat, nlev, T=T, slope=-1.5, seed=seed)
     return unit_rms_plus_noise(f, noise, seed)
 

@@ -54,8 +54,8 @@ def smooth_field(shape, seed, offset=0.0):
 # ---------------------------------------------------------------- raw arrays
 @pytest.mark.parametrize("dims", [3, 2, 1])
 @pytest.mark.parametrize("rate", [16, 8])
-def test_config1_raw_codec(z, dims, rate):
-    f = fieldgen.config1_field()                   # 64 lon x 32 lat x 8 levels
+def test_t21_field_raw_codec(z, dims, rate):
+    f = fieldgen.t21_field()                   # 64 lon x 32 lat x 8 levels
     n = (64, 32, 8)
     nb = z.zfpx_stream_bytes(dims, rate, n)
     out = torch.zeros(nb, dtype=torch.uint8, device="cuda")
@@ -336,17 +336,17 @@ def test_random_views_fuzz(z):
 
 # ---------------------------------------------------------------- full size
 @pytest.fixture(scope="module")
-def config2():
-    return fieldgen.config2_field()
+def t639():
+    return fieldgen.t639_field()
 
 
 @pytest.mark.parametrize("dims", [3, 2])
 @pytest.mark.parametrize("rate", [8, 16])
-def test_config2_full_size_sampled(z, config2, rate, dims):
+def test_t639_field_full_size_sampled(z, t639, rate, dims):
     """1280 x 640 x 137, 8 x 8 ranks, z->lambda: the launch the benchmark
     times, checked message by message on a sample (the oracle codes one
     message in well under a second) and as a whole by invariants."""
-    x = config2
+    x = t639
     xd = dev(x)
     nz, ny, nx = x.shape
     plan = z.Plan.for_fields(xd, 8, 8, 0, dims)

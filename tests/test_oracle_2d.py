@@ -104,7 +104,7 @@ def test_partial_blocks_and_raster_order():
 
 
 def test_error_non_increasing_with_rate_and_better_than_1d():
-    f = fieldgen.config1_field()
+    f = fieldgen.t21_field()
     for g in (f, fieldgen.temperature_like(f)):
         x = g.astype(np.float64)
         prev = np.inf
@@ -124,7 +124,7 @@ def test_error_non_increasing_with_rate_and_better_than_1d():
 @pytest.mark.parametrize("rate", [4, 8, 13, 16, 32])
 def test_second_statement_agrees(rate):
     rng = np.random.default_rng(25 + rate)
-    arrays = [np.ascontiguousarray(fieldgen.config1_field()[:2, :16, :32])]
+    arrays = [np.ascontiguousarray(fieldgen.t21_field()[:2, :16, :32])]
     arrays += [(rng.standard_normal(s) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
                for s in [(1, 1, 1), (2, 5, 7), (3, 6, 9)]]
     arrays += [np.full((1, 4, 4), 250.0, np.float32), np.zeros((1, 3, 5), np.float32)]

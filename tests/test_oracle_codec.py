@@ -253,7 +253,7 @@ def test_strided_views_equal_contiguous():
 
 def test_error_non_increasing_with_rate():
     import fieldgen
-    f = fieldgen.config1_field()
+    f = fieldgen.t21_field()
     fields = [f, fieldgen.temperature_like(f)]
     x64 = [g.astype(np.float64) for g in fields]
     for g, x in zip(fields, x64):

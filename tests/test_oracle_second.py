@@ -22,8 +22,8 @@ def _check(dims, rate, a):
 
 
 @pytest.mark.parametrize("dims,rate", [(3, 16), (3, 8), (1, 16), (1, 8)])
-def test_config1_field(dims, rate):
-    x = fieldgen.config1_field()
+def test_t21_field(dims, rate):
+    x = fieldgen.t21_field()
     part = x[:, :, :32] if dims == 3 else x[:2]           # keep the pure-Python side fast
     _check(dims, rate, np.ascontiguousarray(part))
 
