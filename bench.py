@@ -301,7 +301,7 @@ def _octahedral_fields():
     import torch
     from fieldgen import octahedral as og
     fields = []
-    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+    for i, (nlev, kind, dims, rate) in enumerate(og.O1280_TEN_FIELDS):
         src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
         fields.append((src, torch.empty_like(src), dims, rate))
     return og.row_lengths(1280), fields
@@ -908,7 +908,7 @@ def run_profile_case(args):
         return 0
     from fieldgen import octahedral as og
     fields = []
-    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+    for i, (nlev, kind, dims, rate) in enumerate(og.O1280_TEN_FIELDS):
         lev = max(1, nlev // 16)
         src = og.octahedral_field(1280, lev, 300 + i, kind=kind, device="cuda")
         fields.append((src, torch.empty_like(src), dims if lev > 1 else 1, rate))

@@ -80,7 +80,7 @@ def octahedral_field(N, nlev, seed, kind="power", device="cpu", rho=0.95, slope=
 
 
 # The ten fields of the batched workload: (levels, flavour, block dims, rate).
-CONFIG3_FIELDS = [
+O1280_TEN_FIELDS = [
     (137, "temperature", 3, 8), (137, "power", 3, 16), (137, "humidity", 3, 8), (137, "power", 3, 16),
     (1, "temperature", 1, 8), (137, "humidity", 3, 16), (91, "power", 3, 8), (60, "humidity", 3, 16),
     (30, "temperature", 3, 8), (1, "humidity", 1, 16),

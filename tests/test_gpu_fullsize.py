@@ -104,7 +104,7 @@ def test_pair_full_size_sampled(z, rate):
 def o1280():
     lens = og.row_lengths(1280)
     fields = []
-    for i, (nlev, kind, dims, rate) in enumerate(og.CONFIG3_FIELDS):
+    for i, (nlev, kind, dims, rate) in enumerate(og.O1280_TEN_FIELDS):
         src = og.octahedral_field(1280, nlev, 300 + i, kind=kind, device="cuda")
         fields.append((src, torch.empty_like(src), dims, rate))
     yield lens, fields
