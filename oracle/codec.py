@@ -55,6 +55,13 @@ def lib():
                                         i64p, ctypes.c_void_p, ctypes.c_int64]
         L.zfpo_decode_array.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, i64p,
                                         ctypes.c_void_p, i64p]
+        L.zfpo_accuracy_kmin.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.zfpo_accuracy_minexp.argtypes = [ctypes.c_double]
+        L.zfpo_accuracy_max_payload_bytes.argtypes = [i64p]
+        L.zfpo_accuracy_max_payload_bytes.restype = ctypes.c_int64
+        L.zfpo_encode_accuracy.argtypes = [ctypes.c_void_p, i64p, i64p, ctypes.c_double, ctypes.c_void_p,
+                                           ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
+        L.zfpo_decode_accuracy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p]
         _lib = L
     return _lib
 
@@ -209,4 +216,43 @@ def decode_array(dims, rate, stream, out):
                                  _i64x3(_strides_elems(out)))
     if rc:
         raise ValueError("zfpo_decode_array failed: %d" % rc)
+    return out
+
+
+# ---------------------------------------------------------------- accuracy mode
+def accuracy_minexp(tol):
+    return int(lib().zfpo_accuracy_minexp(float(tol)))
+
+
+def accuracy_kmin(emax, minexp):
+    return int(lib().zfpo_accuracy_kmin(int(emax), int(minexp)))
+
+
+def encode_accuracy(a, tol):
+    """Accuracy-mode coding of a float32 array indexed [z][y][x] (any strides) with
+    3-D blocks.  Returns (lengths uint16 per block, payload bytes, total bits)."""
+    nz, ny, nx = a.shape
+    n = (nx, ny, nz)
+    nblk = block_count(3, n)
+    cap = int(lib().zfpo_accuracy_max_payload_bytes(_i64x3(n)))
+    lengths = np.zeros(max(nblk, 1), dtype=np.uint16)
+    payload = np.zeros(max(cap, 1), dtype=np.uint8)
+    bits = ctypes.c_uint64(0)
+    rc = lib().zfpo_encode_accuracy(a.ctypes.data_as(ctypes.c_void_p), _i64x3(n), _i64x3(_strides_elems(a)),
+                                    float(tol), _ptr(lengths), _ptr(payload), cap, ctypes.byref(bits))
+    if rc:
+        raise ValueError("zfpo_encode_accuracy failed: %d" % rc)
+    total = int(bits.value)
+    return lengths[:nblk], payload[:(total + 7) // 8], total
+
+
+def decode_accuracy(lengths, payload, out):
+    """Decode into the float32 array ``out`` indexed [z][y][x] (written in place)."""
+    nz, ny, nx = out.shape
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint16)
+    payload = np.ascontiguousarray(np.concatenate([np.asarray(payload, np.uint8), np.zeros(8, np.uint8)]))
+    rc = lib().zfpo_decode_accuracy(_ptr(lengths), _ptr(payload), _i64x3((nx, ny, nz)),
+                                    out.ctypes.data_as(ctypes.c_void_p), _i64x3(_strides_elems(out)))
+    if rc:
+        raise ValueError("zfpo_decode_accuracy failed: %d" % rc)
     return out

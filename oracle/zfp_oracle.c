@@ -556,3 +556,150 @@ int zfpo_decode_array(int dims, int rate, const uint8_t *in, const int64_t n[3],
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Variable-rate coding to an absolute error tolerance (3-D blocks).  The   */
+/* paper names ZFP's accuracy mode and leaves it for future work (Sec.      */
+/* II-C); the readings here:                                                 */
+/*   minexp = floor(log2 tol); a block with exponent e_max codes its bit     */
+/*   planes from 31 down to kmin = clamp(minexp - e_max + 22, 0, 32), with   */
+/*   the same header, transform, order and group-tested coder as the fixed-  */
+/*   rate mode, and at most 16 * 64 = 1024 bits (the rate-16 budget: a block */
+/*   whose planes do not fit is cut there).  Dropping planes below kmin      */
+/*   changes a coefficient by less than 2^kmin; the inverse transform's gain */
+/*   is below 2^6 and its rounding adds a few units, so the reconstruction   */
+/*   error stays below 2^(kmin + 7) * 2^(e_max - 30) = tol / 2 for blocks    */
+/*   whose kmin is not clamped at 0 and whose bits are not cut.              */
+/*   Zero blocks (the fixed-rate rule) take 1 bit; a block with kmin = 32    */
+/*   takes its 9 header bits and no plane.                                   */
+/* Stream of an array: per block (raster order, edge-replicated partial     */
+/* blocks as in the fixed-rate arrays) its bit count L in lengths[], and     */
+/* the blocks' bits back to back in payload (LSB first).  A block decodes    */
+/* as the rate-16 block made of its L bits followed by zeros: zero bits      */
+/* after the last coded plane read as planes with nothing in them.           */
+/* ------------------------------------------------------------------------ */
+int zfpo_accuracy_kmin(int emax, int minexp)
+{
+    int k = minexp - emax + 22;
+    return k < 0 ? 0 : (k > 32 ? 32 : k);
+}
+
+static uint64_t encode_planes_down_to(bitw *w, int S, const uint32_t *u, uint64_t budget, int kstop)
+{
+    uint64_t left = budget;
+    int n = 0;
+    for (int k = 31; k >= kstop; k--) {
+        unsigned X[64];
+        for (int i = 0; i < S; i++) X[i] = (u[i] >> k) & 1u;
+        if (code_plane(w, S, X, &n, &left)) break;
+        if (left == 0) break;
+    }
+    return budget - left;
+}
+
+/* One block's bits in accuracy mode, written at w (buffer zeroed); returns L. */
+static uint64_t encode_block_accuracy(bitw *w, const float *v, int minexp)
+{
+    const uint64_t start = w->pos;
+    double M = 0.0;
+    for (int i = 0; i < 64; i++) {
+        double a = fabs((double)v[i]);
+        if (a > M || a != a) M = a;
+    }
+    int emax = 0, zero = 1;
+    if (M > 0.0 && isfinite(M)) {
+        (void)frexp(M, &emax);
+        zero = (emax + 127 <= 0);
+    }
+    if (zero) { put_bit(w, 0); return 1; }
+    put_bit(w, 1);
+    unsigned e = (unsigned)(emax + 127);
+    for (int b = 0; b < 8; b++) put_bit(w, (e >> b) & 1u);
+    const int kmin = zfpo_accuracy_kmin(emax, minexp);
+    if (kmin < 32) {
+        int32_t q[64];
+        for (int i = 0; i < 64; i++) q[i] = (int32_t)ldexp((double)v[i], 30 - emax);
+        zfpo_xform_forward(3, q);
+        int order[64];
+        zfpo_sequency_order(3, order);
+        uint32_t u[64];
+        for (int t = 0; t < 64; t++) u[t] = zfpo_to_negabinary(q[order[t]]);
+        encode_planes_down_to(w, 64, u, 64 * 16 - 9, kmin);
+    }
+    return w->pos - start;
+}
+
+int zfpo_accuracy_minexp(double tol)
+{
+    int e = 0;
+    (void)frexp(tol, &e);          /* tol = m 2^e, m in [0.5, 1): floor(log2 tol) = e - 1 */
+    return e - 1;
+}
+
+int64_t zfpo_accuracy_max_payload_bytes(const int64_t n[3])
+{
+    return zfpo_block_count(3, n) * 128;
+}
+
+static void gather3(const float *base, const int64_t n[3], const int64_t s[3],
+                    int64_t xb, int64_t yb, int64_t zb, float *v)
+{
+    for (int k = 0; k < 4; k++)
+        for (int j = 0; j < 4; j++)
+            for (int i = 0; i < 4; i++) {
+                int64_t x = imin64(4 * xb + i, n[0] - 1);
+                int64_t y = imin64(4 * yb + j, n[1] - 1);
+                int64_t z = imin64(4 * zb + k, n[2] - 1);
+                v[i + 4 * j + 16 * k] = base[x * s[0] + y * s[1] + z * s[2]];
+            }
+}
+
+int zfpo_encode_accuracy(const float *base, const int64_t n[3], const int64_t s[3], double tol,
+                         uint16_t *lengths, uint8_t *payload, int64_t payload_bytes, uint64_t *total_bits)
+{
+    if (!(tol > 0.0) || !isfinite(tol)) return -1;
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1) { *total_bits = 0; return 0; }
+    if (payload_bytes < zfpo_accuracy_max_payload_bytes(n)) return -2;
+    memset(payload, 0, (size_t)payload_bytes);
+    const int minexp = zfpo_accuracy_minexp(tol);
+    bitw w = {payload, 0};
+    float v[64];
+    int64_t bx = (n[0] + 3) / 4, by = (n[1] + 3) / 4, bz = (n[2] + 3) / 4, b = 0;
+    for (int64_t zb = 0; zb < bz; zb++)
+        for (int64_t yb = 0; yb < by; yb++)
+            for (int64_t xb = 0; xb < bx; xb++) {
+                gather3(base, n, s, xb, yb, zb, v);
+                lengths[b++] = (uint16_t)encode_block_accuracy(&w, v, minexp);
+            }
+    *total_bits = w.pos;
+    return 0;
+}
+
+int zfpo_decode_accuracy(const uint16_t *lengths, const uint8_t *payload, const int64_t n[3],
+                         float *base, const int64_t s[3])
+{
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1) return 0;
+    bitr r = {payload, 0};
+    float v[64];
+    int64_t bx = (n[0] + 3) / 4, by = (n[1] + 3) / 4, bz = (n[2] + 3) / 4, b = 0;
+    for (int64_t zb = 0; zb < bz; zb++)
+        for (int64_t yb = 0; yb < by; yb++)
+            for (int64_t xb = 0; xb < bx; xb++) {
+                uint8_t blk[128];
+                memset(blk, 0, sizeof blk);
+                bitw bw = {blk, 0};
+                const unsigned L = lengths[b++];
+                if (L > 1024) return -1;
+                for (unsigned i = 0; i < L; i++) put_bit(&bw, get_bit(&r));
+                bitr br = {blk, 0};
+                decode_block(&br, 3, 16, v);
+                for (int k = 0; k < 4; k++)
+                    for (int j = 0; j < 4; j++)
+                        for (int i = 0; i < 4; i++) {
+                            int64_t x = 4 * xb + i, y = 4 * yb + j, z = 4 * zb + k;
+                            if (x < n[0] && y < n[1] && z < n[2])
+                                base[x * s[0] + y * s[1] + z * s[2]] = v[i + 4 * j + 16 * k];
+                        }
+            }
+    return 0;
+}

@@ -81,16 +81,32 @@ def _order(dims):
 
 def encode_block(dims, rate, values):
     """Bits (list of 0/1) of one block of 4^dims float32 values."""
+    maxbits = (4 ** dims) * rate
+    bits = _code(dims, values, maxbits - 9, lambda e: 0)
+    return bits + [0] * (maxbits - len(bits))
+
+
+def encode_block_accuracy(values, tol):
+    """Bits of one 3-D block in the accuracy mode: planes from 31 down to
+    kmin = minexp - e_max + 22 (clamped to 0..32, minexp = floor(log2 tol)),
+    at most 1024 bits, no fill."""
+    minexp = math.frexp(tol)[1] - 1
+    return _code(3, values, 1024 - 9, lambda e: min(32, max(0, minexp - e + 22)))
+
+
+def _code(dims, values, budget, kstop_of):
+    """Header and planes 31 .. kstop_of(e_max) of one block, at most budget bits
+    after the header; a zero block is the single bit 0."""
     size = 4 ** dims
-    maxbits = size * rate
     vals = [float(v) for v in np.asarray(values, dtype=np.float32).reshape(-1)]
     big = max(abs(v) for v in vals)
     if not math.isfinite(big) or big == 0.0:
-        return [0] * maxbits
+        return [0]
     e = math.frexp(big)[1]
     if e + 127 <= 0:
-        return [0] * maxbits
+        return [0]
     bits = [1] + [(e + 127) >> b & 1 for b in range(8)]
+    kstop = kstop_of(e)
     q = [int(math.trunc(v * 2.0 ** (30 - e))) for v in vals]
     for axis in _lines(dims):
         for line in axis:
@@ -98,9 +114,8 @@ def encode_block(dims, rate, values):
             for t, val in zip(line, out):
                 q[t] = val
     u = [(_wrap(q[idx]) + 0xAAAAAAAA & 0xFFFFFFFF) ^ 0xAAAAAAAA for idx in _order(dims)]
-    budget = maxbits - 9
     n = 0
-    for k in range(31, -1, -1):
+    for k in range(31, kstop - 1, -1):
         if budget <= 0:
             break
         plane = [c >> k & 1 for c in u]
@@ -130,7 +145,7 @@ def encode_block(dims, rate, values):
                 j += 1
             if budget == 0:
                 break
-    return bits + [0] * (maxbits - len(bits))
+    return bits
 
 
 def decode_block(dims, rate, bits):
