@@ -193,6 +193,34 @@ ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[
 ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                 const int64_t stride[3], float *d_out, void *stream);
 
+/* ---- accuracy mode: variable rate to an absolute tolerance (3-D blocks) ---
+ * The ZFP mode the paper names and leaves for future work (Sec. II-C).  Every
+ * 4x4x4 block (raster order, partial blocks edge-replicated as in the raw
+ * codec) keeps its bit planes 31 .. kmin, kmin = clamp(floor(log2 tolerance)
+ * - e_max + 22, 0, 32), at most 1024 bits (the rate-16 budget, which cuts
+ * blocks whose planes do not fit): the reconstruction error of a block that
+ * is not cut and whose kmin is not clamped at 0 stays within the tolerance.
+ * A zero block takes 1 bit, a block below the tolerance its 9 header bits.
+ * Output: d_lengths[b] = bits of block b (uint16, one per block) and
+ * d_payload = the blocks' bits back to back, LSB first, in 64-bit words;
+ * *d_total_bits (device) = their sum; the payload's used part is
+ * 8 * ceil(total / 64) bytes.  Both calls need caller-owned device scratch
+ * d_work (256-byte aligned) of zfpx_accuracy_workspace_bytes(n) bytes; the
+ * encoder needs cap >= zfpx_accuracy_max_payload_bytes(n) (it zeroes that much
+ * of d_payload).  Decode takes the lengths and the payload (len bytes, a
+ * multiple of 8 covering the used part) and writes the array through stride.
+ * Calls using the same d_work must not overlap on the GPU.  Errors:
+ * ZFPX_EINVAL (NULL, extents < 1, tolerance not positive and finite,
+ * misaligned pointers), ZFPX_ESIZE, ZFPX_ECUDA. */
+ZFPX_API size_t zfpx_accuracy_workspace_bytes(const int64_t n[3]);
+ZFPX_API size_t zfpx_accuracy_max_payload_bytes(const int64_t n[3]);
+ZFPX_API int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t stride[3], double tolerance,
+                                  uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                                  void *d_work, size_t work_bytes, void *stream);
+ZFPX_API int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_payload, size_t len,
+                                  const int64_t n[3], const int64_t stride[3], float *d_out, void *d_work,
+                                  size_t work_bytes, void *stream);
+
 /* ---- batched ragged-row fields in one persistent launch -------------------
  * Many fields with different level counts, block dimensionality and rate
  * (ZFP fixed rate, Sec. II-C) on one grid of ragged rows: rows back to back,

@@ -1,0 +1,316 @@
+// Accuracy mode: variable-rate coding of 3-D blocks to an absolute error
+// tolerance (the ZFP mode the paper names and leaves for future work, Sec.
+// II-C), built on the fixed-rate kernels.
+//
+// Readings (identical in the CPU oracle): minexp = floor(log2 tol); a block
+// with exponent e_max keeps its bit planes 31 .. kmin, kmin = clamp(minexp -
+// e_max + 22, 0, 32), cut at the rate-16 budget of 1024 bits; a zero block is
+// its one 0 bit, a block with kmin = 32 its 9 header bits.  Because the plane
+// coder is embedded, a block's accuracy-mode bits are the first L bits of its
+// rate-16 stream, and the rate-16 decoder reads the same block from those L
+// bits followed by zeros (zeros after the last coded plane are empty planes).
+//
+// Encode: the rate-16 encoder writes every block to a 128-byte slot; one
+// thread per block walks its slot's planes down to kmin to find L; an
+// exclusive scan of the L (per 1024-block tile, then over the tiles) gives
+// every block's bit offset; one thread per block ORs its L bits into the
+// zeroed payload at that offset (words shared by neighbouring blocks take
+// atomic ORs).  Decode: the same scan, one thread per block copies its L bits
+// back into a zeroed slot, then the rate-16 decoder.
+#include <cmath>
+#include <cuda_runtime.h>
+
+#include "zfpx_internal.h"
+#include "zfpx_block.cuh"
+
+namespace zfpx {
+namespace {
+
+using namespace blk;
+
+constexpr int kTile = 1024;                  // blocks per scan tile (one CTA)
+constexpr int kSlotWords = 16;               // 1024 bits per block slot
+constexpr int kCutBits = 64 * kSlotWords;
+
+__device__ __forceinline__ int acc_kmin(int emax, int minexp)
+{
+    const int k = minexp - emax + 22;
+    return k < 0 ? 0 : (k > 32 ? 32 : k);
+}
+
+// Reader over one block's slot in global memory; bits past the slot read as 0.
+struct SlotReader {
+    const uint64_t *w;
+    int pos;
+    __device__ __forceinline__ uint64_t peek() const
+    {
+        const int i = pos >> 6, sh = pos & 63;
+        const uint64_t lo = i < kSlotWords ? __ldg(w + i) : 0ull;
+        const uint64_t hi = i + 1 < kSlotWords ? __ldg(w + i + 1) : 0ull;
+        return sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+    }
+    __device__ __forceinline__ void skip(int k) { pos += k; }
+};
+
+// L for every block: parse the slot's planes 31 .. kmin with the rate-16 budget.
+__global__ void __launch_bounds__(256) acc_lengths_kernel(const uint64_t *__restrict__ slots, int64_t nblocks,
+                                                          int minexp, uint16_t *__restrict__ lengths)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const uint64_t *w = slots + b * kSlotWords;
+    const uint64_t head = __ldg(w);
+    int L;
+    if (!(head & 1ull)) {
+        L = 1;
+    } else {
+        const int emax = (int)((head >> 1) & 0xffu) - 127;
+        const int kmin = acc_kmin(emax, minexp);
+        SlotReader rd{w, 9};
+        int n = 0, R = kCutBits - 9;
+#pragma unroll 1
+        for (int k = 31; k >= kmin && R > 0; k--) (void)decode_plane<64>(rd, n, R);
+        L = kCutBits - R;
+    }
+    lengths[b] = (uint16_t)L;
+}
+
+// Exclusive scan of the lengths inside each tile of kTile blocks; the tile's
+// total goes to totals[tile].
+__global__ void __launch_bounds__(kTile) acc_scan_tiles_kernel(const uint16_t *__restrict__ lengths,
+                                                               int64_t nblocks, uint32_t *__restrict__ local,
+                                                               uint64_t *__restrict__ totals)
+{
+    __shared__ uint32_t warp_sum[kTile / 32];
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const int64_t b = (int64_t)blockIdx.x * kTile + t;
+    const uint32_t v = b < nblocks ? lengths[b] : 0u;
+    uint32_t x = v;                                        // inclusive scan in the warp
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, d);
+        if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t s = warp_sum[lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, s, d);
+            if (lane >= d) s += y;
+        }
+        warp_sum[lane] = s;                                // inclusive over warps
+    }
+    __syncthreads();
+    const uint32_t before = (wid ? warp_sum[wid - 1] : 0u) + x - v;
+    if (b < nblocks) local[b] = before;
+    if (t == kTile - 1) totals[blockIdx.x] = warp_sum[kTile / 32 - 1];
+}
+
+// Exclusive scan of the tile totals (one CTA, sequential over chunks of
+// kTile tiles); the grand total goes to *total_bits.
+__global__ void __launch_bounds__(kTile) acc_scan_totals_kernel(const uint64_t *__restrict__ totals, int64_t ntiles,
+                                                                uint64_t *__restrict__ tile_off,
+                                                                uint64_t *__restrict__ total_bits)
+{
+    __shared__ uint64_t warp_sum[kTile / 32];
+    __shared__ uint64_t carry;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    if (t == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += kTile) {
+        const int64_t i = base + t;
+        const uint64_t v = i < ntiles ? totals[i] : 0ull;
+        uint64_t x = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint64_t y = __shfl_up_sync(0xffffffffu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) warp_sum[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            uint64_t s = warp_sum[lane];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint64_t y = __shfl_up_sync(0xffffffffu, s, d);
+                if (lane >= d) s += y;
+            }
+            warp_sum[lane] = s;
+        }
+        __syncthreads();
+        const uint64_t c = carry;
+        if (i < ntiles) tile_off[i] = c + (wid ? warp_sum[wid - 1] : 0ull) + x - v;
+        __syncthreads();
+        if (t == 0) carry = c + warp_sum[kTile / 32 - 1];
+        __syncthreads();
+    }
+    if (t == 0) *total_bits = carry;
+}
+
+// Every block ORs its L bits into the zeroed payload at its bit offset.
+__global__ void __launch_bounds__(256) acc_pack_kernel(const uint64_t *__restrict__ slots, int64_t nblocks,
+                                                       const uint16_t *__restrict__ lengths,
+                                                       const uint32_t *__restrict__ local,
+                                                       const uint64_t *__restrict__ tile_off,
+                                                       unsigned long long *__restrict__ payload)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const uint64_t off = tile_off[b / kTile] + local[b];
+    const int L = lengths[b];
+    const uint64_t *w = slots + b * kSlotWords;
+    const int sh = (int)(off & 63);
+    unsigned long long *d = payload + (off >> 6);
+#pragma unroll 1
+    for (int i = 0; 64 * i < L; i++) {
+        uint64_t v = __ldg(w + i);
+        const int rem = L - 64 * i;
+        if (rem < 64) v &= (1ull << rem) - 1ull;
+        if (!v) continue;
+        atomicOr(d + i, (unsigned long long)(v << sh));
+        if (sh && (v >> (64 - sh))) atomicOr(d + i + 1, (unsigned long long)(v >> (64 - sh)));
+    }
+}
+
+// Every block copies its L bits back into a zeroed 1024-bit slot.
+__global__ void __launch_bounds__(256) acc_unpack_kernel(const uint64_t *__restrict__ payload, int64_t pwords,
+                                                         int64_t nblocks, const uint16_t *__restrict__ lengths,
+                                                         const uint32_t *__restrict__ local,
+                                                         const uint64_t *__restrict__ tile_off,
+                                                         uint64_t *__restrict__ slots)
+{
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nblocks) return;
+    const uint64_t off = tile_off[b / kTile] + local[b];
+    const int L = min((int)lengths[b], kCutBits);
+    const int sh = (int)(off & 63);
+    const int64_t j0 = (int64_t)(off >> 6);
+    uint64_t *s = slots + b * kSlotWords;
+#pragma unroll
+    for (int i = 0; i < kSlotWords; i++) {
+        uint64_t v = 0;
+        const int rem = L - 64 * i;
+        if (rem > 0) {
+            const int64_t j = j0 + i;
+            const uint64_t lo = j < pwords ? __ldg(payload + j) : 0ull;
+            const uint64_t hi = (sh && j + 1 < pwords) ? __ldg(payload + j + 1) : 0ull;
+            v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+            if (rem < 64) v &= (1ull << rem) - 1ull;
+        }
+        s[i] = v;
+    }
+}
+
+struct AccWork {
+    uint64_t *slots;
+    uint32_t *local;
+    uint64_t *totals, *tile_off, *total;
+    int64_t nblocks, ntiles;
+};
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+int64_t acc_blocks(const int64_t n[3]) { return ((n[0] + 3) / 4) * ((n[1] + 3) / 4) * ((n[2] + 3) / 4); }
+
+size_t acc_work_bytes(int64_t nb)
+{
+    const int64_t nt = (nb + kTile - 1) / kTile;
+    return align256((size_t)nb * 128) + align256((size_t)nb * 4) + 2 * align256((size_t)nt * 8) + 256;
+}
+
+AccWork acc_carve(void *work, int64_t nb)
+{
+    AccWork a;
+    a.nblocks = nb;
+    a.ntiles = (nb + kTile - 1) / kTile;
+    char *p = static_cast<char *>(work);
+    a.slots = reinterpret_cast<uint64_t *>(p); p += align256((size_t)nb * 128);
+    a.local = reinterpret_cast<uint32_t *>(p); p += align256((size_t)nb * 4);
+    a.totals = reinterpret_cast<uint64_t *>(p); p += align256((size_t)a.ntiles * 8);
+    a.tile_off = reinterpret_cast<uint64_t *>(p); p += align256((size_t)a.ntiles * 8);
+    a.total = reinterpret_cast<uint64_t *>(p);
+    return a;
+}
+
+int acc_scan(const AccWork &a, const uint16_t *lengths, uint64_t *total_bits, cudaStream_t st)
+{
+    acc_scan_tiles_kernel<<<(unsigned)a.ntiles, kTile, 0, st>>>(lengths, a.nblocks, a.local, a.totals);
+    count_launch();
+    acc_scan_totals_kernel<<<1, kTile, 0, st>>>(a.totals, a.ntiles, a.tile_off, total_bits);
+    count_launch();
+    return check_launch();
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+}  // namespace
+}  // namespace zfpx
+
+using namespace zfpx;
+
+extern "C" {
+
+size_t zfpx_accuracy_workspace_bytes(const int64_t n[3])
+{
+    if (!n || n[0] < 1 || n[1] < 1 || n[2] < 1) return 0;
+    return acc_work_bytes(acc_blocks(n));
+}
+
+size_t zfpx_accuracy_max_payload_bytes(const int64_t n[3])
+{
+    if (!n || n[0] < 1 || n[1] < 1 || n[2] < 1) return 0;
+    return (size_t)acc_blocks(n) * 128;
+}
+
+int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t stride[3], double tolerance,
+                         uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                         void *d_work, size_t work_bytes, void *stream)
+{
+    if (!d_in || !n || !stride || !d_lengths || !d_payload || !d_total_bits || !d_work) return ZFPX_EINVAL;
+    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
+    for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
+    if (!aligned(d_payload, 8) || !aligned(d_work, 256) || !aligned(d_lengths, 2) || !aligned(d_total_bits, 8))
+        return ZFPX_EINVAL;
+    const int64_t nb = acc_blocks(n);
+    if (cap < (size_t)nb * 128 || work_bytes < acc_work_bytes(nb)) return ZFPX_ESIZE;
+    int e = 0;
+    (void)frexp(tolerance, &e);
+    const int minexp = e - 1;                           // floor(log2 tolerance)
+    cudaStream_t st = (cudaStream_t)stream;
+    const AccWork a = acc_carve(d_work, nb);
+    int rc = zfpx_encode(3, 16, d_in, n, stride, reinterpret_cast<uint8_t *>(a.slots), (size_t)nb * 128, stream);
+    if (rc) return rc;
+    const unsigned grid = (unsigned)((nb + 255) / 256);
+    acc_lengths_kernel<<<grid, 256, 0, st>>>(a.slots, nb, minexp, d_lengths);
+    count_launch();
+    if ((rc = check_launch())) return rc;
+    if ((rc = acc_scan(a, d_lengths, d_total_bits, st))) return rc;
+    if (cudaMemsetAsync(d_payload, 0, (size_t)nb * 128, st) != cudaSuccess) return ZFPX_ECUDA;
+    acc_pack_kernel<<<grid, 256, 0, st>>>(a.slots, nb, d_lengths, a.local, a.tile_off,
+                                          reinterpret_cast<unsigned long long *>(d_payload));
+    count_launch();
+    return check_launch();
+}
+
+int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_payload, size_t len, const int64_t n[3],
+                         const int64_t stride[3], float *d_out, void *d_work, size_t work_bytes, void *stream)
+{
+    if (!d_lengths || !d_payload || !n || !stride || !d_out || !d_work) return ZFPX_EINVAL;
+    for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
+    if (!aligned(d_payload, 8) || !aligned(d_work, 256) || !aligned(d_lengths, 2)) return ZFPX_EINVAL;
+    const int64_t nb = acc_blocks(n);
+    if (work_bytes < acc_work_bytes(nb)) return ZFPX_ESIZE;
+    cudaStream_t st = (cudaStream_t)stream;
+    const AccWork a = acc_carve(d_work, nb);
+    int rc = acc_scan(a, d_lengths, a.total, st);
+    if (rc) return rc;
+    acc_unpack_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(
+        reinterpret_cast<const uint64_t *>(d_payload), (int64_t)(len / 8), nb, d_lengths, a.local, a.tile_off, a.slots);
+    count_launch();
+    if ((rc = check_launch())) return rc;
+    return zfpx_decode(3, 16, reinterpret_cast<const uint8_t *>(a.slots), (size_t)nb * 128, n, stride, d_out, stream);
+}
+
+}  // extern "C"

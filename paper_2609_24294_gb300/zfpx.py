@@ -107,6 +107,10 @@ def lib():
         "zfpx_batch_encode": ([vp, vp, sz, vp], ctypes.c_int),
         "zfpx_batch_decode": ([vp, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_num_kernels": ([vp], ctypes.c_int),
+        "zfpx_accuracy_workspace_bytes": ([i64p], sz),
+        "zfpx_accuracy_max_payload_bytes": ([i64p], sz),
+        "zfpx_encode_accuracy": ([vp, i64p, i64p, ctypes.c_double, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_decode_accuracy": ([vp, vp, sz, i64p, i64p, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -300,6 +304,36 @@ def zfpx_decode(dims, rate, inp, dst, stream=None):
     n, s = field_view(dst)
     _check(lib().zfpx_decode(dims, rate, _dev(inp, "in"), _nbytes(inp), _i64x3(n), _i64x3(s), _dev(dst, "dst"),
                              _stream(stream)), "zfpx_decode")
+
+
+def zfpx_accuracy_workspace_bytes(n):
+    return int(lib().zfpx_accuracy_workspace_bytes(_i64x3(n)))
+
+
+def zfpx_accuracy_max_payload_bytes(n):
+    return int(lib().zfpx_accuracy_max_payload_bytes(_i64x3(n)))
+
+
+def zfpx_encode_accuracy(src, tolerance, lengths, payload, total_bits, work, stream=None):
+    """Accuracy-mode encode of a [lev][lat][lon] float32 field (any strides) with 3-D
+    blocks; lengths: uint16 tensor (one per block), payload: uint8 tensor of at least
+    zfpx_accuracy_max_payload_bytes, total_bits: int64 tensor of one element, work:
+    uint8 tensor of zfpx_accuracy_workspace_bytes (all on the device)."""
+    if src.dtype != torch.float32:
+        raise ValueError("src must be float32")
+    n, s = field_view(src)
+    _check(lib().zfpx_encode_accuracy(_dev(src, "src"), _i64x3(n), _i64x3(s), float(tolerance),
+                                      _dev(lengths, "lengths"), _dev(payload, "payload"), _nbytes(payload),
+                                      _dev(total_bits, "total_bits"), _dev(work, "work"), _nbytes(work),
+                                      _stream(stream)), "zfpx_encode_accuracy")
+
+
+def zfpx_decode_accuracy(lengths, payload, dst, work, stream=None):
+    """Accuracy-mode decode into the float32 field dst (any strides)."""
+    n, s = field_view(dst)
+    _check(lib().zfpx_decode_accuracy(_dev(lengths, "lengths"), _dev(payload, "payload"), _nbytes(payload),
+                                      _i64x3(n), _i64x3(s), _dev(dst, "dst"), _dev(work, "work"), _nbytes(work),
+                                      _stream(stream)), "zfpx_decode_accuracy")
 
 
 class PairGraph:

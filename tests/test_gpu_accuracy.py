@@ -1,0 +1,92 @@
+"""GPU parity of the accuracy mode (variable-rate 3-D blocks to an absolute
+tolerance, Sec. II-C's named future mode) through the C ABI against the CPU
+oracle: per-block bit counts, total bits and payload bytes bit-exact, decoded
+values bit-exact; small ragged and strided arrays and the 1280 x 640 x 137
+field."""
+import numpy as np
+import pytest
+import torch
+
+import fieldgen
+from oracle import codec as oc
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def z():
+    from paper_2609_24294_gb300 import build, zfpx
+    build.build()
+    zfpx.lib()
+    return zfpx
+
+
+def _run(z, src, tol):
+    """GPU encode + decode; returns (lengths, payload bytes, total bits, decoded)."""
+    n = tuple(reversed(src.shape))
+    nblk = ((n[0] + 3) // 4) * ((n[1] + 3) // 4) * ((n[2] + 3) // 4)
+    lengths = torch.zeros(nblk, dtype=torch.int16, device="cuda")
+    payload = torch.zeros(z.zfpx_accuracy_max_payload_bytes(n), dtype=torch.uint8, device="cuda")
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    work = torch.zeros(z.zfpx_accuracy_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    z.zfpx_encode_accuracy(src, tol, lengths, payload, total, work)
+    torch.cuda.synchronize()
+    bits = int(total.item())
+    used = 8 * ((bits + 63) // 64)
+    dec = torch.full(src.shape, float("nan"), device="cuda")
+    z.zfpx_decode_accuracy(lengths, payload[:max(used, 8)], dec, work)
+    torch.cuda.synchronize()
+    return lengths.cpu().numpy().view(np.uint16), payload.cpu().numpy(), bits, dec.cpu().numpy()
+
+
+def _check(z, x, src, tol):
+    L, P, bits, dec = _run(z, src, tol)
+    rL, rP, rbits = oc.encode_accuracy(np.ascontiguousarray(x), tol)
+    assert bits == rbits
+    np.testing.assert_array_equal(L, rL)
+    nb = (bits + 7) // 8
+    assert P[:nb].tobytes() == rP[:nb].tobytes()
+    assert not P[8 * ((bits + 63) // 64):].any()
+    rdec = np.empty_like(np.ascontiguousarray(x))
+    oc.decode_accuracy(rL, rP, rdec)
+    assert dec.view(np.uint32).tobytes() == rdec.view(np.uint32).tobytes()
+    return L, bits
+
+
+@pytest.mark.parametrize("rel", [1e-1, 1e-3, 1e-5])
+@pytest.mark.parametrize("shape", [(1, 1, 1), (4, 4, 4), (7, 5, 3), (9, 13, 22), (17, 26, 37)])
+def test_small_arrays(z, shape, rel):
+    rng = np.random.default_rng(sum(shape))
+    g = np.cumsum(np.cumsum(rng.standard_normal(shape), axis=2), axis=1)
+    x = (250.0 + g).astype(np.float32)
+    tol = rel * float(np.abs(x).max())
+    _check(z, x, torch.from_numpy(x).cuda(), tol)
+
+
+def test_special_values_and_views(z):
+    rng = np.random.default_rng(7)
+    big = (rng.standard_normal((12, 20, 40)) * 10.0 ** rng.integers(-30, 30, (12, 20, 40))).astype(np.float32)
+    big[0:4, 0:4, 0:4] = 0.0
+    big[0:4, 4:8, 0:4] = 3.25
+    big[4:8, 0:4, 0:4] = np.float32(5e-40)
+    big[5, 5, 5] = np.inf
+    big[9, 9, 9] = np.nan
+    x = big[1:11, 2:19, 3:37]                                       # unaligned view
+    src = torch.from_numpy(big).cuda()[1:11, 2:19, 3:37]
+    for tol in (1e-3, 1.0, 1e6):
+        _check(z, x, src, tol)
+
+
+def test_repeated_calls_share_the_workspace(z):
+    x = (250.0 + np.cumsum(np.random.default_rng(3).standard_normal((8, 16, 40)), axis=2)).astype(np.float32)
+    src = torch.from_numpy(x).cuda()
+    a = _run(z, src, 0.01)
+    b = _run(z, src, 0.01)
+    np.testing.assert_array_equal(a[0], b[0])
+    assert a[2] == b[2] and a[1].tobytes() == b[1].tobytes()
+
+
+def test_t639_field_full_size(z):
+    x = fieldgen.t639_field()
+    L, bits = _check(z, x, torch.from_numpy(x).cuda(), 1e-3)
+    assert 0 < bits < 16 * x.size                                    # variable, below the rate-16 cut
