@@ -536,6 +536,38 @@ def extra_blocks_2d(z, xd, reps, peak):
     return res
 
 
+def extra_accuracy(z, xd, reps, peak):
+    """The accuracy mode (variable rate to an absolute tolerance, 3-D blocks) on the
+    benchmark field as one array: per tolerance the bits per value, the errors
+    against the float32 input, and the encode / decode times (the rate-16 codec plus
+    the per-block bit counts, the scan and the bit-level pack / unpack)."""
+    import torch
+    n = tuple(reversed(xd.shape))
+    nblk = ((n[0] + 3) // 4) * ((n[1] + 3) // 4) * ((n[2] + 3) // 4)
+    lengths = torch.zeros(nblk, dtype=torch.int16, device="cuda")
+    payload = torch.zeros(z.zfpx_accuracy_max_payload_bytes(n), dtype=torch.uint8, device="cuda")
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    work = torch.zeros(z.zfpx_accuracy_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(xd)
+    fbytes = 4 * xd.numel()
+    x64 = xd.double()
+    res = {"workload": "1280x640x137 f32 (unit RMS per level) as one array, 3-D blocks, absolute tolerances"}
+    for tol in (1e-2, 1e-3, 1e-4):
+        te = _events_ms(lambda: z.zfpx_encode_accuracy(xd, tol, lengths, payload, total, work), reps)
+        bits = int(total.item())
+        used = payload[:max(8, 8 * ((bits + 63) // 64))]
+        td = _events_ms(lambda: z.zfpx_decode_accuracy(lengths, used, out, work), reps)
+        d = (out.double() - x64).abs()
+        cut = int((lengths >= 1024).sum())
+        res["tol_%g" % tol] = {"bits_per_value": bits / xd.numel(), "max_abs_error": float(d.max()),
+                               "rel_l2": float((out.double() - x64).norm() / x64.norm()),
+                               "blocks_cut_at_1024_bits": cut, "blocks": nblk,
+                               "encode_ms": te, "decode_ms": td,
+                               "encode_f32_GBps": fbytes / (te / 1e3) / 1e9, "decode_f32_GBps": fbytes / (td / 1e3) / 1e9}
+    del lengths, payload, work, out
+    return res
+
+
 def _flushed_ms(fn, reps, flush):
     """Mean device time of fn, each repetition after an L2 flush (a write larger
     than L2), timed with events around fn alone."""
@@ -829,6 +861,10 @@ def run_gpu(args):
             extras["blocks_2d"] = extra_blocks_2d(z, xd, reps, peak)
         except Exception as e:
             extras["blocks_2d"] = {"error": repr(e)}
+        try:
+            extras["accuracy_mode"] = extra_accuracy(z, xd, reps, peak)
+        except Exception as e:
+            extras["accuracy_mode"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()
