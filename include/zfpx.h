@@ -221,6 +221,34 @@ ZFPX_API int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_pa
                                   const int64_t n[3], const int64_t stride[3], float *d_out, void *d_work,
                                   size_t work_bytes, void *stream);
 
+/* The accuracy mode on a transposition plan (dims 3): every message's box is
+ * coded as above, so messages vary in size and the exchange becomes an
+ * all-to-all-v, the per-message sizes first, then the payloads (on one GPU,
+ * device-local copies).  Per plan: G = zfpx_plan_accuracy_blocks (blocks of all
+ * messages), scratch d_work of zfpx_plan_accuracy_workspace_bytes (256-byte
+ * aligned, shared by the three calls, which must not overlap on the GPU).
+ *   pack_compress: d_lengths (G uint16, messages in send order, blocks in
+ *     raster order), d_payload (cap >= 128 G bytes; message m starts on a
+ *     64-bit word, messages back to back in send order), d_msg_words (one per
+ *     message in send order: its payload in 64-bit words).
+ *   exchange: moves lengths and payloads to the receive order (by destination
+ *     rank, then source peer), both payload buffers of cap >= 128 G bytes.
+ *   decompress_unpack: from the received lengths and payload (len bytes) and
+ *     the same d_msg_words, writes the plan's destination view.
+ * Errors: ZFPX_EINVAL (NULL, dims != 3, tolerance, alignment), ZFPX_ESIZE,
+ * ZFPX_ECUDA. */
+ZFPX_API size_t zfpx_plan_accuracy_blocks(zfpx_plan plan);
+ZFPX_API size_t zfpx_plan_accuracy_workspace_bytes(zfpx_plan plan);
+ZFPX_API int zfpx_pack_compress_accuracy(zfpx_plan plan, double tolerance, const float *d_src, uint16_t *d_lengths,
+                                         uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                         size_t work_bytes, void *stream);
+ZFPX_API int zfpx_exchange_accuracy(zfpx_plan plan, const uint64_t *d_msg_words, const uint16_t *d_len_send,
+                                    const uint8_t *d_pay_send, uint16_t *d_len_recv, uint8_t *d_pay_recv, size_t cap,
+                                    void *d_work, size_t work_bytes, void *stream);
+ZFPX_API int zfpx_decompress_unpack_accuracy(zfpx_plan plan, const uint64_t *d_msg_words, const uint16_t *d_len_recv,
+                                             const uint8_t *d_pay_recv, size_t len, float *d_dst, void *d_work,
+                                             size_t work_bytes, void *stream);
+
 /* ---- batched ragged-row fields in one persistent launch -------------------
  * Many fields with different level counts, block dimensionality and rate
  * (ZFP fixed rate, Sec. II-C) on one grid of ragged rows: rows back to back,

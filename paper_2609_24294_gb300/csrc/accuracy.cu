@@ -17,7 +17,9 @@
 // zeroed payload at that offset (words shared by neighbouring blocks take
 // atomic ORs).  Decode: the same scan, one thread per block copies its L bits
 // back into a zeroed slot, then the rate-16 decoder.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "zfpx_internal.h"
@@ -311,6 +313,360 @@ int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_payload, si
     count_launch();
     if ((rc = check_launch())) return rc;
     return zfpx_decode(3, 16, reinterpret_cast<const uint8_t *>(a.slots), (size_t)nb * 128, n, stride, d_out, stream);
+}
+
+}  // extern "C"
+
+// ============================================================================
+// The accuracy mode on a transposition plan: every message is coded as in the
+// raw accuracy mode (its box's 3-D blocks, edge-replicated inside the box);
+// messages become variable in size, so the exchange is an all-to-all-v: the
+// per-message word counts go first, then the payloads.  On one GPU both are
+// device-local copies.  A message's payload starts on a 64-bit word.
+namespace zfpx {
+std::vector<int64_t> layout_offsets(const zfpx_plan_s *p, int rate, int layout, int64_t *total);
+namespace {
+
+// One message as the accuracy kernels see it (send-order index m).
+struct AccMsg {
+    int64_t gb0;        // first block in the send-order block list (and lengths array)
+    int64_t gr0;        // first block in the receive-order block list
+    int64_t nb;         // blocks
+    int64_t slot_send;  // byte offset of its rate-16 slots in the send layout
+    int64_t slot_recv;  // byte offset of its rate-16 slots in the receive layout
+};
+
+struct PlanAcc {
+    const AccMsg *msgs;       // M, send order
+    const int32_t *rorder;    // M: send index of the message at receive position r
+    const int64_t *rgb0;      // M: gr0 of the message at receive position r (ascending)
+    int64_t *pay_send;        // M: payload word offset in the send buffer
+    int64_t *pay_recv;        // M: payload word offset in the receive buffer
+    int M;
+    int64_t G;                // blocks in all messages
+};
+
+__device__ __forceinline__ int last_le(const int64_t *a, const AccMsg *m, int M, int64_t g, bool by_msgs)
+{
+    int lo = 0, hi = M - 1;                  // last index whose start <= g (starts ascending)
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const int64_t s = by_msgs ? m[mid].gb0 : a[mid];
+        if (s <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t goff(const uint32_t *local, const uint64_t *tile_off, int64_t G,
+                                         const uint64_t *total, int64_t g)
+{
+    return g < G ? tile_off[g / kTile] + local[g] : *total;
+}
+
+__global__ void __launch_bounds__(256) pacc_lengths_kernel(PlanAcc P, const uint8_t *__restrict__ slots, int minexp,
+                                                           uint16_t *__restrict__ lengths)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.G) return;
+    const int m = last_le(nullptr, P.msgs, P.M, g, true);
+    const AccMsg &a = P.msgs[m];
+    const uint64_t *w = reinterpret_cast<const uint64_t *>(slots + a.slot_send) + (g - a.gb0) * kSlotWords;
+    const uint64_t head = __ldg(w);
+    int L = 1;
+    if (head & 1ull) {
+        const int kmin = acc_kmin((int)((head >> 1) & 0xffu) - 127, minexp);
+        SlotReader rd{w, 9};
+        int n = 0, R = kCutBits - 9;
+#pragma unroll 1
+        for (int k = 31; k >= kmin && R > 0; k--) (void)decode_plane<64>(rd, n, R);
+        L = kCutBits - R;
+    }
+    lengths[g] = (uint16_t)L;
+}
+
+// Word counts and payload offsets of the messages (one thread: M is a few
+// thousand at most).  With `send` the counts come from the block scan of the
+// send-order lengths and are written to words[]; otherwise words[] is input.
+__global__ void pacc_messages_kernel(PlanAcc P, const uint32_t *__restrict__ local,
+                                     const uint64_t *__restrict__ tile_off, const uint64_t *__restrict__ total,
+                                     uint64_t *__restrict__ words, int send)
+{
+    if (threadIdx.x || blockIdx.x) return;
+    int64_t o = 0;
+    for (int m = 0; m < P.M; m++) {
+        if (send) {
+            const AccMsg &a = P.msgs[m];
+            const uint64_t bits = goff(local, tile_off, P.G, total, a.gb0 + a.nb) - goff(local, tile_off, P.G, total, a.gb0);
+            words[m] = (bits + 63) / 64;
+        }
+        P.pay_send[m] = o;
+        o += (int64_t)words[m];
+    }
+    o = 0;
+    for (int r = 0; r < P.M; r++) {
+        const int m = P.rorder[r];
+        P.pay_recv[m] = o;
+        o += (int64_t)words[m];
+    }
+}
+
+__global__ void __launch_bounds__(256) pacc_pack_kernel(PlanAcc P, const uint8_t *__restrict__ slots,
+                                                        const uint16_t *__restrict__ lengths,
+                                                        const uint32_t *__restrict__ local,
+                                                        const uint64_t *__restrict__ tile_off,
+                                                        const uint64_t *__restrict__ total,
+                                                        unsigned long long *__restrict__ payload)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= P.G) return;
+    const int m = last_le(nullptr, P.msgs, P.M, g, true);
+    const AccMsg &a = P.msgs[m];
+    const uint64_t off = (uint64_t)P.pay_send[m] * 64 +
+                         (goff(local, tile_off, P.G, total, g) - goff(local, tile_off, P.G, total, a.gb0));
+    const int L = lengths[g];
+    const uint64_t *w = reinterpret_cast<const uint64_t *>(slots + a.slot_send) + (g - a.gb0) * kSlotWords;
+    const int sh = (int)(off & 63);
+    unsigned long long *d = payload + (off >> 6);
+#pragma unroll 1
+    for (int i = 0; 64 * i < L; i++) {
+        uint64_t v = __ldg(w + i);
+        const int rem = L - 64 * i;
+        if (rem < 64) v &= (1ull << rem) - 1ull;
+        if (!v) continue;
+        atomicOr(d + i, (unsigned long long)(v << sh));
+        if (sh && (v >> (64 - sh))) atomicOr(d + i + 1, (unsigned long long)(v >> (64 - sh)));
+    }
+}
+
+// The all-to-all-v on one GPU: CTA m moves message m's payload words and its
+// block bit counts from the send to the receive buffers.
+__global__ void __launch_bounds__(256) pacc_exchange_kernel(PlanAcc P, const uint64_t *__restrict__ words,
+                                                            const uint64_t *__restrict__ pay_in,
+                                                            uint64_t *__restrict__ pay_out,
+                                                            const uint16_t *__restrict__ len_in,
+                                                            uint16_t *__restrict__ len_out, int64_t cap_words)
+{
+    const int m = blockIdx.x;
+    const AccMsg a = P.msgs[m];
+    // counts that would run past either buffer are cut there
+    const int64_t nw = min((int64_t)min(words[m], (uint64_t)cap_words),
+                           cap_words - max(P.pay_send[m], P.pay_recv[m]));
+    const uint64_t *s = pay_in + P.pay_send[m];
+    uint64_t *d = pay_out + P.pay_recv[m];
+    for (int64_t i = threadIdx.x; i < nw; i += blockDim.x) d[i] = __ldg(s + i);
+    for (int64_t i = threadIdx.x; i < a.nb; i += blockDim.x) len_out[a.gr0 + i] = len_in[a.gb0 + i];
+}
+
+__global__ void __launch_bounds__(256) pacc_unpack_kernel(PlanAcc P, const uint64_t *__restrict__ payload, int64_t pwords,
+                                                          const uint16_t *__restrict__ lengths,
+                                                          const uint32_t *__restrict__ local,
+                                                          const uint64_t *__restrict__ tile_off,
+                                                          const uint64_t *__restrict__ total, uint8_t *__restrict__ slots)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;     // receive-order block
+    if (g >= P.G) return;
+    const int r = last_le(P.rgb0, nullptr, P.M, g, false);
+    const int m = P.rorder[r];
+    const AccMsg &a = P.msgs[m];
+    const uint64_t off = (uint64_t)P.pay_recv[m] * 64 +
+                         (goff(local, tile_off, P.G, total, g) - goff(local, tile_off, P.G, total, a.gr0));
+    const int L = min((int)lengths[g], kCutBits);
+    const int sh = (int)(off & 63);
+    const int64_t j0 = (int64_t)(off >> 6);
+    uint64_t *s = reinterpret_cast<uint64_t *>(slots + a.slot_recv) + (g - a.gr0) * kSlotWords;
+#pragma unroll
+    for (int i = 0; i < kSlotWords; i++) {
+        uint64_t v = 0;
+        const int rem = L - 64 * i;
+        if (rem > 0) {
+            const int64_t j = j0 + i;
+            const uint64_t lo = j < pwords ? __ldg(payload + j) : 0ull;
+            const uint64_t hi = (sh && j + 1 < pwords) ? __ldg(payload + j + 1) : 0ull;
+            v = sh ? (lo >> sh) | (hi << (64 - sh)) : lo;
+            if (rem < 64) v &= (1ull << rem) - 1ull;
+        }
+        s[i] = v;
+    }
+}
+
+struct PlanAccWork {
+    PlanAcc P;
+    uint8_t *slots;
+    AccWork scan;             // local / totals / tile_off / total for G blocks
+    size_t bytes;
+};
+
+int64_t plan_blocks(const zfpx_plan_s *p, std::vector<AccMsg> *msgs, std::vector<int32_t> *rorder,
+                    std::vector<int64_t> *rgb0)
+{
+    const size_t M = p->msgs.size();
+    auto c4 = [](int64_t v) { return (v + 3) / 4; };
+    std::vector<int64_t> nb(M);
+    int64_t G = 0;
+    for (size_t i = 0; i < M; i++) {
+        const HostMsg &m = p->msgs[i];
+        nb[i] = c4(m.nx) * c4(m.ny) * c4(m.nz);
+        G += nb[i];
+    }
+    if (!msgs) return G;
+    const std::vector<int64_t> so = layout_offsets(p, 16, ZFPX_LAYOUT_SEND, nullptr);
+    const std::vector<int64_t> ro = layout_offsets(p, 16, ZFPX_LAYOUT_RECV, nullptr);
+    std::vector<int32_t> ord(M);
+    for (size_t i = 0; i < M; i++) ord[i] = (int32_t)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t a, int32_t b) {
+        const HostMsg &x = p->msgs[a], &y = p->msgs[b];
+        return x.dst != y.dst ? x.dst < y.dst : x.src_peer < y.src_peer;
+    });
+    msgs->assign(M, AccMsg{});
+    rorder->assign(ord.begin(), ord.end());
+    rgb0->assign(M, 0);
+    int64_t g = 0;
+    for (size_t i = 0; i < M; i++) {
+        (*msgs)[i].gb0 = g; (*msgs)[i].nb = nb[i];
+        (*msgs)[i].slot_send = so[i]; (*msgs)[i].slot_recv = ro[i];
+        g += nb[i];
+    }
+    g = 0;
+    for (size_t r = 0; r < M; r++) {
+        (*msgs)[ord[r]].gr0 = g;
+        (*rgb0)[r] = g;
+        g += nb[ord[r]];
+    }
+    return G;
+}
+
+size_t plan_acc_bytes(const zfpx_plan_s *p, int64_t G)
+{
+    const size_t M = p->msgs.size();
+    return align256((size_t)buffer_bytes(p, 16)) + acc_work_bytes(G) - align256((size_t)G * 128) +
+           align256(M * sizeof(AccMsg)) + align256(M * 4) + 3 * align256(M * 8);
+}
+
+// Carves the scratch and uploads the message tables (pageable copies: the
+// host vectors have been read when the call returns).
+int plan_acc_setup(const zfpx_plan_s *p, void *work, size_t work_bytes, cudaStream_t st, PlanAccWork *w)
+{
+    std::vector<AccMsg> msgs;
+    std::vector<int32_t> rorder;
+    std::vector<int64_t> rgb0;
+    const int64_t G = plan_blocks(p, &msgs, &rorder, &rgb0);
+    const size_t M = msgs.size();
+    if (work_bytes < plan_acc_bytes(p, G)) return ZFPX_ESIZE;
+    char *c = static_cast<char *>(work);
+    w->slots = reinterpret_cast<uint8_t *>(c); c += align256((size_t)buffer_bytes(p, 16));
+    w->scan.nblocks = G;
+    w->scan.ntiles = (G + kTile - 1) / kTile;
+    w->scan.slots = nullptr;
+    w->scan.local = reinterpret_cast<uint32_t *>(c); c += align256((size_t)G * 4);
+    w->scan.totals = reinterpret_cast<uint64_t *>(c); c += align256((size_t)w->scan.ntiles * 8);
+    w->scan.tile_off = reinterpret_cast<uint64_t *>(c); c += align256((size_t)w->scan.ntiles * 8);
+    w->scan.total = reinterpret_cast<uint64_t *>(c); c += 256;
+    AccMsg *dm = reinterpret_cast<AccMsg *>(c); c += align256(M * sizeof(AccMsg));
+    int32_t *dr = reinterpret_cast<int32_t *>(c); c += align256(M * 4);
+    int64_t *dg = reinterpret_cast<int64_t *>(c); c += align256(M * 8);
+    w->P.pay_send = reinterpret_cast<int64_t *>(c); c += align256(M * 8);
+    w->P.pay_recv = reinterpret_cast<int64_t *>(c); c += align256(M * 8);
+    w->P.msgs = dm; w->P.rorder = dr; w->P.rgb0 = dg; w->P.M = (int)M; w->P.G = G;
+    if (M && (cudaMemcpyAsync(dm, msgs.data(), M * sizeof(AccMsg), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+              cudaMemcpyAsync(dr, rorder.data(), M * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+              cudaMemcpyAsync(dg, rgb0.data(), M * 8, cudaMemcpyHostToDevice, st) != cudaSuccess))
+        return ZFPX_ECUDA;
+    return ZFPX_OK;
+}
+
+unsigned grid256(int64_t n) { return (unsigned)std::max<int64_t>(1, (n + 255) / 256); }
+
+}  // namespace
+}  // namespace zfpx
+
+extern "C" {
+
+size_t zfpx_plan_accuracy_blocks(zfpx_plan p)
+{
+    return p ? (size_t)plan_blocks(p, nullptr, nullptr, nullptr) : 0;
+}
+
+size_t zfpx_plan_accuracy_workspace_bytes(zfpx_plan p)
+{
+    if (!p || p->dims != 3) return 0;
+    return plan_acc_bytes(p, plan_blocks(p, nullptr, nullptr, nullptr));
+}
+
+int zfpx_pack_compress_accuracy(zfpx_plan p, double tolerance, const float *d_src, uint16_t *d_lengths,
+                                uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                size_t work_bytes, void *stream)
+{
+    if (!p || !d_src || !d_lengths || !d_payload || !d_msg_words || !d_work || p->dims != 3) return ZFPX_EINVAL;
+    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
+    if (!aligned(d_payload, 8) || !aligned(d_work, 256) || !aligned(d_lengths, 2) || !aligned(d_msg_words, 8))
+        return ZFPX_EINVAL;
+    const int64_t G = plan_blocks(p, nullptr, nullptr, nullptr);
+    if (cap < (size_t)G * 128) return ZFPX_ESIZE;
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanAccWork w;
+    int rc = plan_acc_setup(p, d_work, work_bytes, st, &w);
+    if (rc) return rc;
+    if (G == 0)                                    // every message empty
+        return cudaMemsetAsync(d_msg_words, 0, p->msgs.size() * 8, st) == cudaSuccess ? ZFPX_OK : ZFPX_ECUDA;
+    int e = 0;
+    (void)frexp(tolerance, &e);
+    if ((rc = zfpx_pack_compress(p, 16, d_src, w.slots, (size_t)buffer_bytes(p, 16), ZFPX_LAYOUT_SEND, stream)))
+        return rc;
+    pacc_lengths_kernel<<<grid256(G), 256, 0, st>>>(w.P, w.slots, e - 1, d_lengths);
+    count_launch();
+    if ((rc = check_launch()) || (rc = acc_scan(w.scan, d_lengths, w.scan.total, st))) return rc;
+    pacc_messages_kernel<<<1, 32, 0, st>>>(w.P, w.scan.local, w.scan.tile_off, w.scan.total, d_msg_words, 1);
+    count_launch();
+    if (cudaMemsetAsync(d_payload, 0, (size_t)G * 128, st) != cudaSuccess) return ZFPX_ECUDA;
+    pacc_pack_kernel<<<grid256(G), 256, 0, st>>>(w.P, w.slots, d_lengths, w.scan.local, w.scan.tile_off,
+                                                 w.scan.total, reinterpret_cast<unsigned long long *>(d_payload));
+    count_launch();
+    return check_launch();
+}
+
+int zfpx_exchange_accuracy(zfpx_plan p, const uint64_t *d_msg_words, const uint16_t *d_len_send,
+                           const uint8_t *d_pay_send, uint16_t *d_len_recv, uint8_t *d_pay_recv, size_t cap,
+                           void *d_work, size_t work_bytes, void *stream)
+{
+    if (!p || !d_msg_words || !d_len_send || !d_pay_send || !d_len_recv || !d_pay_recv || !d_work || p->dims != 3)
+        return ZFPX_EINVAL;
+    if (!aligned(d_pay_send, 8) || !aligned(d_pay_recv, 8) || !aligned(d_work, 256)) return ZFPX_EINVAL;
+    const int64_t G = plan_blocks(p, nullptr, nullptr, nullptr);
+    if (cap < (size_t)G * 128) return ZFPX_ESIZE;
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanAccWork w;
+    int rc = plan_acc_setup(p, d_work, work_bytes, st, &w);
+    if (rc || w.P.M == 0) return rc;
+    pacc_messages_kernel<<<1, 32, 0, st>>>(w.P, nullptr, nullptr, nullptr, const_cast<uint64_t *>(d_msg_words), 0);
+    count_launch();
+    pacc_exchange_kernel<<<(unsigned)w.P.M, 256, 0, st>>>(w.P, d_msg_words,
+                                                           reinterpret_cast<const uint64_t *>(d_pay_send),
+                                                           reinterpret_cast<uint64_t *>(d_pay_recv), d_len_send,
+                                                           d_len_recv, (int64_t)(cap / 8));
+    count_launch();
+    return check_launch();
+}
+
+int zfpx_decompress_unpack_accuracy(zfpx_plan p, const uint64_t *d_msg_words, const uint16_t *d_len_recv,
+                                    const uint8_t *d_pay_recv, size_t len, float *d_dst, void *d_work,
+                                    size_t work_bytes, void *stream)
+{
+    if (!p || !d_msg_words || !d_len_recv || !d_pay_recv || !d_dst || !d_work || p->dims != 3) return ZFPX_EINVAL;
+    if (!aligned(d_pay_recv, 8) || !aligned(d_work, 256) || !aligned(d_len_recv, 2)) return ZFPX_EINVAL;
+    const int64_t G = plan_blocks(p, nullptr, nullptr, nullptr);
+    cudaStream_t st = (cudaStream_t)stream;
+    PlanAccWork w;
+    int rc = plan_acc_setup(p, d_work, work_bytes, st, &w);
+    if (rc || G == 0) return rc;
+    pacc_messages_kernel<<<1, 32, 0, st>>>(w.P, nullptr, nullptr, nullptr, const_cast<uint64_t *>(d_msg_words), 0);
+    count_launch();
+    if ((rc = acc_scan(w.scan, d_len_recv, w.scan.total, st))) return rc;
+    pacc_unpack_kernel<<<grid256(G), 256, 0, st>>>(w.P, reinterpret_cast<const uint64_t *>(d_pay_recv),
+                                                   (int64_t)(len / 8), d_len_recv, w.scan.local, w.scan.tile_off,
+                                                   w.scan.total, w.slots);
+    count_launch();
+    if ((rc = check_launch())) return rc;
+    return zfpx_decompress_unpack(p, 16, w.slots, (size_t)buffer_bytes(p, 16), d_dst, ZFPX_LAYOUT_RECV, stream);
 }
 
 }  // extern "C"

@@ -69,7 +69,7 @@ int64_t message_bytes(const zfpx_plan_s *p, const HostMsg &m, int rate)
 }
 
 // Offsets of every message (send order index) in the given layout.
-static std::vector<int64_t> layout_offsets(const zfpx_plan_s *p, int rate, int layout, int64_t *total)
+std::vector<int64_t> layout_offsets(const zfpx_plan_s *p, int rate, int layout, int64_t *total)
 {
     const size_t M = p->msgs.size();
     std::vector<size_t> order(M);

@@ -111,6 +111,11 @@ def lib():
         "zfpx_accuracy_max_payload_bytes": ([i64p], sz),
         "zfpx_encode_accuracy": ([vp, i64p, i64p, ctypes.c_double, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_decode_accuracy": ([vp, vp, sz, i64p, i64p, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_plan_accuracy_blocks": ([vp], sz),
+        "zfpx_plan_accuracy_workspace_bytes": ([vp], sz),
+        "zfpx_pack_compress_accuracy": ([vp, ctypes.c_double, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_exchange_accuracy": ([vp, vp, vp, vp, vp, vp, sz, vp, sz, vp], ctypes.c_int),
+        "zfpx_decompress_unpack_accuracy": ([vp, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -334,6 +339,47 @@ def zfpx_decode_accuracy(lengths, payload, dst, work, stream=None):
     _check(lib().zfpx_decode_accuracy(_dev(lengths, "lengths"), _dev(payload, "payload"), _nbytes(payload),
                                       _i64x3(n), _i64x3(s), _dev(dst, "dst"), _dev(work, "work"), _nbytes(work),
                                       _stream(stream)), "zfpx_decode_accuracy")
+
+
+class AccuracyTransposition:
+    """The accuracy mode on a plan: pack+compress, the all-to-all-v and
+    decompress+unpack with device buffers owned here (PyTorch allocations)."""
+
+    def __init__(self, plan):
+        self.plan = plan
+        self.G = int(lib().zfpx_plan_accuracy_blocks(plan.handle))
+        M = plan.num_messages()
+        self.cap = max(8, 128 * self.G)
+        dev = "cuda"
+        self.len_send = torch.zeros(max(1, self.G), dtype=torch.int16, device=dev)
+        self.len_recv = torch.zeros_like(self.len_send)
+        self.pay_send = torch.zeros(self.cap, dtype=torch.uint8, device=dev)
+        self.pay_recv = torch.zeros_like(self.pay_send)
+        self.words = torch.zeros(max(1, M), dtype=torch.int64, device=dev)
+        self.work = torch.zeros(int(lib().zfpx_plan_accuracy_workspace_bytes(plan.handle)), dtype=torch.uint8,
+                                device=dev)
+
+    def compress(self, src, tolerance, stream=None):
+        self.plan._check_field(src, self.plan.src_strides, "src")
+        _check(lib().zfpx_pack_compress_accuracy(self.plan.handle, float(tolerance), _dev(src, "src"),
+                                                 _dev(self.len_send, "lengths"), _dev(self.pay_send, "payload"),
+                                                 self.cap, _dev(self.words, "words"), _dev(self.work, "work"),
+                                                 _nbytes(self.work), _stream(stream)), "zfpx_pack_compress_accuracy")
+
+    def exchange(self, stream=None):
+        _check(lib().zfpx_exchange_accuracy(self.plan.handle, _dev(self.words, "words"),
+                                            _dev(self.len_send, "len_send"), _dev(self.pay_send, "pay_send"),
+                                            _dev(self.len_recv, "len_recv"), _dev(self.pay_recv, "pay_recv"),
+                                            self.cap, _dev(self.work, "work"), _nbytes(self.work),
+                                            _stream(stream)), "zfpx_exchange_accuracy")
+
+    def decompress(self, dst, stream=None):
+        self.plan._check_field(dst, self.plan.dst_strides, "dst")
+        _check(lib().zfpx_decompress_unpack_accuracy(self.plan.handle, _dev(self.words, "words"),
+                                                     _dev(self.len_recv, "len_recv"), _dev(self.pay_recv, "pay_recv"),
+                                                     self.cap, _dev(dst, "dst"), _dev(self.work, "work"),
+                                                     _nbytes(self.work), _stream(stream)),
+               "zfpx_decompress_unpack_accuracy")
 
 
 class PairGraph:

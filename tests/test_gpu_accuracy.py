@@ -90,3 +90,64 @@ def test_t639_field_full_size(z):
     x = fieldgen.t639_field()
     L, bits = _check(z, x, torch.from_numpy(x).cuda(), 1e-3)
     assert 0 < bits < 16 * x.size                                    # variable, below the rate-16 cut
+
+
+# ---------------------------------------------------------------- plans: the all-to-all-v
+@pytest.mark.parametrize("t", [0, 1])
+@pytest.mark.parametrize("shape,pr,pc", [((17, 23, 37), 3, 2), ((20, 16, 48), 1, 4), ((3, 8, 8), 2, 4)])
+def test_plan_accuracy_matches_oracle(z, shape, pr, pc, t):
+    from oracle import plan as opl
+    rng = np.random.default_rng(sum(shape) + t)
+    nz, ny, nx = shape
+    x = (250.0 + np.cumsum(np.cumsum(rng.standard_normal(shape), axis=2), axis=1)).astype(np.float32)
+    tol = 1e-3 * float(np.abs(x).max())
+    xd = torch.from_numpy(x).cuda()
+    dst_store = torch.full((nz, ny, nx + 6), float("nan"), device="cuda")
+    dst = dst_store[:, :, :nx]
+    plan = z.Plan.for_fields(xd, pr, pc, t, 3, dst=dst)
+    acc = z.AccuracyTransposition(plan)
+    acc.compress(xd, tol)
+    acc.exchange()
+    acc.decompress(dst)
+    torch.cuda.synchronize()
+    oplan = opl.Plan(nx, ny, nz, pr, pc, t, 3)
+    msgs = oplan.messages
+    exp = []
+    for m in msgs:
+        box = np.ascontiguousarray(x[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx])
+        if box.size == 0:
+            exp.append((np.zeros(0, np.uint16), np.zeros(0, np.uint8), 0))
+        else:
+            exp.append(oc.encode_accuracy(box, tol))
+    words = acc.words.cpu().numpy()[:len(msgs)]
+    np.testing.assert_array_equal(words, [(b + 63) // 64 for _, _, b in exp])
+    G = acc.G
+    len_send = acc.len_send.cpu().numpy().view(np.uint16)[:G]
+    np.testing.assert_array_equal(len_send, np.concatenate([L for L, _, _ in exp]) if G else len_send)
+    pay_send = acc.pay_send.cpu().numpy()
+    o = 0
+    for (L, P, b), w in zip(exp, words):
+        nb = (b + 7) // 8
+        assert pay_send[8 * o:8 * o + nb].tobytes() == P[:nb].tobytes()
+        o += int(w)
+    # receive order: by destination rank, then source peer
+    rorder = sorted(range(len(msgs)), key=lambda i: (msgs[i].dst, msgs[i].src_peer))
+    len_recv = acc.len_recv.cpu().numpy().view(np.uint16)[:G]
+    if G:
+        np.testing.assert_array_equal(len_recv, np.concatenate([exp[i][0] for i in rorder]))
+    pay_recv = acc.pay_recv.cpu().numpy()
+    o = 0
+    for i in rorder:
+        L, P, b = exp[i]
+        nb = (b + 7) // 8
+        assert pay_recv[8 * o:8 * o + nb].tobytes() == P[:nb].tobytes()
+        o += int(words[i])
+    rdst = np.full_like(x, np.nan)
+    for m, (L, P, b) in zip(msgs, exp):
+        if m.nx * m.ny * m.nz == 0:
+            continue
+        box = np.empty((m.nz, m.ny, m.nx), np.float32)
+        oc.decode_accuracy(L, P, box)
+        rdst[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx] = box
+    assert dst.cpu().numpy().view(np.uint32).tobytes() == rdst.view(np.uint32).tobytes()
+    assert torch.isnan(dst_store[:, :, nx:]).all()
