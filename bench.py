@@ -565,6 +565,24 @@ def extra_accuracy(z, xd, reps, peak):
                                "encode_ms": te, "decode_ms": td,
                                "encode_f32_GBps": fbytes / (te / 1e3) / 1e9, "decode_f32_GBps": fbytes / (td / 1e3) / 1e9}
     del lengths, payload, work, out
+    # the same field over the 8 x 8 plan: variable-size messages and the all-to-all-v
+    plan = z.Plan.for_fields(xd, PR, PC, 0, 3)
+    acc = z.AccuracyTransposition(plan)
+    for tol in (1e-2, 1e-3):
+        tc = _events_ms(lambda: acc.compress(xd, tol), reps)
+        tx = _events_ms(lambda: acc.exchange(), reps)
+        res.setdefault("plan_8x8", {})
+        out2 = torch.empty_like(xd)
+        td = _events_ms(lambda: acc.decompress(out2), reps)
+        w = acc.words.cpu().numpy()
+        res["plan_8x8"]["tol_%g" % tol] = {
+            "compress_ms": tc, "exchange_ms": tx, "decompress_ms": td,
+            "message_bytes_min_median_max": [int(8 * w.min()), int(8 * np.median(w)), int(8 * w.max())],
+            "bits_per_value": float(64 * w.sum()) / xd.numel(),
+            "max_abs_error": float((out2.double() - x64).abs().max())}
+        del out2
+    del acc
+    plan.close()
     return res
 
 
