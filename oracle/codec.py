@@ -62,6 +62,8 @@ def lib():
         L.zfpo_encode_accuracy.argtypes = [ctypes.c_void_p, i64p, i64p, ctypes.c_double, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
         L.zfpo_decode_accuracy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p]
+        L.zfpo_encode_precision.argtypes = [ctypes.c_void_p, i64p, i64p, ctypes.c_int, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
         _lib = L
     return _lib
 
@@ -231,6 +233,16 @@ def accuracy_kmin(emax, minexp):
 def encode_accuracy(a, tol):
     """Accuracy-mode coding of a float32 array indexed [z][y][x] (any strides) with
     3-D blocks.  Returns (lengths uint16 per block, payload bytes, total bits)."""
+    return _encode_variable(a, float(tol), None)
+
+
+def encode_precision(a, prec):
+    """Precision-mode coding (the top `prec` bit planes of every block); the same
+    output as encode_accuracy and decoded by decode_accuracy."""
+    return _encode_variable(a, None, int(prec))
+
+
+def _encode_variable(a, tol, prec):
     nz, ny, nx = a.shape
     n = (nx, ny, nz)
     nblk = block_count(3, n)
@@ -238,10 +250,13 @@ def encode_accuracy(a, tol):
     lengths = np.zeros(max(nblk, 1), dtype=np.uint16)
     payload = np.zeros(max(cap, 1), dtype=np.uint8)
     bits = ctypes.c_uint64(0)
-    rc = lib().zfpo_encode_accuracy(a.ctypes.data_as(ctypes.c_void_p), _i64x3(n), _i64x3(_strides_elems(a)),
-                                    float(tol), _ptr(lengths), _ptr(payload), cap, ctypes.byref(bits))
+    args = (a.ctypes.data_as(ctypes.c_void_p), _i64x3(n), _i64x3(_strides_elems(a)))
+    if prec is None:
+        rc = lib().zfpo_encode_accuracy(*args, tol, _ptr(lengths), _ptr(payload), cap, ctypes.byref(bits))
+    else:
+        rc = lib().zfpo_encode_precision(*args, prec, _ptr(lengths), _ptr(payload), cap, ctypes.byref(bits))
     if rc:
-        raise ValueError("zfpo_encode_accuracy failed: %d" % rc)
+        raise ValueError("variable-rate encode failed: %d" % rc)
     total = int(bits.value)
     return lengths[:nblk], payload[:(total + 7) // 8], total
 

@@ -597,8 +597,10 @@ static uint64_t encode_planes_down_to(bitw *w, int S, const uint32_t *u, uint64_
     return budget - left;
 }
 
-/* One block's bits in accuracy mode, written at w (buffer zeroed); returns L. */
-static uint64_t encode_block_accuracy(bitw *w, const float *v, int minexp)
+/* One block's bits in accuracy mode (prec == 0) or precision mode (prec in
+ * 1..32: planes 31 down to 32 - prec, the mode that keeps a fixed number of
+ * bit planes per block), written at w (buffer zeroed); returns L. */
+static uint64_t encode_block_accuracy(bitw *w, const float *v, int minexp, int prec)
 {
     const uint64_t start = w->pos;
     double M = 0.0;
@@ -615,7 +617,7 @@ static uint64_t encode_block_accuracy(bitw *w, const float *v, int minexp)
     put_bit(w, 1);
     unsigned e = (unsigned)(emax + 127);
     for (int b = 0; b < 8; b++) put_bit(w, (e >> b) & 1u);
-    const int kmin = zfpo_accuracy_kmin(emax, minexp);
+    const int kmin = prec > 0 ? 32 - prec : zfpo_accuracy_kmin(emax, minexp);
     if (kmin < 32) {
         int32_t q[64];
         for (int i = 0; i < 64; i++) q[i] = (int32_t)ldexp((double)v[i], 30 - emax);
@@ -654,14 +656,12 @@ static void gather3(const float *base, const int64_t n[3], const int64_t s[3],
             }
 }
 
-int zfpo_encode_accuracy(const float *base, const int64_t n[3], const int64_t s[3], double tol,
-                         uint16_t *lengths, uint8_t *payload, int64_t payload_bytes, uint64_t *total_bits)
+static int encode_variable(const float *base, const int64_t n[3], const int64_t s[3], int minexp, int prec,
+                           uint16_t *lengths, uint8_t *payload, int64_t payload_bytes, uint64_t *total_bits)
 {
-    if (!(tol > 0.0) || !isfinite(tol)) return -1;
     if (n[0] < 1 || n[1] < 1 || n[2] < 1) { *total_bits = 0; return 0; }
     if (payload_bytes < zfpo_accuracy_max_payload_bytes(n)) return -2;
     memset(payload, 0, (size_t)payload_bytes);
-    const int minexp = zfpo_accuracy_minexp(tol);
     bitw w = {payload, 0};
     float v[64];
     int64_t bx = (n[0] + 3) / 4, by = (n[1] + 3) / 4, bz = (n[2] + 3) / 4, b = 0;
@@ -669,10 +669,26 @@ int zfpo_encode_accuracy(const float *base, const int64_t n[3], const int64_t s[
         for (int64_t yb = 0; yb < by; yb++)
             for (int64_t xb = 0; xb < bx; xb++) {
                 gather3(base, n, s, xb, yb, zb, v);
-                lengths[b++] = (uint16_t)encode_block_accuracy(&w, v, minexp);
+                lengths[b++] = (uint16_t)encode_block_accuracy(&w, v, minexp, prec);
             }
     *total_bits = w.pos;
     return 0;
+}
+
+int zfpo_encode_accuracy(const float *base, const int64_t n[3], const int64_t s[3], double tol,
+                         uint16_t *lengths, uint8_t *payload, int64_t payload_bytes, uint64_t *total_bits)
+{
+    if (!(tol > 0.0) || !isfinite(tol)) return -1;
+    return encode_variable(base, n, s, zfpo_accuracy_minexp(tol), 0, lengths, payload, payload_bytes, total_bits);
+}
+
+/* Precision mode: every block keeps its top `prec` bit planes (1..32), same
+ * stream layout and cut as the accuracy mode; decoded by zfpo_decode_accuracy. */
+int zfpo_encode_precision(const float *base, const int64_t n[3], const int64_t s[3], int prec,
+                          uint16_t *lengths, uint8_t *payload, int64_t payload_bytes, uint64_t *total_bits)
+{
+    if (prec < 1 || prec > 32) return -1;
+    return encode_variable(base, n, s, 0, prec, lengths, payload, payload_bytes, total_bits);
 }
 
 int zfpo_decode_accuracy(const uint16_t *lengths, const uint8_t *payload, const int64_t n[3],

@@ -1,4 +1,4 @@
-"""Pins of the oracle's accuracy mode (variable-rate coding to an absolute
+"""Pins of the oracle's accuracy and precision modes (variable-rate coding to an absolute
 error tolerance, 3-D blocks; the mode the paper names and leaves for future
 work, Sec. II-C).  Each pin ties it to something fixed independently: the
 error bound the plane cut-off is chosen for, the embedded property of the
@@ -108,3 +108,48 @@ def test_second_statement_agrees(rel):
         assert [int(l) for l in L] == [len(zp.encode_block_accuracy(b, tol))
                                       for b in _blocks(a.astype(np.float64)).astype(np.float32)]
         np.testing.assert_array_equal(np.unpackbits(P, bitorder="little")[:bits], np.array(stream, np.uint8))
+
+
+# ---------------------------------------------------------------- precision mode
+def test_precision_error_bound_prefix_and_monotone():
+    # planes 31 .. 32 - p kept: by the same argument as the accuracy cut-off the
+    # error of an uncut block stays below 2^(e_max - p + 9); the bits are a prefix
+    # of the rate-16 stream and grow with p
+    for a in _fields():
+        x = a.astype(np.float64)
+        blk = _blocks(x)
+        prev_bits, prev_err = 0, np.inf
+        for p in (2, 6, 10, 14, 18, 24):
+            L, P, bits = codec.encode_precision(a, p)
+            out = np.empty_like(a)
+            codec.decode_accuracy(L, P, out)
+            err = _blocks(np.abs(out.astype(np.float64) - x))
+            for b in range(blk.shape[0]):
+                m = np.abs(blk[b]).max()
+                if m > 0 and L[b] < 1024:
+                    assert err[b].max() <= 2.0 ** (np.frexp(m)[1] - p + 9), (p, b)
+            assert bits >= prev_bits
+            e = np.linalg.norm(out - x)
+            assert e <= prev_err
+            prev_bits, prev_err = bits, e
+    rng = np.random.default_rng(44)
+    for _ in range(100):
+        v = (np.cumsum(rng.standard_normal(64)) * 10.0 ** rng.uniform(-8, 8)).astype(np.float32)
+        fixed = np.unpackbits(codec.encode_block(3, 16, v), bitorder="little")
+        for p in (1, 5, 11, 17, 32):
+            L, P, bits = codec.encode_precision(v.reshape(4, 4, 4), p)
+            np.testing.assert_array_equal(np.unpackbits(P, bitorder="little")[:bits], fixed[:bits])
+
+
+@pytest.mark.parametrize("p", [3, 12, 20])
+def test_precision_second_statement_agrees(p):
+    rng = np.random.default_rng(45 + p)
+    a = np.ascontiguousarray((rng.standard_normal((5, 7, 9)) * 10.0 ** rng.uniform(-5, 5)).astype(np.float32))
+    L, P, bits = codec.encode_precision(a, p)
+    stream, lens = [], []
+    for blk in _blocks(a.astype(np.float64)).astype(np.float32):
+        bb = zp._code(3, blk, 1024 - 9, lambda e: 32 - p)
+        stream += bb
+        lens.append(len(bb))
+    assert [int(l) for l in L] == lens
+    np.testing.assert_array_equal(np.unpackbits(P, bitorder="little")[:bits], np.array(stream, np.uint8))
