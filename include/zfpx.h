@@ -193,7 +193,7 @@ ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[
 ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                 const int64_t stride[3], float *d_out, void *stream);
 
-/* ---- accuracy mode: variable rate to an absolute tolerance (3-D blocks) ---
+/* ---- accuracy and precision modes: variable rate (3-D blocks) --------------
  * The ZFP mode the paper names and leaves for future work (Sec. II-C).  Every
  * 4x4x4 block (raster order, partial blocks edge-replicated as in the raw
  * codec) keeps its bit planes 31 .. kmin, kmin = clamp(floor(log2 tolerance)
@@ -217,6 +217,12 @@ ZFPX_API size_t zfpx_accuracy_max_payload_bytes(const int64_t n[3]);
 ZFPX_API int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t stride[3], double tolerance,
                                   uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
                                   void *d_work, size_t work_bytes, void *stream);
+/* Precision mode: every block keeps its top `precision` bit planes (1..32), the
+ * same cut, output and scratch as the accuracy mode; zfpx_decode_accuracy
+ * decodes it. */
+ZFPX_API int zfpx_encode_precision(const float *d_in, const int64_t n[3], const int64_t stride[3], int precision,
+                                   uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                                   void *d_work, size_t work_bytes, void *stream);
 ZFPX_API int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_payload, size_t len,
                                   const int64_t n[3], const int64_t stride[3], float *d_out, void *d_work,
                                   size_t work_bytes, void *stream);
@@ -242,6 +248,10 @@ ZFPX_API size_t zfpx_plan_accuracy_workspace_bytes(zfpx_plan plan);
 ZFPX_API int zfpx_pack_compress_accuracy(zfpx_plan plan, double tolerance, const float *d_src, uint16_t *d_lengths,
                                          uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
                                          size_t work_bytes, void *stream);
+/* The precision mode on a plan (the same layout; exchange and decode as above). */
+ZFPX_API int zfpx_pack_compress_precision(zfpx_plan plan, int precision, const float *d_src, uint16_t *d_lengths,
+                                          uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                          size_t work_bytes, void *stream);
 ZFPX_API int zfpx_exchange_accuracy(zfpx_plan plan, const uint64_t *d_msg_words, const uint16_t *d_len_send,
                                     const uint8_t *d_pay_send, uint16_t *d_len_recv, uint8_t *d_pay_recv, size_t cap,
                                     void *d_work, size_t work_bytes, void *stream);

@@ -1,6 +1,8 @@
-// Accuracy mode: variable-rate coding of 3-D blocks to an absolute error
-// tolerance (the ZFP mode the paper names and leaves for future work, Sec.
-// II-C), built on the fixed-rate kernels.
+// Accuracy and precision modes: variable-rate coding of 3-D blocks to an
+// absolute error tolerance, or to a fixed number of bit planes per block (the
+// ZFP modes the paper names and leaves for future work, Sec. II-C), built on
+// the fixed-rate kernels.  Precision p keeps planes 31 .. 32 - p; the rest of
+// what follows holds for both.
 //
 // Readings (identical in the CPU oracle): minexp = floor(log2 tol); a block
 // with exponent e_max keeps its bit planes 31 .. kmin, kmin = clamp(minexp -
@@ -34,8 +36,10 @@ constexpr int kTile = 1024;                  // blocks per scan tile (one CTA)
 constexpr int kSlotWords = 16;               // 1024 bits per block slot
 constexpr int kCutBits = 64 * kSlotWords;
 
-__device__ __forceinline__ int acc_kmin(int emax, int minexp)
+// Lowest plane kept: the accuracy rule, or 32 - prec in precision mode (prec > 0).
+__device__ __forceinline__ int acc_kmin(int emax, int minexp, int prec)
 {
+    if (prec > 0) return 32 - prec;
     const int k = minexp - emax + 22;
     return k < 0 ? 0 : (k > 32 ? 32 : k);
 }
@@ -56,7 +60,7 @@ struct SlotReader {
 
 // L for every block: parse the slot's planes 31 .. kmin with the rate-16 budget.
 __global__ void __launch_bounds__(256) acc_lengths_kernel(const uint64_t *__restrict__ slots, int64_t nblocks,
-                                                          int minexp, uint16_t *__restrict__ lengths)
+                                                          int minexp, int prec, uint16_t *__restrict__ lengths)
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nblocks) return;
@@ -67,7 +71,7 @@ __global__ void __launch_bounds__(256) acc_lengths_kernel(const uint64_t *__rest
         L = 1;
     } else {
         const int emax = (int)((head >> 1) & 0xffu) - 127;
-        const int kmin = acc_kmin(emax, minexp);
+        const int kmin = acc_kmin(emax, minexp, prec);
         SlotReader rd{w, 9};
         int n = 0, R = kCutBits - 9;
 #pragma unroll 1
@@ -266,26 +270,22 @@ size_t zfpx_accuracy_max_payload_bytes(const int64_t n[3])
     return (size_t)acc_blocks(n) * 128;
 }
 
-int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t stride[3], double tolerance,
-                         uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
-                         void *d_work, size_t work_bytes, void *stream)
+static int encode_variable(const float *d_in, const int64_t n[3], const int64_t stride[3], int minexp, int prec,
+                           uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                           void *d_work, size_t work_bytes, void *stream)
 {
     if (!d_in || !n || !stride || !d_lengths || !d_payload || !d_total_bits || !d_work) return ZFPX_EINVAL;
-    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
     for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return ZFPX_EINVAL;
     if (!aligned(d_payload, 8) || !aligned(d_work, 256) || !aligned(d_lengths, 2) || !aligned(d_total_bits, 8))
         return ZFPX_EINVAL;
     const int64_t nb = acc_blocks(n);
     if (cap < (size_t)nb * 128 || work_bytes < acc_work_bytes(nb)) return ZFPX_ESIZE;
-    int e = 0;
-    (void)frexp(tolerance, &e);
-    const int minexp = e - 1;                           // floor(log2 tolerance)
     cudaStream_t st = (cudaStream_t)stream;
     const AccWork a = acc_carve(d_work, nb);
     int rc = zfpx_encode(3, 16, d_in, n, stride, reinterpret_cast<uint8_t *>(a.slots), (size_t)nb * 128, stream);
     if (rc) return rc;
     const unsigned grid = (unsigned)((nb + 255) / 256);
-    acc_lengths_kernel<<<grid, 256, 0, st>>>(a.slots, nb, minexp, d_lengths);
+    acc_lengths_kernel<<<grid, 256, 0, st>>>(a.slots, nb, minexp, prec, d_lengths);
     count_launch();
     if ((rc = check_launch())) return rc;
     if ((rc = acc_scan(a, d_lengths, d_total_bits, st))) return rc;
@@ -294,6 +294,26 @@ int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t st
                                           reinterpret_cast<unsigned long long *>(d_payload));
     count_launch();
     return check_launch();
+}
+
+int zfpx_encode_accuracy(const float *d_in, const int64_t n[3], const int64_t stride[3], double tolerance,
+                         uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                         void *d_work, size_t work_bytes, void *stream)
+{
+    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
+    int e = 0;
+    (void)frexp(tolerance, &e);                         // floor(log2 tolerance) = e - 1
+    return encode_variable(d_in, n, stride, e - 1, 0, d_lengths, d_payload, cap, d_total_bits, d_work,
+                           work_bytes, stream);
+}
+
+int zfpx_encode_precision(const float *d_in, const int64_t n[3], const int64_t stride[3], int precision,
+                          uint16_t *d_lengths, uint8_t *d_payload, size_t cap, uint64_t *d_total_bits,
+                          void *d_work, size_t work_bytes, void *stream)
+{
+    if (precision < 1 || precision > 32) return ZFPX_EINVAL;
+    return encode_variable(d_in, n, stride, 0, precision, d_lengths, d_payload, cap, d_total_bits, d_work,
+                           work_bytes, stream);
 }
 
 int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_payload, size_t len, const int64_t n[3],
@@ -364,7 +384,7 @@ __device__ __forceinline__ uint64_t goff(const uint32_t *local, const uint64_t *
 }
 
 __global__ void __launch_bounds__(256) pacc_lengths_kernel(PlanAcc P, const uint8_t *__restrict__ slots, int minexp,
-                                                           uint16_t *__restrict__ lengths)
+                                                           int prec, uint16_t *__restrict__ lengths)
 {
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= P.G) return;
@@ -374,7 +394,7 @@ __global__ void __launch_bounds__(256) pacc_lengths_kernel(PlanAcc P, const uint
     const uint64_t head = __ldg(w);
     int L = 1;
     if (head & 1ull) {
-        const int kmin = acc_kmin((int)((head >> 1) & 0xffu) - 127, minexp);
+        const int kmin = acc_kmin((int)((head >> 1) & 0xffu) - 127, minexp, prec);
         SlotReader rd{w, 9};
         int n = 0, R = kCutBits - 9;
 #pragma unroll 1
@@ -592,12 +612,11 @@ size_t zfpx_plan_accuracy_workspace_bytes(zfpx_plan p)
     return plan_acc_bytes(p, plan_blocks(p, nullptr, nullptr, nullptr));
 }
 
-int zfpx_pack_compress_accuracy(zfpx_plan p, double tolerance, const float *d_src, uint16_t *d_lengths,
-                                uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
-                                size_t work_bytes, void *stream)
+static int pack_compress_variable(zfpx_plan p, int minexp, int prec, const float *d_src, uint16_t *d_lengths,
+                                  uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                  size_t work_bytes, void *stream)
 {
     if (!p || !d_src || !d_lengths || !d_payload || !d_msg_words || !d_work || p->dims != 3) return ZFPX_EINVAL;
-    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
     if (!aligned(d_payload, 8) || !aligned(d_work, 256) || !aligned(d_lengths, 2) || !aligned(d_msg_words, 8))
         return ZFPX_EINVAL;
     const int64_t G = plan_blocks(p, nullptr, nullptr, nullptr);
@@ -608,11 +627,9 @@ int zfpx_pack_compress_accuracy(zfpx_plan p, double tolerance, const float *d_sr
     if (rc) return rc;
     if (G == 0)                                    // every message empty
         return cudaMemsetAsync(d_msg_words, 0, p->msgs.size() * 8, st) == cudaSuccess ? ZFPX_OK : ZFPX_ECUDA;
-    int e = 0;
-    (void)frexp(tolerance, &e);
     if ((rc = zfpx_pack_compress(p, 16, d_src, w.slots, (size_t)buffer_bytes(p, 16), ZFPX_LAYOUT_SEND, stream)))
         return rc;
-    pacc_lengths_kernel<<<grid256(G), 256, 0, st>>>(w.P, w.slots, e - 1, d_lengths);
+    pacc_lengths_kernel<<<grid256(G), 256, 0, st>>>(w.P, w.slots, minexp, prec, d_lengths);
     count_launch();
     if ((rc = check_launch()) || (rc = acc_scan(w.scan, d_lengths, w.scan.total, st))) return rc;
     pacc_messages_kernel<<<1, 32, 0, st>>>(w.P, w.scan.local, w.scan.tile_off, w.scan.total, d_msg_words, 1);
@@ -622,6 +639,26 @@ int zfpx_pack_compress_accuracy(zfpx_plan p, double tolerance, const float *d_sr
                                                  w.scan.total, reinterpret_cast<unsigned long long *>(d_payload));
     count_launch();
     return check_launch();
+}
+
+int zfpx_pack_compress_accuracy(zfpx_plan p, double tolerance, const float *d_src, uint16_t *d_lengths,
+                                uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                size_t work_bytes, void *stream)
+{
+    if (!(tolerance > 0.0) || !(tolerance < HUGE_VAL)) return ZFPX_EINVAL;
+    int e = 0;
+    (void)frexp(tolerance, &e);
+    return pack_compress_variable(p, e - 1, 0, d_src, d_lengths, d_payload, cap, d_msg_words, d_work, work_bytes,
+                                  stream);
+}
+
+int zfpx_pack_compress_precision(zfpx_plan p, int precision, const float *d_src, uint16_t *d_lengths,
+                                 uint8_t *d_payload, size_t cap, uint64_t *d_msg_words, void *d_work,
+                                 size_t work_bytes, void *stream)
+{
+    if (precision < 1 || precision > 32) return ZFPX_EINVAL;
+    return pack_compress_variable(p, 0, precision, d_src, d_lengths, d_payload, cap, d_msg_words, d_work,
+                                  work_bytes, stream);
 }
 
 int zfpx_exchange_accuracy(zfpx_plan p, const uint64_t *d_msg_words, const uint16_t *d_len_send,

@@ -114,6 +114,8 @@ def lib():
         "zfpx_plan_accuracy_blocks": ([vp], sz),
         "zfpx_plan_accuracy_workspace_bytes": ([vp], sz),
         "zfpx_pack_compress_accuracy": ([vp, ctypes.c_double, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_pack_compress_precision": ([vp, ctypes.c_int, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_encode_precision": ([vp, i64p, i64p, ctypes.c_int, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_exchange_accuracy": ([vp, vp, vp, vp, vp, vp, sz, vp, sz, vp], ctypes.c_int),
         "zfpx_decompress_unpack_accuracy": ([vp, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
@@ -333,6 +335,18 @@ def zfpx_encode_accuracy(src, tolerance, lengths, payload, total_bits, work, str
                                       _stream(stream)), "zfpx_encode_accuracy")
 
 
+def zfpx_encode_precision(src, precision, lengths, payload, total_bits, work, stream=None):
+    """Precision-mode encode (every block keeps its top `precision` bit planes);
+    the same buffers as zfpx_encode_accuracy, decoded by zfpx_decode_accuracy."""
+    if src.dtype != torch.float32:
+        raise ValueError("src must be float32")
+    n, s = field_view(src)
+    _check(lib().zfpx_encode_precision(_dev(src, "src"), _i64x3(n), _i64x3(s), int(precision),
+                                       _dev(lengths, "lengths"), _dev(payload, "payload"), _nbytes(payload),
+                                       _dev(total_bits, "total_bits"), _dev(work, "work"), _nbytes(work),
+                                       _stream(stream)), "zfpx_encode_precision")
+
+
 def zfpx_decode_accuracy(lengths, payload, dst, work, stream=None):
     """Accuracy-mode decode into the float32 field dst (any strides)."""
     n, s = field_view(dst)
@@ -342,8 +356,9 @@ def zfpx_decode_accuracy(lengths, payload, dst, work, stream=None):
 
 
 class AccuracyTransposition:
-    """The accuracy mode on a plan: pack+compress, the all-to-all-v and
-    decompress+unpack with device buffers owned here (PyTorch allocations)."""
+    """The accuracy (or precision) mode on a plan: pack+compress, the
+    all-to-all-v and decompress+unpack with device buffers owned here (PyTorch
+    allocations)."""
 
     def __init__(self, plan):
         self.plan = plan
@@ -365,6 +380,13 @@ class AccuracyTransposition:
                                                  _dev(self.len_send, "lengths"), _dev(self.pay_send, "payload"),
                                                  self.cap, _dev(self.words, "words"), _dev(self.work, "work"),
                                                  _nbytes(self.work), _stream(stream)), "zfpx_pack_compress_accuracy")
+
+    def compress_precision(self, src, precision, stream=None):
+        self.plan._check_field(src, self.plan.src_strides, "src")
+        _check(lib().zfpx_pack_compress_precision(self.plan.handle, int(precision), _dev(src, "src"),
+                                                  _dev(self.len_send, "lengths"), _dev(self.pay_send, "payload"),
+                                                  self.cap, _dev(self.words, "words"), _dev(self.work, "work"),
+                                                  _nbytes(self.work), _stream(stream)), "zfpx_pack_compress_precision")
 
     def exchange(self, stream=None):
         _check(lib().zfpx_exchange_accuracy(self.plan.handle, _dev(self.words, "words"),

@@ -151,3 +151,48 @@ def test_plan_accuracy_matches_oracle(z, shape, pr, pc, t):
         rdst[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx] = box
     assert dst.cpu().numpy().view(np.uint32).tobytes() == rdst.view(np.uint32).tobytes()
     assert torch.isnan(dst_store[:, :, nx:]).all()
+
+
+# ---------------------------------------------------------------- precision mode
+@pytest.mark.parametrize("p", [4, 12, 20, 32])
+def test_precision_arrays_and_plan(z, p):
+    from oracle import plan as opl
+    rng = np.random.default_rng(50 + p)
+    shape = (9, 13, 22)
+    x = (np.cumsum(np.cumsum(rng.standard_normal(shape), axis=2), axis=1) * 10.0 ** rng.uniform(-3, 3)).astype(np.float32)
+    src = torch.from_numpy(x).cuda()
+    n = tuple(reversed(shape))
+    nblk = 3 * 4 * 6
+    lengths = torch.zeros(nblk, dtype=torch.int16, device="cuda")
+    payload = torch.zeros(z.zfpx_accuracy_max_payload_bytes(n), dtype=torch.uint8, device="cuda")
+    total = torch.zeros(1, dtype=torch.int64, device="cuda")
+    work = torch.zeros(z.zfpx_accuracy_workspace_bytes(n), dtype=torch.uint8, device="cuda")
+    z.zfpx_encode_precision(src, p, lengths, payload, total, work)
+    dec = torch.full_like(src, float("nan"))
+    z.zfpx_decode_accuracy(lengths, payload, dec, work)
+    torch.cuda.synchronize()
+    rL, rP, rbits = oc.encode_precision(x, p)
+    assert int(total.item()) == rbits
+    np.testing.assert_array_equal(lengths.cpu().numpy().view(np.uint16), rL)
+    assert payload.cpu().numpy()[:(rbits + 7) // 8].tobytes() == rP.tobytes()
+    rdec = np.empty_like(x)
+    oc.decode_accuracy(rL, rP, rdec)
+    assert dec.cpu().numpy().view(np.uint32).tobytes() == rdec.view(np.uint32).tobytes()
+    # on a plan, through the all-to-all-v
+    plan = z.Plan.for_fields(src, 2, 3, 0, 3)
+    acc = z.AccuracyTransposition(plan)
+    acc.compress_precision(src, p)
+    acc.exchange()
+    out = torch.full_like(src, float("nan"))
+    acc.decompress(out)
+    torch.cuda.synchronize()
+    rout = np.full_like(x, np.nan)
+    for m in opl.Plan(n[0], n[1], n[2], 2, 3, 0, 3).messages:
+        if m.nx * m.ny * m.nz == 0:
+            continue
+        box = np.ascontiguousarray(x[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx])
+        L, P, b = oc.encode_precision(box, p)
+        o = np.empty_like(box)
+        oc.decode_accuracy(L, P, o)
+        rout[m.z0:m.z0 + m.nz, m.y0:m.y0 + m.ny, m.x0:m.x0 + m.nx] = o
+    assert out.cpu().numpy().view(np.uint32).tobytes() == rout.view(np.uint32).tobytes()
