@@ -62,6 +62,15 @@ def lib():
         L.zfpo_encode_accuracy.argtypes = [ctypes.c_void_p, i64p, i64p, ctypes.c_double, ctypes.c_void_p,
                                            ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
         L.zfpo_decode_accuracy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p]
+        L.zfpo_xform_forward_i64.argtypes = [ctypes.c_void_p]
+        L.zfpo_xform_inverse_i64.argtypes = [ctypes.c_void_p]
+        L.zfpo_stream_bytes_f64.argtypes = [ctypes.c_int, i64p]
+        L.zfpo_stream_bytes_f64.restype = ctypes.c_int64
+        L.zfpo_encode_block_f64.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.zfpo_decode_block_f64.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+        L.zfpo_encode_array_f64.argtypes = [ctypes.c_int, ctypes.c_void_p, i64p, i64p, ctypes.c_void_p,
+                                            ctypes.c_int64]
+        L.zfpo_decode_array_f64.argtypes = [ctypes.c_int, ctypes.c_void_p, i64p, ctypes.c_void_p, i64p]
         L.zfpo_encode_precision.argtypes = [ctypes.c_void_p, i64p, i64p, ctypes.c_int, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_uint64)]
         _lib = L
@@ -270,4 +279,67 @@ def decode_accuracy(lengths, payload, out):
                                     out.ctypes.data_as(ctypes.c_void_p), _i64x3(_strides_elems(out)))
     if rc:
         raise ValueError("zfpo_decode_accuracy failed: %d" % rc)
+    return out
+
+
+# ---------------------------------------------------------------- float64 fields (3-D blocks)
+def xform_forward_i64(q):
+    a = np.ascontiguousarray(q, dtype=np.int64).copy()
+    lib().zfpo_xform_forward_i64(_ptr(a))
+    return a
+
+
+def xform_inverse_i64(q):
+    a = np.ascontiguousarray(q, dtype=np.int64).copy()
+    lib().zfpo_xform_inverse_i64(_ptr(a))
+    return a
+
+
+def stream_bytes_f64(rate, n):
+    return int(lib().zfpo_stream_bytes_f64(rate, _i64x3(n)))
+
+
+def encode_block_f64(rate, v):
+    v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+    assert v.size == 64
+    out = np.zeros(8 * rate, dtype=np.uint8)
+    if lib().zfpo_encode_block_f64(rate, _ptr(v), _ptr(out)):
+        raise ValueError("invalid rate")
+    return out
+
+
+def decode_block_f64(rate, stream):
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    v = np.zeros(64, dtype=np.float64)
+    if lib().zfpo_decode_block_f64(rate, _ptr(stream), _ptr(v)):
+        raise ValueError("invalid rate")
+    return v
+
+
+def _strides_f64(a):
+    assert a.dtype == np.float64 and a.ndim == 3
+    sz, sy, sx = (s // 8 for s in a.strides)
+    return (sx, sy, sz)
+
+
+def encode_array_f64(rate, a):
+    """Encode a float64 array indexed [z][y][x] (any strides) with 3-D blocks."""
+    nz, ny, nx = a.shape
+    n = (nx, ny, nz)
+    nbytes = stream_bytes_f64(rate, n)
+    out = np.zeros(max(nbytes, 1), dtype=np.uint8)
+    rc = lib().zfpo_encode_array_f64(rate, a.ctypes.data_as(ctypes.c_void_p), _i64x3(n), _i64x3(_strides_f64(a)),
+                                     _ptr(out), nbytes)
+    if rc:
+        raise ValueError("zfpo_encode_array_f64 failed: %d" % rc)
+    return out[:nbytes]
+
+
+def decode_array_f64(rate, stream, out):
+    nz, ny, nx = out.shape
+    stream = np.ascontiguousarray(stream, dtype=np.uint8)
+    rc = lib().zfpo_decode_array_f64(rate, _ptr(stream), _i64x3((nx, ny, nz)), out.ctypes.data_as(ctypes.c_void_p),
+                                     _i64x3(_strides_f64(out)))
+    if rc:
+        raise ValueError("zfpo_decode_array_f64 failed: %d" % rc)
     return out

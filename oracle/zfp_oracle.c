@@ -719,3 +719,201 @@ int zfpo_decode_accuracy(const uint16_t *lengths, const uint8_t *payload, const 
             }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* float64 fields (the paper cites CAMS data in float64, Sec. III; its own  */
+/* fields are float32), 3-D blocks, fixed rate r bits per value (1..64).    */
+/* The same steps with the double format's sizes (readings):                */
+/*   e_max = frexp exponent of max|x|; zero block if max|x| is 0, below      */
+/*   2^-1023 (e_max + 1023 <= 0) or non-finite: one 0 bit;                   */
+/*   header: a 1 bit, then e_max + 1023 in 11 bits, LSB first;               */
+/*   q = trunc(x 2^(62 - e_max)) as int64 (|q| < 2^62);                      */
+/*   the same five-step lifting in int64 (floor halving), axes x, y, z;      */
+/*   the same coefficient order; negabinary with 0xAAAA...AA (64 bits);      */
+/*   bit planes 63 .. 0 with the same group-tested coder, cut at 64 r bits;  */
+/*   decode x = q 2^(e_max - 62) rounded once to nearest even.               */
+/* ------------------------------------------------------------------------ */
+typedef __int128 i128;
+
+static i128 wrap64(i128 v)
+{
+    const int64_t w = (int64_t)(uint64_t)(unsigned __int128)v;
+    if ((i128)w != v) g_overflow++;
+    return w;
+}
+static i128 floor_half128(i128 v) { return (v - (v & 1)) / 2; }
+#define INT64_HALF(v) floor_half128(wrap64(v))
+
+static void lift_forward_i64(int64_t *p, ptrdiff_t s)
+{
+    i128 a = p[0], b = p[s], c = p[2 * s], d = p[3 * s];
+    LIFT_FORWARD(a, b, c, d, INT64_HALF);
+    p[0] = (int64_t)wrap64(a); p[s] = (int64_t)wrap64(b);
+    p[2 * s] = (int64_t)wrap64(c); p[3 * s] = (int64_t)wrap64(d);
+}
+static void lift_inverse_i64(int64_t *p, ptrdiff_t s)
+{
+    i128 a = p[0], b = p[s], c = p[2 * s], d = p[3 * s];
+    LIFT_INVERSE(a, b, c, d, INT64_HALF);
+    p[0] = (int64_t)wrap64(a); p[s] = (int64_t)wrap64(b);
+    p[2 * s] = (int64_t)wrap64(c); p[3 * s] = (int64_t)wrap64(d);
+}
+
+void zfpo_xform_forward_i64(int64_t *q)
+{
+    for (int k = 0; k < 4; k++)
+        for (int j = 0; j < 4; j++) lift_forward_i64(q + 4 * j + 16 * k, 1);
+    for (int k = 0; k < 4; k++)
+        for (int i = 0; i < 4; i++) lift_forward_i64(q + i + 16 * k, 4);
+    for (int j = 0; j < 4; j++)
+        for (int i = 0; i < 4; i++) lift_forward_i64(q + i + 4 * j, 16);
+}
+void zfpo_xform_inverse_i64(int64_t *q)
+{
+    for (int j = 0; j < 4; j++)
+        for (int i = 0; i < 4; i++) lift_inverse_i64(q + i + 4 * j, 16);
+    for (int k = 0; k < 4; k++)
+        for (int i = 0; i < 4; i++) lift_inverse_i64(q + i + 16 * k, 4);
+    for (int k = 0; k < 4; k++)
+        for (int j = 0; j < 4; j++) lift_inverse_i64(q + 4 * j + 16 * k, 1);
+}
+
+static const uint64_t kNega64 = 0xAAAAAAAAAAAAAAAAull;
+
+static void encode_block_f64(bitw *w, int rate, const double *v)
+{
+    const uint64_t maxbits = 64ull * (uint64_t)rate;
+    const uint64_t start = w->pos;
+    double M = 0.0;
+    for (int i = 0; i < 64; i++) {
+        double a = fabs(v[i]);
+        if (a > M || a != a) M = a;
+    }
+    int emax = 0, zero = 1;
+    if (M > 0.0 && isfinite(M)) {
+        (void)frexp(M, &emax);
+        zero = (emax + 1023 <= 0);
+    }
+    if (zero) { put_bit(w, 0); w->pos = start + maxbits; return; }
+    put_bit(w, 1);
+    unsigned e = (unsigned)(emax + 1023);
+    for (int b = 0; b < 11; b++) put_bit(w, (e >> b) & 1u);
+    int64_t q[64];
+    for (int i = 0; i < 64; i++) q[i] = (int64_t)ldexp(v[i], 62 - emax);     /* exact, truncates */
+    zfpo_xform_forward_i64(q);
+    int order[64];
+    zfpo_sequency_order(3, order);
+    uint64_t u[64];
+    for (int t = 0; t < 64; t++) u[t] = ((uint64_t)q[order[t]] + kNega64) ^ kNega64;
+    uint64_t left = maxbits - 12;
+    int n = 0;
+    for (int k = 63; k >= 0 && left > 0; k--) {
+        unsigned X[64];
+        for (int i = 0; i < 64; i++) X[i] = (unsigned)((u[i] >> k) & 1u);
+        if (code_plane(w, 64, X, &n, &left)) break;
+    }
+    w->pos = start + maxbits;
+}
+
+static void decode_block_f64(bitr *r, int rate, double *v)
+{
+    const uint64_t maxbits = 64ull * (uint64_t)rate;
+    const uint64_t start = r->pos;
+    if (!get_bit(r)) {
+        for (int i = 0; i < 64; i++) v[i] = 0.0;
+        r->pos = start + maxbits;
+        return;
+    }
+    unsigned e = 0;
+    for (int b = 0; b < 11; b++) e |= get_bit(r) << b;
+    const int emax = (int)e - 1023;
+    uint64_t u[64];
+    for (int i = 0; i < 64; i++) u[i] = 0;
+    uint64_t left = maxbits - 12;
+    int n = 0;
+    for (int k = 63; k >= 0 && left > 0; k--) {
+        unsigned X[64];
+        for (int i = 0; i < 64; i++) X[i] = 0;
+        int stopped = decode_plane(r, 64, X, &n, &left);
+        for (int i = 0; i < 64; i++) u[i] |= (uint64_t)X[i] << k;
+        if (stopped) break;
+    }
+    int order[64];
+    zfpo_sequency_order(3, order);
+    int64_t q[64];
+    for (int t = 0; t < 64; t++) q[order[t]] = (int64_t)((u[t] ^ kNega64) - kNega64);
+    zfpo_xform_inverse_i64(q);
+    for (int i = 0; i < 64; i++)
+        v[i] = (double)ldexpl((long double)q[i], emax - 62);    /* q exact in long double: one rounding */
+    r->pos = start + maxbits;
+}
+
+static int valid_rate_f64(int rate) { return rate >= 1 && rate <= 64; }
+
+int64_t zfpo_stream_bytes_f64(int rate, const int64_t n[3])
+{
+    return (zfpo_block_count(3, n) * 64 * rate + 7) / 8;
+}
+
+int zfpo_encode_block_f64(int rate, const double *v, uint8_t *out /* zeroed */)
+{
+    if (!valid_rate_f64(rate)) return -1;
+    bitw w = {out, 0};
+    encode_block_f64(&w, rate, v);
+    return 0;
+}
+int zfpo_decode_block_f64(int rate, const uint8_t *in, double *v)
+{
+    if (!valid_rate_f64(rate)) return -1;
+    bitr r = {in, 0};
+    decode_block_f64(&r, rate, v);
+    return 0;
+}
+
+int zfpo_encode_array_f64(int rate, const double *base, const int64_t n[3], const int64_t s[3],
+                          uint8_t *out, int64_t out_bytes)
+{
+    if (!valid_rate_f64(rate)) return -1;
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1) return 0;
+    if (out_bytes < zfpo_stream_bytes_f64(rate, n)) return -2;
+    memset(out, 0, (size_t)zfpo_stream_bytes_f64(rate, n));
+    bitw w = {out, 0};
+    double v[64];
+    int64_t bx = (n[0] + 3) / 4, by = (n[1] + 3) / 4, bz = (n[2] + 3) / 4;
+    for (int64_t zb = 0; zb < bz; zb++)
+        for (int64_t yb = 0; yb < by; yb++)
+            for (int64_t xb = 0; xb < bx; xb++) {
+                for (int k = 0; k < 4; k++)
+                    for (int j = 0; j < 4; j++)
+                        for (int i = 0; i < 4; i++) {
+                            int64_t x = imin64(4 * xb + i, n[0] - 1);
+                            int64_t y = imin64(4 * yb + j, n[1] - 1);
+                            int64_t z = imin64(4 * zb + k, n[2] - 1);
+                            v[i + 4 * j + 16 * k] = base[x * s[0] + y * s[1] + z * s[2]];
+                        }
+                encode_block_f64(&w, rate, v);
+            }
+    return 0;
+}
+
+int zfpo_decode_array_f64(int rate, const uint8_t *in, const int64_t n[3], double *base, const int64_t s[3])
+{
+    if (!valid_rate_f64(rate)) return -1;
+    if (n[0] < 1 || n[1] < 1 || n[2] < 1) return 0;
+    bitr r = {in, 0};
+    double v[64];
+    int64_t bx = (n[0] + 3) / 4, by = (n[1] + 3) / 4, bz = (n[2] + 3) / 4;
+    for (int64_t zb = 0; zb < bz; zb++)
+        for (int64_t yb = 0; yb < by; yb++)
+            for (int64_t xb = 0; xb < bx; xb++) {
+                decode_block_f64(&r, rate, v);
+                for (int k = 0; k < 4; k++)
+                    for (int j = 0; j < 4; j++)
+                        for (int i = 0; i < 4; i++) {
+                            int64_t x = 4 * xb + i, y = 4 * yb + j, z = 4 * zb + k;
+                            if (x < n[0] && y < n[1] && z < n[2])
+                                base[x * s[0] + y * s[1] + z * s[2]] = v[i + 4 * j + 16 * k];
+                        }
+            }
+    return 0;
+}

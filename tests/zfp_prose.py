@@ -21,7 +21,13 @@ def _wrap(v):
     return v - (1 << 32) if v & 0x80000000 else v
 
 
-def _fwd4(v):
+def _wrap64(v):
+    """int64 ring value of a Python int."""
+    v &= (1 << 64) - 1
+    return v - (1 << 64) if v >> 63 else v
+
+
+def _fwd4(v, _wrap=_wrap):
     """Integer lifting of one 4-vector; halvings are floor shifts."""
     x, y, z, w = v
     x = _wrap(x + w) >> 1
@@ -37,7 +43,7 @@ def _fwd4(v):
     return [x, y, z, w]
 
 
-def _inv4(v):
+def _inv4(v, _wrap=_wrap):
     """The steps of _fwd4 undone in reverse order (a halving undone by a doubling)."""
     x, y, z, w = v
     y = _wrap(y + (w >> 1))
@@ -94,28 +100,35 @@ def encode_block_accuracy(values, tol):
     return _code(3, values, 1024 - 9, lambda e: min(32, max(0, minexp - e + 22)))
 
 
-def _code(dims, values, budget, kstop_of):
-    """Header and planes 31 .. kstop_of(e_max) of one block, at most budget bits
-    after the header; a zero block is the single bit 0."""
+# the two value formats: exponent bias and bits, integer precision, planes
+F32 = dict(dtype=np.float32, bias=127, ebits=8, intprec=30, planes=32, wrap=_wrap)
+F64 = dict(dtype=np.float64, bias=1023, ebits=11, intprec=62, planes=64, wrap=_wrap64)
+
+
+def _code(dims, values, budget, kstop_of, fmt=F32):
+    """Header and planes (top) .. kstop_of(e_max) of one block, at most budget
+    bits after the header; a zero block is the single bit 0."""
     size = 4 ** dims
-    vals = [float(v) for v in np.asarray(values, dtype=np.float32).reshape(-1)]
+    vals = [float(v) for v in np.asarray(values, dtype=fmt["dtype"]).reshape(-1)]
     big = max(abs(v) for v in vals)
     if not math.isfinite(big) or big == 0.0:
         return [0]
     e = math.frexp(big)[1]
-    if e + 127 <= 0:
+    if e + fmt["bias"] <= 0:
         return [0]
-    bits = [1] + [(e + 127) >> b & 1 for b in range(8)]
+    bits = [1] + [(e + fmt["bias"]) >> b & 1 for b in range(fmt["ebits"])]
     kstop = kstop_of(e)
-    q = [int(math.trunc(v * 2.0 ** (30 - e))) for v in vals]
+    q = [int(math.trunc(math.ldexp(v, fmt["intprec"] - e))) for v in vals]
     for axis in _lines(dims):
         for line in axis:
-            out = _fwd4([q[t] for t in line])
+            out = _fwd4([q[t] for t in line], fmt["wrap"])
             for t, val in zip(line, out):
                 q[t] = val
-    u = [(_wrap(q[idx]) + 0xAAAAAAAA & 0xFFFFFFFF) ^ 0xAAAAAAAA for idx in _order(dims)]
+    P = fmt["planes"]
+    nega = int("10" * (P // 2), 2)
+    u = [(fmt["wrap"](q[idx]) + nega & ((1 << P) - 1)) ^ nega for idx in _order(dims)]
     n = 0
-    for k in range(31, kstop - 1, -1):
+    for k in range(P - 1, kstop - 1, -1):
         if budget <= 0:
             break
         plane = [c >> k & 1 for c in u]
@@ -256,3 +269,67 @@ def decode_array(dims, rate, stream, shape):
                         if z + k < nz and y + j < ny and x + i < nx:
                             out[z + k, y + j, x + i] = vals[16 * k + 4 * j + i]
     return out
+
+
+def encode_block_f64(rate, values):
+    """Bits of one 3-D block of float64 values at rate bits per value."""
+    maxbits = 64 * rate
+    bits = _code(3, values, maxbits - 12, lambda e: 0, F64)
+    return bits + [0] * (maxbits - len(bits))
+
+
+def decode_block_f64(rate, bits):
+    """float64 values of one 3-D block from its 64 rate bits (the plane loop of
+    decode_block with 64 planes, an 11-bit exponent and int64 coefficients)."""
+    size, maxbits = 64, 64 * rate
+    bits = list(bits)[:maxbits]
+    if not bits[0]:
+        return np.zeros(size)
+    e = sum(bits[1 + b] << b for b in range(11)) - 1023
+    pos, budget, n = 12, maxbits - 12, 0
+    u = [0] * size
+    for k in range(63, -1, -1):
+        if budget <= 0:
+            break
+        for i in range(n):
+            if budget == 0:
+                break
+            u[i] |= bits[pos] << k
+            pos += 1
+            budget -= 1
+        while n < size and budget > 0:
+            g = bits[pos]
+            pos += 1
+            budget -= 1
+            if not g:
+                break
+            j = n
+            while True:
+                if j == size - 1:
+                    u[j] |= 1 << k
+                    n = size
+                    break
+                if budget == 0:
+                    break
+                b = bits[pos]
+                pos += 1
+                budget -= 1
+                if b:
+                    u[j] |= 1 << k
+                    n = j + 1
+                    break
+                j += 1
+            if budget == 0:
+                break
+    nega = int("10" * 32, 2)
+    q = [0] * size
+    for idx, c in zip(_order(3), u):
+        q[idx] = _wrap64((c ^ nega) - nega)
+    for axis in reversed(_lines(3)):
+        for line in axis:
+            out = _inv4([q[t] for t in line], _wrap64)
+            for t, val in zip(line, out):
+                q[t] = val
+    # q 2^(e - 62) rounded once: exact rational, then the nearest double
+    from fractions import Fraction
+    return np.array([float(Fraction(v) * Fraction(2) ** (e - 62)) for v in q])
