@@ -227,6 +227,27 @@ ZFPX_API int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_pa
                                   const int64_t n[3], const int64_t stride[3], float *d_out, void *d_work,
                                   size_t work_bytes, void *stream);
 
+/* ---- float64 fields: 3-D blocks, fixed rate (raw arrays) -----------------
+ * The fixed-rate method with the double format's sizes, for the float64
+ * fields the paper's data comes in (Sec. III): per 4x4x4 block a 1 bit and
+ * the 11-bit biased exponent e_max + 1023 (e_max = the frexp exponent of the
+ * block's largest magnitude; a zero block, one 0 bit, if that magnitude is
+ * 0, below 2^-1023 or not finite), q = trunc(x 2^(62 - e_max)) as int64, the
+ * five-step lifting in int64, the 3-D coefficient order, 64-bit negabinary
+ * and group-tested bit planes 63 .. 0 cut at exactly 64 * rate bits.  Decode
+ * rounds q 2^(e_max - 62) once to nearest even (subnormal results included).
+ * rate = bits per value, 1 .. 32; the stream is the blocks' 8 * rate bytes
+ * each, in raster block order (x fastest).  d_in/d_out: device arrays read or
+ * written through stride (in elements, >= 0; any view), 8-byte aligned; the
+ * stream 8-byte aligned for encode, 4-byte for decode.  Errors: ZFPX_EINVAL
+ * (NULL, rate, extents < 1, alignment), ZFPX_ESIZE (cap / len below
+ * zfpx_stream_bytes_f64), ZFPX_ECUDA. */
+ZFPX_API size_t zfpx_stream_bytes_f64(int rate, const int64_t n[3]);
+ZFPX_API int zfpx_encode_f64(int rate, const double *d_in, const int64_t n[3], const int64_t stride[3],
+                             uint8_t *d_out, size_t cap, void *stream);
+ZFPX_API int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
+                             const int64_t stride[3], double *d_out, void *stream);
+
 /* The accuracy mode on a transposition plan (dims 3): every message's box is
  * coded as above, so messages vary in size and the exchange becomes an
  * all-to-all-v, the per-message sizes first, then the payloads (on one GPU,

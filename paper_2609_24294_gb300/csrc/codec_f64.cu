@@ -1,0 +1,366 @@
+// float64 fields, 3-D blocks, fixed rate (raw arrays).  The float32 method
+// with the double format's sizes (readings identical in the CPU oracle):
+// e_max = frexp exponent of max|x|; zero block (one 0 bit) if max|x| is 0,
+// below 2^-1023 or non-finite; header = a 1 bit and e_max + 1023 in 11 bits;
+// q = trunc(x 2^(62 - e_max)) in int64; the five-step lifting in int64 along
+// x, y, z; the 3-D coefficient order; 64-bit negabinary; group-tested bit
+// planes 63 .. 0 cut at exactly 64 r bits; decode x = q 2^(e_max - 62)
+// rounded once to nearest even.
+//
+// A block's 64 int64 values do not fit a lane's registers, so this path keeps
+// them in shared memory: one lane per block, 32 consecutive blocks per warp,
+// one warp per CTA ([value][lane] tiles, each lane in its own column).  The
+// 64 bit planes come from four 32x32 register transposes (low / high 32
+// coefficients x low / high 32 bits).  Rates 1 .. 32 bits per value.
+#include <algorithm>
+#include <climits>
+#include <cuda_runtime.h>
+
+#include "zfpx_internal.h"
+#include "zfpx_block.cuh"
+#include "zfpx_smem.cuh"
+
+namespace zfpx {
+namespace {
+
+using namespace blk;
+
+constexpr int kMaxRate = 32;
+constexpr uint64_t kNega64 = 0xAAAAAAAAAAAAAAAAull;
+
+__device__ __forceinline__ int64_t add64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
+__device__ __forceinline__ int64_t sub64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a - (uint64_t)b); }
+
+// The five lifting steps on one line of the [value][lane] tile (stride s
+// values), floor halving; and their inverse.
+__device__ __forceinline__ void lift_fwd64(int64_t *t, int s)
+{
+    int64_t a = t[0], b = t[s * 32], c = t[2 * s * 32], d = t[3 * s * 32];
+    a = add64(a, d) >> 1; d = sub64(d, a);
+    c = add64(c, b) >> 1; b = sub64(b, c);
+    a = add64(a, c) >> 1; c = sub64(c, a);
+    d = add64(d, b) >> 1; b = sub64(b, d);
+    d = add64(d, b >> 1); b = sub64(b, d >> 1);
+    t[0] = a; t[s * 32] = b; t[2 * s * 32] = c; t[3 * s * 32] = d;
+}
+__device__ __forceinline__ void lift_inv64(int64_t *t, int s)
+{
+    int64_t a = t[0], b = t[s * 32], c = t[2 * s * 32], d = t[3 * s * 32];
+    b = add64(b, d >> 1); d = sub64(d, b >> 1);
+    b = add64(b, d); d = sub64(add64(d, d), b);
+    c = add64(c, a); a = sub64(add64(a, a), c);
+    b = add64(b, c); c = sub64(add64(c, c), b);
+    d = add64(d, a); a = sub64(add64(a, a), d);
+    t[0] = a; t[s * 32] = b; t[2 * s * 32] = c; t[3 * s * 32] = d;
+}
+
+// Writer into this lane's column of a [word][lane] tile of nwords + 2 words.
+struct VarWriter {
+    uint64_t *sm;
+    uint64_t acc;
+    int nb, w, lane, nwords;
+    __device__ __forceinline__ uint64_t &word(int i) const { return sm[i * 32 + lane]; }
+    __device__ __forceinline__ void put(uint64_t bits, int len)
+    {
+        acc |= bits << nb;
+        int t = nb + len;
+        if (t >= 64) {
+            word(w) = acc;
+            w++;
+            acc = nb ? (bits >> (64 - nb)) : 0ull;
+            t -= 64;
+        }
+        nb = t;
+    }
+    __device__ __forceinline__ void finish()
+    {
+        if (nb > 0) { word(w) = acc; w++; }
+        for (; w < nwords; w++) word(w) = 0ull;
+    }
+};
+
+struct TileReader64 {
+    const StreamTile &t;
+    int pos;
+    __device__ __forceinline__ uint64_t peek() const { return tile_peek(t, pos); }
+    __device__ __forceinline__ void skip(int k) { pos += k; }
+};
+
+struct Geom64 {
+    int64_t n[3], s[3];
+    int64_t bx, by, nblocks, nunits;
+    int rate;
+};
+
+__device__ __forceinline__ void block_origin(const Geom64 &g, int64_t b, int64_t &x0, int64_t &y0, int64_t &z0)
+{
+    const int64_t t = b / g.bx;
+    x0 = 4 * (b - t * g.bx);
+    y0 = 4 * (t % g.by);
+    z0 = 4 * (t / g.by);
+}
+
+// exponent: 0 for a zero block, else e_max + 1023 (1 .. 2046)
+__device__ __forceinline__ int block_exponent(uint64_t amax)
+{
+    const int E = (int)(amax >> 52);
+    if (E == 2047 || amax < 0x0008000000000000ull) return 0;     // non-finite, or below 2^-1023
+    return E == 0 ? 1 : E + 1;                                   // frexp exponent + 1023
+}
+
+__global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict__ src, uint8_t *__restrict__ out,
+                                                        Geom64 g)
+{
+    __shared__ int64_t vals[64 * 32];
+    __shared__ uint64_t planes[64 * 32];
+    __shared__ uint64_t stile[(kMaxRate + 2) * 32];
+    constexpr int kSeq[64] = ZFPX_SEQ3;
+    const int lane = threadIdx.x;
+    int64_t *v = vals + lane;
+    SmemPlanes pl{planes, lane};
+    for (int64_t u = blockIdx.x; u < g.nunits; u += gridDim.x) {
+        const int64_t b0 = u * 32;
+        const int nact = (int)min((int64_t)32, g.nblocks - b0);
+        if (lane < nact) {
+            int64_t x0, y0, z0;
+            block_origin(g, b0 + lane, x0, y0, z0);
+            uint64_t amax = 0;
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) {
+                const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                const double x = __ldg(src + min(z0 + k, g.n[2] - 1) * g.s[2] + min(y0 + j, g.n[1] - 1) * g.s[1] +
+                                       min(x0 + i, g.n[0] - 1) * g.s[0]);
+                const uint64_t bits = (uint64_t)__double_as_longlong(x);
+                const uint64_t a = bits & 0x7fffffffffffffffull;
+                amax = a > amax ? a : amax;
+                v[r * 32] = (int64_t)bits;
+            }
+            const int e = block_exponent(amax);
+            VarWriter wr{stile, 0ull, 0, 0, lane, g.rate};
+            if (!e) {
+                wr.finish();
+            } else {
+                // q = trunc(x 2^(62 - e_max)) with e_max = e - 1023, as two
+                // exact power-of-two products (each factor a normal double)
+                const int sh = 62 - (e - 1023);
+                const int s1 = sh > 600 ? 600 : sh;
+                const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
+                const double f2 = __longlong_as_double((long long)(sh - s1 + 1023) << 52);
+#pragma unroll 1
+                for (int r = 0; r < 64; r++)
+                    v[r * 32] = __double2ll_rz((__longlong_as_double(v[r * 32]) * f1) * f2);
+#pragma unroll 1
+                for (int k = 0; k < 4; k++)
+                    for (int j = 0; j < 4; j++) lift_fwd64(v + (16 * k + 4 * j) * 32, 1);
+#pragma unroll 1
+                for (int k = 0; k < 4; k++)
+                    for (int i = 0; i < 4; i++) lift_fwd64(v + (16 * k + i) * 32, 4);
+#pragma unroll 1
+                for (int j = 0; j < 4; j++)
+                    for (int i = 0; i < 4; i++) lift_fwd64(v + (4 * j + i) * 32, 16);
+                // negabinary in coding order, then the 64 planes by quadrant
+#pragma unroll 1
+                for (int hb = 0; hb < 2; hb++)
+#pragma unroll 1
+                    for (int ch = 0; ch < 2; ch++) {
+                        uint32_t w[32];
+#pragma unroll
+                        for (int t = 0; t < 32; t++) {
+                            const uint64_t un = ((uint64_t)v[kSeq[32 * ch + t] * 32] + kNega64) ^ kNega64;
+                            w[t] = (uint32_t)(un >> (32 * hb));
+                        }
+                        transpose32(w);
+#pragma unroll
+                        for (int k = 0; k < 32; k++) pl.store_half(32 * hb + k, ch, w[k]);
+                    }
+                wr.put(1ull | ((uint64_t)e << 1), 12);
+                int n = 0, R = 64 * g.rate - 12;
+#pragma unroll 1
+                for (int k = 63; k >= 0 && R > 0; k--) code_plane<64>(wr, pl.load(k), n, R);
+                wr.finish();
+            }
+        }
+        __syncwarp();
+        uint64_t *dst = reinterpret_cast<uint64_t *>(out) + b0 * g.rate;
+        for (int idx = lane; idx < nact * g.rate; idx += 32) dst[idx] = stile[(idx % g.rate) * 32 + idx / g.rate];
+        __syncwarp();
+    }
+}
+
+// x = q 2^(e_max - 62) rounded once to nearest even, e_max = e - 1023.
+__device__ __forceinline__ double dequantize64(int64_t q, int e)
+{
+    const int s = e - 1023 - 62;                                 // x = q 2^s
+    if (s >= -1022 || q == 0) {
+        // (double)q rounds once; the scaling by 2^s is exact while the result
+        // is normal, which holds for every q != 0 once s >= -1022
+        const int s1 = s < -600 ? -600 : s;
+        return (__ll2double_rn(q) * __longlong_as_double((long long)(s1 + 1023) << 52)) *
+               __longlong_as_double((long long)(s - s1 + 1023) << 52);
+    }
+    const uint64_t a = q < 0 ? 0ull - (uint64_t)q : (uint64_t)q;
+    const uint64_t sign = q < 0 ? 0x8000000000000000ull : 0ull;
+    // normal result: a 2^s >= 2^-1022, i.e. a >= 2^(-1022 - s)
+    const int t = -1022 - s;                                     // >= 1 here
+    if (t < 64 && a >= (1ull << t)) {
+        const int s1 = s < -600 ? -600 : s;
+        const double r = (__ull2double_rn(a) * __longlong_as_double((long long)(s1 + 1023) << 52)) *
+                         __longlong_as_double((long long)(s - s1 + 1023) << 52);
+        return sign ? -r : r;
+    }
+    // subnormal: a 2^(s + 1074) units of 2^-1074, rounded to nearest even
+    const int u = s + 1074;
+    uint64_t m;
+    if (u >= 0) {
+        m = a << u;                                              // a < 2^(t) so this stays below 2^52
+    } else {
+        const int d = -u;
+        if (d >= 64) {
+            m = 0;                                               // below half the smallest subnormal
+        } else {
+            const uint64_t lo = a & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+            m = a >> d;
+            m += (lo > half || (lo == half && (m & 1ull))) ? 1ull : 0ull;
+        }
+    }
+    return __longlong_as_double((long long)(m | sign));
+}
+
+__global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restrict__ in, double *__restrict__ dst,
+                                                        Geom64 g)
+{
+    __shared__ int64_t vals[64 * 32];
+    __shared__ uint64_t planes[64 * 32];
+    __shared__ uint32_t tile[(2 * kMaxRate + 3) * 32];
+    constexpr int kSeq[64] = ZFPX_SEQ3;
+    const int lane = threadIdx.x;
+    int64_t *v = vals + lane;
+    SmemPlanes pl{planes, lane};
+    const StreamTile st{tile, lane};
+    for (int64_t u = blockIdx.x; u < g.nunits; u += gridDim.x) {
+        const int64_t b0 = u * 32;
+        const int nact = (int)min((int64_t)32, g.nblocks - b0);
+        if (lane >= nact) continue;
+        const int64_t b = b0 + lane;
+        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(in + b * 8 * g.rate);
+        for (int i = 0; i < 2 * g.rate; i++) tile[i * 32 + lane] = __ldg(s32 + i);
+        for (int i = 2 * g.rate; i < 2 * g.rate + 3; i++) tile[i * 32 + lane] = 0u;
+        int64_t x0, y0, z0;
+        block_origin(g, b, x0, y0, z0);
+        const uint64_t head = tile_peek(st, 0);
+        if (!(head & 1ull)) {
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) v[r * 32] = 0;
+        } else {
+            const int e = (int)((head >> 1) & 0x7ffu);
+            TileReader64 rd{st, 12};
+            int n = 0, R = 64 * g.rate - 12, kmin = 64;
+#pragma unroll 1
+            for (int k = 63; k >= 0 && R > 0; k--) {
+                pl.store(k, decode_plane<64>(rd, n, R));
+                kmin = k;
+            }
+#pragma unroll 1
+            for (int k = 0; k < kmin; k++) pl.store(k, 0ull);
+#pragma unroll 1
+            for (int hb = 0; hb < 2; hb++)
+#pragma unroll 1
+                for (int ch = 0; ch < 2; ch++) {
+                    uint32_t w[32];
+#pragma unroll
+                    for (int k = 0; k < 32; k++) w[k] = pl.load_half(32 * hb + k, ch);
+                    transpose32(w);
+                    // w[t] = bits 32 hb .. 32 hb + 31 of coefficient 32 ch + t
+#pragma unroll
+                    for (int t = 0; t < 32; t++) {
+                        int64_t *c = v + kSeq[32 * ch + t] * 32;
+                        const uint64_t part = (uint64_t)w[t] << (32 * hb);
+                        *c = hb ? (int64_t)(((uint64_t)*c & 0xffffffffull) | part) : (int64_t)part;
+                    }
+                }
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) v[r * 32] = sub64((int64_t)((uint64_t)v[r * 32] ^ kNega64), (int64_t)kNega64);
+#pragma unroll 1
+            for (int j = 0; j < 4; j++)
+                for (int i = 0; i < 4; i++) lift_inv64(v + (4 * j + i) * 32, 16);
+#pragma unroll 1
+            for (int k = 0; k < 4; k++)
+                for (int i = 0; i < 4; i++) lift_inv64(v + (16 * k + i) * 32, 4);
+#pragma unroll 1
+            for (int k = 0; k < 4; k++)
+                for (int j = 0; j < 4; j++) lift_inv64(v + (16 * k + 4 * j) * 32, 1);
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) v[r * 32] = __double_as_longlong(dequantize64(v[r * 32], e));
+        }
+#pragma unroll 1
+        for (int r = 0; r < 64; r++) {
+            const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+            if (x0 + i < g.n[0] && y0 + j < g.n[1] && z0 + k < g.n[2])
+                dst[(z0 + k) * g.s[2] + (y0 + j) * g.s[1] + (x0 + i) * g.s[0]] = __longlong_as_double(v[r * 32]);
+        }
+    }
+}
+
+Geom64 make_geom(const int64_t n[3], const int64_t s[3], int rate)
+{
+    Geom64 g;
+    for (int a = 0; a < 3; a++) { g.n[a] = n[a]; g.s[a] = s[a]; }
+    g.bx = (n[0] + 3) / 4; g.by = (n[1] + 3) / 4;
+    g.nblocks = g.bx * g.by * ((n[2] + 3) / 4);
+    g.nunits = (g.nblocks + 31) / 32;
+    g.rate = rate;
+    return g;
+}
+
+unsigned grid_f64(const void *fn, int64_t nunits)
+{
+    const int64_t cap = (int64_t)num_sms() * occupancy(fn, 32);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nunits, cap));
+}
+
+bool valid_f64_args(int rate, const int64_t n[3], const int64_t stride[3])
+{
+    if (rate < 1 || rate > kMaxRate || !n || !stride) return false;
+    for (int a = 0; a < 3; a++) if (n[a] < 1 || stride[a] < 0) return false;
+    return true;
+}
+
+}  // namespace
+}  // namespace zfpx
+
+using namespace zfpx;
+
+extern "C" {
+
+size_t zfpx_stream_bytes_f64(int rate, const int64_t n[3])
+{
+    if (!n || rate < 1 || rate > kMaxRate) return 0;
+    for (int a = 0; a < 3; a++) if (n[a] < 1) return 0;
+    return (size_t)(((n[0] + 3) / 4) * ((n[1] + 3) / 4) * ((n[2] + 3) / 4) * 8 * rate);
+}
+
+int zfpx_encode_f64(int rate, const double *d_in, const int64_t n[3], const int64_t stride[3], uint8_t *d_out,
+                    size_t cap, void *stream)
+{
+    if (!d_in || !d_out || !valid_f64_args(rate, n, stride)) return ZFPX_EINVAL;
+    if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
+    if (cap < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
+    const Geom64 g = make_geom(n, stride, rate);
+    encode_f64_kernel<<<grid_f64((const void *)encode_f64_kernel, g.nunits), 32, 0, (cudaStream_t)stream>>>(d_in, d_out, g);
+    count_launch();
+    return check_launch();
+}
+
+int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3], const int64_t stride[3],
+                    double *d_out, void *stream)
+{
+    if (!d_in || !d_out || !valid_f64_args(rate, n, stride)) return ZFPX_EINVAL;
+    if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 3u)) return ZFPX_EINVAL;
+    if (len < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
+    const Geom64 g = make_geom(n, stride, rate);
+    decode_f64_kernel<<<grid_f64((const void *)decode_f64_kernel, g.nunits), 32, 0, (cudaStream_t)stream>>>(d_in, d_out, g);
+    count_launch();
+    return check_launch();
+}
+
+}  // extern "C"

@@ -118,6 +118,9 @@ def lib():
         "zfpx_encode_precision": ([vp, i64p, i64p, ctypes.c_int, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
         "zfpx_exchange_accuracy": ([vp, vp, vp, vp, vp, vp, sz, vp, sz, vp], ctypes.c_int),
         "zfpx_decompress_unpack_accuracy": ([vp, vp, vp, vp, sz, vp, vp, sz, vp], ctypes.c_int),
+        "zfpx_stream_bytes_f64": ([ctypes.c_int, i64p], sz),
+        "zfpx_encode_f64": ([ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
+        "zfpx_decode_f64": ([ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -353,6 +356,29 @@ def zfpx_decode_accuracy(lengths, payload, dst, work, stream=None):
     _check(lib().zfpx_decode_accuracy(_dev(lengths, "lengths"), _dev(payload, "payload"), _nbytes(payload),
                                       _i64x3(n), _i64x3(s), _dev(dst, "dst"), _dev(work, "work"), _nbytes(work),
                                       _stream(stream)), "zfpx_decode_accuracy")
+
+
+def zfpx_stream_bytes_f64(rate, n):
+    return int(lib().zfpx_stream_bytes_f64(int(rate), _i64x3(n)))
+
+
+def zfpx_encode_f64(rate, src, out, stream=None):
+    """Fixed-rate encode of a float64 [lev][lat][lon] tensor (any strides) into
+    the uint8 tensor out (>= zfpx_stream_bytes_f64 bytes)."""
+    if src.dtype != torch.float64:
+        raise ValueError("src must be float64")
+    n, s = field_view(src)
+    _check(lib().zfpx_encode_f64(int(rate), _dev(src, "src"), _i64x3(n), _i64x3(s), _dev(out, "out"),
+                                 _nbytes(out), _stream(stream)), "zfpx_encode_f64")
+
+
+def zfpx_decode_f64(rate, stream_bytes, dst, stream=None):
+    """Fixed-rate decode into the float64 tensor dst (any strides)."""
+    if dst.dtype != torch.float64:
+        raise ValueError("dst must be float64")
+    n, s = field_view(dst)
+    _check(lib().zfpx_decode_f64(int(rate), _dev(stream_bytes, "stream"), _nbytes(stream_bytes), _i64x3(n),
+                                 _i64x3(s), _dev(dst, "dst"), _stream(stream)), "zfpx_decode_f64")
 
 
 class AccuracyTransposition:
