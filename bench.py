@@ -536,6 +536,34 @@ def extra_blocks_2d(z, xd, reps, peak):
     return res
 
 
+def extra_float64(z, xd, reps, peak):
+    """The benchmark field held as float64 (the precision the paper's fields come in)
+    and coded with the float64 fixed-rate 3-D codec on one array: per rate the
+    encode / decode times, throughput of float64 values, the fraction of the
+    measured copy bandwidth (float64 array plus stream) and the error."""
+    import torch
+    x64 = xd.double()
+    n = tuple(reversed(x64.shape))
+    fbytes = 8 * x64.numel()
+    res = {"workload": "1280x640x137 f64 (the f32 field widened) as one array, 3-D blocks, fixed rate"}
+    out = torch.empty_like(x64)
+    for r in (8, 16, 32):
+        nb = z.zfpx_stream_bytes_f64(r, n)
+        st = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        te = _events_ms(lambda: z.zfpx_encode_f64(r, x64, st), reps)
+        td = _events_ms(lambda: z.zfpx_decode_f64(r, st, out), reps)
+        moved = fbytes + nb
+        res["r%d" % r] = {"encode_ms": te, "decode_ms": td,
+                          "encode_f64_GBps": fbytes / (te / 1e3) / 1e9, "decode_f64_GBps": fbytes / (td / 1e3) / 1e9,
+                          "encode_frac_of_measured_hbm": moved / (te / 1e3) / 1e9 / peak,
+                          "decode_frac_of_measured_hbm": moved / (td / 1e3) / 1e9 / peak,
+                          "rel_l2": float((out - x64).norm() / x64.norm()),
+                          "max_abs_error": float((out - x64).abs().max())}
+        del st
+    del x64, out
+    return res
+
+
 def extra_accuracy(z, xd, reps, peak):
     """The accuracy mode (variable rate to an absolute tolerance, 3-D blocks) on the
     benchmark field as one array: per tolerance the bits per value, the errors
@@ -883,6 +911,10 @@ def run_gpu(args):
             extras["accuracy_mode"] = extra_accuracy(z, xd, reps, peak)
         except Exception as e:
             extras["accuracy_mode"] = {"error": repr(e)}
+        try:
+            extras["float64"] = extra_float64(z, xd, reps, peak)
+        except Exception as e:
+            extras["float64"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()

@@ -238,8 +238,8 @@ ZFPX_API int zfpx_decode_accuracy(const uint16_t *d_lengths, const uint8_t *d_pa
  * rounds q 2^(e_max - 62) once to nearest even (subnormal results included).
  * rate = bits per value, 1 .. 32; the stream is the blocks' 8 * rate bytes
  * each, in raster block order (x fastest).  d_in/d_out: device arrays read or
- * written through stride (in elements, >= 0; any view), 8-byte aligned; the
- * stream 8-byte aligned for encode, 4-byte for decode.  Errors: ZFPX_EINVAL
+ * written through stride (in elements, >= 0; any view), 8-byte aligned, and
+ * the stream 8-byte aligned.  Errors: ZFPX_EINVAL
  * (NULL, rate, extents < 1, alignment), ZFPX_ESIZE (cap / len below
  * zfpx_stream_bytes_f64), ZFPX_ECUDA. */
 ZFPX_API size_t zfpx_stream_bytes_f64(int rate, const int64_t n[3]);

@@ -27,6 +27,8 @@ using namespace blk;
 
 constexpr int kMaxRate = 32;
 constexpr uint64_t kNega64 = 0xAAAAAAAAAAAAAAAAull;
+// the 3-D coefficient order (the warp reads one entry at a time: a broadcast)
+__constant__ int kSeq64[64] = ZFPX_SEQ3;
 
 __device__ __forceinline__ int64_t add64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
 __device__ __forceinline__ int64_t sub64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a - (uint64_t)b); }
@@ -79,10 +81,23 @@ struct VarWriter {
     }
 };
 
+// One lane's stream in a [64-bit word][lane] tile; peek(pos) = the 64 stream
+// bits from bit pos on (reads words pos / 64 and pos / 64 + 1).
+struct Tile64 {
+    const uint64_t *sm;
+    int lane;
+    __device__ __forceinline__ uint64_t peek(int pos) const
+    {
+        const int w = pos >> 6, sh = pos & 63;
+        const uint64_t a = sm[w * 32 + lane];
+        return sh ? (a >> sh) | (sm[(w + 1) * 32 + lane] << (64 - sh)) : a;
+    }
+};
+
 struct TileReader64 {
-    const StreamTile &t;
+    const Tile64 &t;
     int pos;
-    __device__ __forceinline__ uint64_t peek() const { return tile_peek(t, pos); }
+    __device__ __forceinline__ uint64_t peek() const { return t.peek(pos); }
     __device__ __forceinline__ void skip(int k) { pos += k; }
 };
 
@@ -113,8 +128,9 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
 {
     __shared__ int64_t vals[64 * 32];
     __shared__ uint64_t planes[64 * 32];
-    __shared__ uint64_t stile[(kMaxRate + 2) * 32];
-    constexpr int kSeq[64] = ZFPX_SEQ3;
+    // the stream tile reuses the values tile: lane l writes its stream words
+    // into its own column only after its last read of its values
+    uint64_t *stile = reinterpret_cast<uint64_t *>(vals);
     const int lane = threadIdx.x;
     int64_t *v = vals + lane;
     SmemPlanes pl{planes, lane};
@@ -166,7 +182,7 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
                         uint32_t w[32];
 #pragma unroll
                         for (int t = 0; t < 32; t++) {
-                            const uint64_t un = ((uint64_t)v[kSeq[32 * ch + t] * 32] + kNega64) ^ kNega64;
+                            const uint64_t un = ((uint64_t)v[kSeq64[32 * ch + t] * 32] + kNega64) ^ kNega64;
                             w[t] = (uint32_t)(un >> (32 * hb));
                         }
                         transpose32(w);
@@ -231,23 +247,25 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
 {
     __shared__ int64_t vals[64 * 32];
     __shared__ uint64_t planes[64 * 32];
-    __shared__ uint32_t tile[(2 * kMaxRate + 3) * 32];
-    constexpr int kSeq[64] = ZFPX_SEQ3;
+    // the stream tile ([64-bit word][lane], rate words and a zero word) sits in
+    // this lane's own column of the values tile, written over only after the
+    // planes are read out of the stream
+    const Tile64 st{reinterpret_cast<const uint64_t *>(vals), (int)threadIdx.x};
     const int lane = threadIdx.x;
     int64_t *v = vals + lane;
     SmemPlanes pl{planes, lane};
-    const StreamTile st{tile, lane};
     for (int64_t u = blockIdx.x; u < g.nunits; u += gridDim.x) {
         const int64_t b0 = u * 32;
         const int nact = (int)min((int64_t)32, g.nblocks - b0);
         if (lane >= nact) continue;
         const int64_t b = b0 + lane;
-        const uint32_t *s32 = reinterpret_cast<const uint32_t *>(in + b * 8 * g.rate);
-        for (int i = 0; i < 2 * g.rate; i++) tile[i * 32 + lane] = __ldg(s32 + i);
-        for (int i = 2 * g.rate; i < 2 * g.rate + 3; i++) tile[i * 32 + lane] = 0u;
+        const uint64_t *s64 = reinterpret_cast<const uint64_t *>(in) + b * g.rate;
+#pragma unroll 1
+        for (int i = 0; i < g.rate; i++) v[i * 32] = (int64_t)__ldg(s64 + i);
+        v[g.rate * 32] = 0;
         int64_t x0, y0, z0;
         block_origin(g, b, x0, y0, z0);
-        const uint64_t head = tile_peek(st, 0);
+        const uint64_t head = st.peek(0);
         if (!(head & 1ull)) {
 #pragma unroll 1
             for (int r = 0; r < 64; r++) v[r * 32] = 0;
@@ -273,7 +291,7 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
                     // w[t] = bits 32 hb .. 32 hb + 31 of coefficient 32 ch + t
 #pragma unroll
                     for (int t = 0; t < 32; t++) {
-                        int64_t *c = v + kSeq[32 * ch + t] * 32;
+                        int64_t *c = v + kSeq64[32 * ch + t] * 32;
                         const uint64_t part = (uint64_t)w[t] << (32 * hb);
                         *c = hb ? (int64_t)(((uint64_t)*c & 0xffffffffull) | part) : (int64_t)part;
                     }
@@ -355,7 +373,7 @@ int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3
                     double *d_out, void *stream)
 {
     if (!d_in || !d_out || !valid_f64_args(rate, n, stride)) return ZFPX_EINVAL;
-    if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 3u)) return ZFPX_EINVAL;
+    if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
     if (len < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
     const Geom64 g = make_geom(n, stride, rate);
     decode_f64_kernel<<<grid_f64((const void *)decode_f64_kernel, g.nunits), 32, 0, (cudaStream_t)stream>>>(d_in, d_out, g);
