@@ -564,6 +564,79 @@ def extra_float64(z, xd, reps, peak):
     return res
 
 
+def extra_sht_fourier(z, xd, reps, peak):
+    """The longitude transform after the first transposition, and the second
+    transposition run in wavenumber space: the FFT of every 1280-point row of the
+    benchmark field (K = 640 wavenumbers, the linear-grid truncation T639) with its
+    time and fraction of the measured copy bandwidth; the spectrum error the first
+    transposition's codec causes (FFT of the decoded lambda-pencil against the FFT
+    of the exact field); and lambda -> theta over 8 x 8 ranks on the real and
+    imaginary wavenumber fields (split over m), with its time and error, beside the
+    same transposition of the grid-point field."""
+    import torch
+    nz, ny, nx = xd.shape
+    K = nx // 2
+    re = torch.empty((nz, ny, K), device="cuda")
+    im = torch.empty_like(re)
+    t = _events_ms(lambda: z.zfpx_rfft_lon(xd, re, im), reps)
+    moved = 4 * xd.numel() + 8 * re.numel()
+    res = {"workload": "1280x640x137 f32, rows of 1280 longitudes -> 640 wavenumbers; 8x8 ranks",
+           "fft_ms": t, "fft_GBps": moved / (t / 1e3) / 1e9,
+           "fft_frac_of_measured_hbm": moved / (t / 1e3) / 1e9 / peak}
+    exact = torch.complex(re.double(), im.double())
+    enorm = float(exact.norm())
+    dre, dim_ = torch.empty_like(re), torch.empty_like(im)
+    plan1 = z.Plan.for_fields(xd, PR, PC, 0, 3)
+    plan2 = z.Plan.for_fields(re, PR, PC, 1, 3)
+    plang = z.Plan.for_fields(xd, PR, PC, 1, 3)
+    x64 = xd.double()
+    for r in RATES:
+        out = {}
+        # transposition 1 coded at rate r, then the FFT of the decoded pencil
+        plan1.prepare(r)
+        sb = torch.zeros(plan1.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        dec = torch.empty_like(xd)
+        z.zfpx_pack_compress(plan1, r, xd, sb)
+        z.zfpx_permute(plan1, r, sb, rb)
+        z.zfpx_decompress_unpack(plan1, r, rb, dec)
+        z.zfpx_rfft_lon(dec, dre, dim_)
+        out["t1_spectrum_rel_l2"] = float((torch.complex(dre.double(), dim_.double()) - exact).norm()) / enorm
+        del sb, rb, dec
+        # transposition 2 on the wavenumber fields
+        plan2.prepare(r)
+        sb = torch.zeros(plan2.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        ore, oim = torch.empty_like(re), torch.empty_like(im)
+
+        def t2():
+            for f, o in ((re, ore), (im, oim)):
+                z.zfpx_pack_compress(plan2, r, f, sb)
+                z.zfpx_permute(plan2, r, sb, rb)
+                z.zfpx_decompress_unpack(plan2, r, rb, o)
+        out["t2_wavenumber_ms"] = _events_ms(t2, reps)
+        out["t2_wavenumber_rel_l2"] = float((torch.complex(ore.double(), oim.double()) - exact).norm()) / enorm
+        del sb, rb, ore, oim
+        # the same transposition on the grid-point field, for comparison
+        plang.prepare(r)
+        sb = torch.zeros(plang.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        rb = torch.zeros_like(sb)
+        og = torch.empty_like(xd)
+
+        def tg():
+            z.zfpx_pack_compress(plang, r, xd, sb)
+            z.zfpx_permute(plang, r, sb, rb)
+            z.zfpx_decompress_unpack(plang, r, rb, og)
+        out["t2_grid_ms"] = _events_ms(tg, reps)
+        out["t2_grid_rel_l2"] = float((og.double() - x64).norm() / x64.norm())
+        del sb, rb, og
+        res["r%d" % r] = out
+    for p in (plan1, plan2, plang):
+        p.close()
+    del exact, x64, re, im, dre, dim_
+    return res
+
+
 def extra_accuracy(z, xd, reps, peak):
     """The accuracy mode (variable rate to an absolute tolerance, 3-D blocks) on the
     benchmark field as one array: per tolerance the bits per value, the errors
@@ -915,6 +988,10 @@ def run_gpu(args):
             extras["float64"] = extra_float64(z, xd, reps, peak)
         except Exception as e:
             extras["float64"] = {"error": repr(e)}
+        try:
+            extras["sht_fourier"] = extra_sht_fourier(z, xd, reps, peak)
+        except Exception as e:
+            extras["sht_fourier"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()

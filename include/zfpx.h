@@ -248,6 +248,24 @@ ZFPX_API int zfpx_encode_f64(int rate, const double *d_in, const int64_t n[3], c
 ZFPX_API int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                              const int64_t stride[3], double *d_out, void *stream);
 
+/* ---- the longitude transform (the FFT after the first transposition) ------
+ * The spectral transform is an FFT in longitude and a Legendre transform in
+ * latitude (Sec. II-A); the z -> lambda all-to-all makes every longitude row
+ * local so that the FFT can run (Sec. II-B).  For every row x_0 .. x_{N-1} of
+ * the [n2][n1][n0] float32 array d_in (n0 = N longitudes, row elements
+ * contiguous: stride[0] == 1; stride[1], stride[2] even, d_in 8-byte aligned)
+ * this writes F_m = (1/N) sum_j x_j exp(-2 pi i j m / N), m = 0 .. K-1, as
+ * real parts to d_re and imaginary parts to d_im, both [n2][n1][K] float32
+ * arrays through ostride (ostride[0] == 1; the same strides for both).
+ * N even, N <= 8192, N / 2 a product of 2, 3 and 5; 1 <= K <= N/2 + 1.
+ * Single-precision arithmetic; twiddles rounded once from double.  The first
+ * call for a given N on a device builds that N's twiddle table (8 N bytes of
+ * device memory, kept for the process; a synchronous upload, so make that
+ * first call outside stream capture).  Errors: ZFPX_EINVAL (NULL, sizes,
+ * strides, alignment), ZFPX_ECUDA. */
+ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t stride[3], int K, float *d_re,
+                           float *d_im, const int64_t ostride[3], void *stream);
+
 /* The accuracy mode on a transposition plan (dims 3): every message's box is
  * coded as above, so messages vary in size and the exchange becomes an
  * all-to-all-v, the per-message sizes first, then the payloads (on one GPU,

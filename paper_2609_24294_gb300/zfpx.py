@@ -121,6 +121,7 @@ def lib():
         "zfpx_stream_bytes_f64": ([ctypes.c_int, i64p], sz),
         "zfpx_encode_f64": ([ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_decode_f64": ([ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
+        "zfpx_rfft_lon": ([vp, i64p, i64p, ctypes.c_int, vp, vp, i64p, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -379,6 +380,21 @@ def zfpx_decode_f64(rate, stream_bytes, dst, stream=None):
     n, s = field_view(dst)
     _check(lib().zfpx_decode_f64(int(rate), _dev(stream_bytes, "stream"), _nbytes(stream_bytes), _i64x3(n),
                                  _i64x3(s), _dev(dst, "dst"), _stream(stream)), "zfpx_decode_f64")
+
+
+def zfpx_rfft_lon(src, re, im, stream=None):
+    """Longitude transform of every row of the float32 [lev][lat][lon] tensor src:
+    re / im (float32 [lev][lat][K], the same strides) get the real / imaginary
+    parts of F_m = (1/N) sum_j x_j e^{-2 pi i j m / N}, m < K = re.shape[-1]."""
+    for t, w in ((src, "src"), (re, "re"), (im, "im")):
+        if t.dtype != torch.float32 or t.dim() != 3:
+            raise ValueError("%s must be a 3-D float32 tensor" % w)
+    if re.shape != im.shape or re.stride() != im.stride() or re.shape[:2] != src.shape[:2]:
+        raise ValueError("re and im must have the same shape and strides, over src's rows")
+    n, s = field_view(src)
+    _, os_ = field_view(re)
+    _check(lib().zfpx_rfft_lon(_dev(src, "src"), _i64x3(n), _i64x3(s), int(re.shape[-1]), _dev(re, "re"),
+                               _dev(im, "im"), _i64x3(os_), _stream(stream)), "zfpx_rfft_lon")
 
 
 class AccuracyTransposition:
