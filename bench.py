@@ -299,6 +299,21 @@ def _events_ms(fn, reps, warmup=2):
 
 def _octahedral_fields():
     import torch
+    if args.profile_case == "sht":
+        xd = torch.from_numpy(make_field()).cuda()
+        nz, ny, nx = xd.shape
+        re = torch.empty((nz, ny, nx // 2), device="cuda")
+        im = torch.empty_like(re)
+        leg = z.Legendre(ny, nx // 2 - 1)
+        a_re = torch.empty((nz, leg.ncoeffs), device="cuda")
+        a_im = torch.empty_like(a_re)
+        for _ in range(max(1, args.steps)):
+            z.zfpx_rfft_lon(xd, re, im)
+            leg.forward(re, im, a_re, a_im)
+        torch.cuda.synchronize()
+        leg.close()
+        print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": 3 * max(1, args.steps)}))
+        return 0
     from fieldgen import octahedral as og
     fields = []
     for i, (nlev, kind, dims, rate) in enumerate(og.O1280_TEN_FIELDS):
@@ -564,27 +579,50 @@ def extra_float64(z, xd, reps, peak):
     return res
 
 
+# float32 FMA peak from the unit counts and the clock (152 SMs x 128 FP32 lanes x
+# 2 flops x 2.07 GHz maximum SM clock), for the SIMT kernels
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
 def extra_sht_fourier(z, xd, reps, peak):
-    """The longitude transform after the first transposition, and the second
-    transposition run in wavenumber space: the FFT of every 1280-point row of the
-    benchmark field (K = 640 wavenumbers, the linear-grid truncation T639) with its
-    time and fraction of the measured copy bandwidth; the spectrum error the first
-    transposition's codec causes (FFT of the decoded lambda-pencil against the FFT
-    of the exact field); and lambda -> theta over 8 x 8 ranks on the real and
-    imaginary wavenumber fields (split over m), with its time and error, beside the
-    same transposition of the grid-point field."""
+    """The spectral transform around the compressed transpositions, on the
+    benchmark field over 8 x 8 ranks: the longitude FFT of every 1280-point row
+    (K = 640 wavenumbers, T639), the second transposition (lambda -> theta) on
+    the real and imaginary wavenumber fields (split over m), and the Legendre
+    transform to the T639 coefficients.  Times and roofline fractions of the two
+    transforms; relative L2 errors of the spectra and of the coefficients with
+    the first transposition compressed, the second, and both, against the same
+    transforms of the uncompressed field."""
     import torch
     nz, ny, nx = xd.shape
     K = nx // 2
+    T = K - 1
     re = torch.empty((nz, ny, K), device="cuda")
     im = torch.empty_like(re)
     t = _events_ms(lambda: z.zfpx_rfft_lon(xd, re, im), reps)
     moved = 4 * xd.numel() + 8 * re.numel()
-    res = {"workload": "1280x640x137 f32, rows of 1280 longitudes -> 640 wavenumbers; 8x8 ranks",
+    res = {"workload": "1280x640x137 f32, rows of 1280 longitudes -> 640 wavenumbers -> T639 coefficients; 8x8 ranks",
            "fft_ms": t, "fft_GBps": moved / (t / 1e3) / 1e9,
            "fft_frac_of_measured_hbm": moved / (t / 1e3) / 1e9 / peak}
+    leg = z.Legendre(ny, T)
+    a_re = torch.empty((nz, leg.ncoeffs), device="cuda")
+    a_im = torch.empty_like(a_re)
+    tl = _events_ms(lambda: leg.forward(re, im, a_re, a_im), reps)
+    nh = ny // 2
+    flops = 2.0 * 2 * nz * nh * leg.ncoeffs                   # folded: nh multiply-adds per coefficient and part
+    res.update({"legendre_ms": tl, "legendre_TFLOPs": flops / (tl / 1e3) / 1e12,
+                "legendre_frac_of_fp32_simt_peak": flops / (tl / 1e3) / 1e12 / FP32_SIMT_TFLOPS,
+                "fp32_simt_peak_TFLOPs": FP32_SIMT_TFLOPS})
     exact = torch.complex(re.double(), im.double())
     enorm = float(exact.norm())
+    a_exact = torch.complex(a_re.double(), a_im.double())
+    anorm = float(a_exact.norm())
+    b_re, b_im = torch.empty_like(a_re), torch.empty_like(a_im)
+
+    def coeff_err(fre, fim):
+        leg.forward(fre, fim, b_re, b_im)
+        return float((torch.complex(b_re.double(), b_im.double()) - a_exact).norm()) / anorm
+
     dre, dim_ = torch.empty_like(re), torch.empty_like(im)
     plan1 = z.Plan.for_fields(xd, PR, PC, 0, 3)
     plan2 = z.Plan.for_fields(re, PR, PC, 1, 3)
@@ -602,6 +640,7 @@ def extra_sht_fourier(z, xd, reps, peak):
         z.zfpx_decompress_unpack(plan1, r, rb, dec)
         z.zfpx_rfft_lon(dec, dre, dim_)
         out["t1_spectrum_rel_l2"] = float((torch.complex(dre.double(), dim_.double()) - exact).norm()) / enorm
+        out["t1_coeff_rel_l2"] = coeff_err(dre, dim_)
         del sb, rb, dec
         # transposition 2 on the wavenumber fields
         plan2.prepare(r)
@@ -609,13 +648,16 @@ def extra_sht_fourier(z, xd, reps, peak):
         rb = torch.zeros_like(sb)
         ore, oim = torch.empty_like(re), torch.empty_like(im)
 
-        def t2():
-            for f, o in ((re, ore), (im, oim)):
+        def t2(fre, fim):
+            for f, o in ((fre, ore), (fim, oim)):
                 z.zfpx_pack_compress(plan2, r, f, sb)
                 z.zfpx_permute(plan2, r, sb, rb)
                 z.zfpx_decompress_unpack(plan2, r, rb, o)
-        out["t2_wavenumber_ms"] = _events_ms(t2, reps)
+        out["t2_wavenumber_ms"] = _events_ms(lambda: t2(re, im), reps)
         out["t2_wavenumber_rel_l2"] = float((torch.complex(ore.double(), oim.double()) - exact).norm()) / enorm
+        out["t2_coeff_rel_l2"] = coeff_err(ore, oim)
+        t2(dre, dim_)                                            # both transpositions compressed
+        out["t1_t2_coeff_rel_l2"] = coeff_err(ore, oim)
         del sb, rb, ore, oim
         # the same transposition on the grid-point field, for comparison
         plang.prepare(r)
@@ -633,7 +675,8 @@ def extra_sht_fourier(z, xd, reps, peak):
         res["r%d" % r] = out
     for p in (plan1, plan2, plang):
         p.close()
-    del exact, x64, re, im, dre, dim_
+    leg.close()
+    del exact, a_exact, x64, re, im, dre, dim_, a_re, a_im, b_re, b_im
     return res
 
 
@@ -1048,6 +1091,8 @@ def run_profile_case(args):
     of float32), one batch encode and one decode launch per repetition.  `blocks12`: the
     benchmark field and plan (1280 x 640 x 137, 8 x 8 ranks) coded with 2-D and then
     1-D blocks, rates 8 and 16, pack+compress and decompress+unpack per repetition.
+    `sht`: the benchmark field's longitude FFT (1280 -> 640 wavenumbers) and the T639
+    Legendre transform of its wavenumber fields, one of each per repetition.
     Prints one line; times nothing."""
     import torch
     from paper_2609_24294_gb300 import build, zfpx as z
@@ -1068,6 +1113,21 @@ def run_profile_case(args):
                 plan.close()
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": n}))
+        return 0
+    if args.profile_case == "sht":
+        xd = torch.from_numpy(make_field()).cuda()
+        nz, ny, nx = xd.shape
+        re = torch.empty((nz, ny, nx // 2), device="cuda")
+        im = torch.empty_like(re)
+        leg = z.Legendre(ny, nx // 2 - 1)
+        a_re = torch.empty((nz, leg.ncoeffs), device="cuda")
+        a_im = torch.empty_like(a_re)
+        for _ in range(max(1, args.steps)):
+            z.zfpx_rfft_lon(xd, re, im)
+            leg.forward(re, im, a_re, a_im)
+        torch.cuda.synchronize()
+        leg.close()
+        print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": 3 * max(1, args.steps)}))
         return 0
     from fieldgen import octahedral as og
     fields = []
@@ -1099,7 +1159,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--profile-case", choices=["batch", "blocks12"], default=None,
+    ap.add_argument("--profile-case", choices=["batch", "blocks12", "sht"], default=None,
                     help="run a reduced workload for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:

@@ -266,6 +266,36 @@ ZFPX_API int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const in
 ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t stride[3], int K, float *d_re,
                            float *d_im, const int64_t ostride[3], void *stream);
 
+/* ---- the Legendre transform (the latitude transform after the second
+ * transposition) -------------------------------------------------------------
+ * The spectral transform's latitude half (Sec. II-A: associated Legendre
+ * functions, Gauss-Legendre quadrature), run on theta-pencils once the
+ * lambda -> theta all-to-all has made every latitude column local (Sec. II-B).
+ * For the wavenumber fields F_m(mu_j) (real and imaginary parts: float32
+ * [n2 = levels][n1 = nlat][n0 >= T + 1 wavenumbers], the same strides for
+ * both, stride[0] == 1; latitudes at the Gauss-Legendre nodes north to south)
+ *     a_l^m = sum_j w_j Pbar_l^m(mu_j) F_m(mu_j),   0 <= m <= l <= T,
+ * Pbar normalised to int_{-1}^{1} Pbar_l^m Pbar_l'^m dmu = delta_ll' with the
+ * Condon-Shortley phase.  Output: per level, a_l^m at m (T+1) - m (m-1)/2 +
+ * (l - m), real parts to d_are and imaginary parts to d_aim, levels
+ * out_stride floats apart (>= (T+1)(T+2)/2).
+ * zfpx_legendre_create builds the plan on the current device: the Gauss
+ * nodes and weights and the table w_j Pbar_l^m(mu_j) over the northern half
+ * (computed in double, rounded once; about (T+1)(T+2) nlat bytes of device
+ * memory, a synchronous upload); nlat even, at most 32768, T + 1 <= nlat.
+ * zfpx_legendre_forward needs caller-owned device scratch d_work (16-byte
+ * aligned) of zfpx_legendre_workspace_bytes(plan, levels) bytes; calls that
+ * share d_work must not overlap on the GPU.  Single precision throughout.
+ * Errors: ZFPX_EINVAL (NULL, sizes, strides, alignment), ZFPX_ESIZE,
+ * ZFPX_ECUDA. */
+typedef struct zfpx_legendre_s *zfpx_legendre;
+ZFPX_API int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T);
+ZFPX_API void zfpx_legendre_destroy(zfpx_legendre plan);
+ZFPX_API size_t zfpx_legendre_workspace_bytes(zfpx_legendre plan, int64_t levels);
+ZFPX_API int zfpx_legendre_forward(zfpx_legendre plan, const float *d_re, const float *d_im, const int64_t n[3],
+                                   const int64_t stride[3], float *d_are, float *d_aim, int64_t out_stride,
+                                   void *d_work, size_t work_bytes, void *stream);
+
 /* The accuracy mode on a transposition plan (dims 3): every message's box is
  * coded as above, so messages vary in size and the exchange becomes an
  * all-to-all-v, the per-message sizes first, then the payloads (on one GPU,

@@ -122,6 +122,10 @@ def lib():
         "zfpx_encode_f64": ([ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_decode_f64": ([ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
         "zfpx_rfft_lon": ([vp, i64p, i64p, ctypes.c_int, vp, vp, i64p, vp], ctypes.c_int),
+        "zfpx_legendre_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_legendre_destroy": ([vp], None),
+        "zfpx_legendre_workspace_bytes": ([vp, ctypes.c_int64], sz),
+        "zfpx_legendre_forward": ([vp, vp, vp, i64p, i64p, vp, vp, ctypes.c_int64, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -395,6 +399,56 @@ def zfpx_rfft_lon(src, re, im, stream=None):
     _, os_ = field_view(re)
     _check(lib().zfpx_rfft_lon(_dev(src, "src"), _i64x3(n), _i64x3(s), int(re.shape[-1]), _dev(re, "re"),
                                _dev(im, "im"), _i64x3(os_), _stream(stream)), "zfpx_rfft_lon")
+
+
+class Legendre:
+    """The Legendre transform on Gauss-Legendre latitudes (zfpx_legendre_create /
+    zfpx_legendre_forward / zfpx_legendre_destroy); the workspace is a PyTorch
+    allocation kept per level count."""
+
+    def __init__(self, nlat, T):
+        h = ctypes.c_void_p()
+        _check(lib().zfpx_legendre_create(ctypes.byref(h), int(nlat), int(T)), "zfpx_legendre_create")
+        self._h, self.nlat, self.T = h, int(nlat), int(T)
+        self.ncoeffs = (self.T + 1) * (self.T + 2) // 2
+        self._work = {}
+
+    def close(self):
+        if self._h:
+            lib().zfpx_legendre_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def workspace_bytes(self, nlev):
+        return int(lib().zfpx_legendre_workspace_bytes(self._h, int(nlev)))
+
+    def forward(self, re, im, are, aim, stream=None):
+        """re, im: float32 [lev][nlat][K] wavenumber fields (same strides); are, aim:
+        float32 [lev][>= ncoeffs] (same level stride), the coefficients a_l^m."""
+        if not self._h:
+            raise ValueError("plan destroyed")
+        for t, w in ((re, "re"), (im, "im"), (are, "are"), (aim, "aim")):
+            if t.dtype != torch.float32:
+                raise ValueError("%s must be float32" % w)
+        if re.shape != im.shape or re.stride() != im.stride() or re.dim() != 3:
+            raise ValueError("re and im must be 3-D with the same shape and strides")
+        if are.dim() != 2 or are.shape != aim.shape or are.stride() != aim.stride() or are.stride(1) != 1 \
+                or are.shape[0] != re.shape[0] or are.shape[1] < self.ncoeffs:
+            raise ValueError("are and aim must be [lev][>= (T+1)(T+2)/2] with unit inner stride")
+        nlev = re.shape[0]
+        work = self._work.get(nlev)
+        if work is None:
+            work = torch.empty(max(16, self.workspace_bytes(nlev)), dtype=torch.uint8, device=re.device)
+            self._work[nlev] = work
+        n, s = field_view(re)
+        _check(lib().zfpx_legendre_forward(self._h, _dev(re, "re"), _dev(im, "im"), _i64x3(n), _i64x3(s),
+                                           _dev(are, "are"), _dev(aim, "aim"), int(are.stride(0)), _dev(work, "work"),
+                                           _nbytes(work), _stream(stream)), "zfpx_legendre_forward")
 
 
 class AccuracyTransposition:
