@@ -21,8 +21,8 @@
 // range near the poles for large m are 0.  A fold kernel writes S and A per
 // order (a transpose through shared memory, into the caller's workspace);
 // a tiled single-precision GEMM kernel (64 x 64 outputs per CTA, 16-deep
-// k steps through shared memory, 4 x 4 per thread) forms the products and
-// scatters them into the triangular output.  Tensor cores are not used: the
+// k steps through double-buffered shared memory, 8 x 4 per thread) forms the
+// products and scatters them into the triangular output.  Tensor cores are not used: the
 // transform needs float32 accuracy, which TF32 and BF16 do not give.
 #include <algorithm>
 #include <cmath>
@@ -33,11 +33,13 @@
 
 struct LegItem {
     int32_t m, p, r0, nr;   // order, parity of l + m, first row (of that parity), rows in this tile
-    int64_t aoff;           // float offset of the tile's first row in the table
+    int32_t ldm;            // row length of this (m, p) table block: its row count rounded up to 4
+    int32_t pad;
+    int64_t aoff;           // float offset of the (m, p) table block ([nlat/2][ldm], latitude-major)
 };
 
 struct zfpx_legendre_s {
-    int nlat = 0, T = 0, nh = 0, lda = 0, device = 0;
+    int nlat = 0, T = 0, nh = 0, device = 0;
     float *d_table = nullptr;
     LegItem *d_items = nullptr;
     int nitems = 0;
@@ -49,7 +51,7 @@ namespace {
 constexpr int kBM = 64, kBN = 64, kBK = 16;
 
 struct LegGeom {
-    int nlat, nh, lda, T, nlev;
+    int nlat, nh, T, nlev;
     int ldc;                 // columns of the folded operand per row (2 nlev rounded up to 4)
     int nct;                 // column tiles
     int64_t is1, is2;        // input strides: latitude, level (floats; longitude/wavenumber stride 1)
@@ -94,63 +96,84 @@ __global__ void __launch_bounds__(256) legendre_fold_kernel(const float *__restr
     }
 }
 
-__global__ void __launch_bounds__(256) legendre_gemm_kernel(const float *__restrict__ table,
-                                                            const float *__restrict__ G,
-                                                            const LegItem *__restrict__ items, LegGeom g,
-                                                            float *__restrict__ are, float *__restrict__ aim)
+// 64 x 64 outputs per CTA of 128 threads, each 8 rows x 4 columns; 16-deep k
+// steps, the next step's tiles loaded into registers while the current one is
+// multiplied out of the other shared-memory buffer (one barrier per step).
+// A tiles come from the latitude-major table block ([j][row], rows of one
+// parity contiguous), B tiles from the folded operand ([j][column]): both are
+// float4 rows copied into shared memory as they are.
+constexpr int kGemmThreads = 128;
+
+__global__ void __launch_bounds__(kGemmThreads) legendre_gemm_kernel(const float *__restrict__ table,
+                                                                     const float *__restrict__ G,
+                                                                     const LegItem *__restrict__ items, LegGeom g,
+                                                                     float *__restrict__ are, float *__restrict__ aim)
 {
-    __shared__ __align__(16) float As[kBK][kBM + 4];
-    __shared__ __align__(16) float Bs[kBK][kBN];
+    __shared__ __align__(16) float As[2][kBK][kBM];
+    __shared__ __align__(16) float Bs[2][kBK][kBN];
     const int tid = threadIdx.x;
     const LegItem it = items[blockIdx.x / g.nct];
     const int c0 = (blockIdx.x % g.nct) * kBN;
     const float *A = table + it.aoff;
     const float *B = G + ((int64_t)it.m * 2 + it.p) * g.nh * g.ldc;
     const int N = 2 * g.nlev;
-    const int ty = tid >> 4, tx = tid & 15;
-    float acc[4][4] = {};
-    // loaders: A, one float4 along k of row ar; B, one float4 along c of k-row bk
-    const int ar = tid >> 2, ak = (tid & 3) * 4;
-    const int bk = tid >> 4, bc = (tid & 15) * 4;
-    for (int k0 = 0; k0 < g.nh; k0 += kBK) {
-        float4 av = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ar < it.nr) {
-            const float *src = A + (int64_t)ar * g.lda + k0 + ak;
-            if (k0 + ak + 3 < g.nh) {
-                av = __ldg(reinterpret_cast<const float4 *>(src));
-            } else {
-                if (k0 + ak < g.nh) av.x = __ldg(src);
-                if (k0 + ak + 1 < g.nh) av.y = __ldg(src + 1);
-                if (k0 + ak + 2 < g.nh) av.z = __ldg(src + 2);
+    const int ty = tid >> 4, tx = tid & 15;                 // rows 8 ty .. 8 ty + 7, columns 4 tx .. 4 tx + 3
+    // loaders: two float4 of A and two of B per thread; element e = tid + 128 h
+    // covers k-row e / 16 and the four rows / columns 4 (e % 16) .. + 3
+    float4 ra[2], rb[2];
+    auto load = [&](int k0) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = tid + kGemmThreads * h, kr = e >> 4, q4 = (e & 15) * 4;
+            const bool kin = k0 + kr < g.nh;
+            ra[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (kin && it.r0 + q4 < it.ldm)
+                ra[h] = __ldg(reinterpret_cast<const float4 *>(A + (int64_t)(k0 + kr) * it.ldm + it.r0 + q4));
+            rb[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int c = c0 + q4;
+            if (kin && c < N) {
+                rb[h] = __ldg(reinterpret_cast<const float4 *>(B + (int64_t)(k0 + kr) * g.ldc + c));
+                if (c + 1 >= N) rb[h].y = 0.f;
+                if (c + 2 >= N) rb[h].z = 0.f;
+                if (c + 3 >= N) rb[h].w = 0.f;
             }
         }
-        As[ak][ar] = av.x; As[ak + 1][ar] = av.y; As[ak + 2][ar] = av.z; As[ak + 3][ar] = av.w;
-        float4 bv = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int c = c0 + bc;
-        if (k0 + bk < g.nh && c < N) {
-            bv = __ldg(reinterpret_cast<const float4 *>(B + (int64_t)(k0 + bk) * g.ldc + c));
-            if (c + 1 >= N) bv.y = 0.f;
-            if (c + 2 >= N) bv.z = 0.f;
-            if (c + 3 >= N) bv.w = 0.f;
+    };
+    auto store = [&](int buf) {
+#pragma unroll
+        for (int h = 0; h < 2; h++) {
+            const int e = tid + kGemmThreads * h, kr = e >> 4, q4 = (e & 15) * 4;
+            *reinterpret_cast<float4 *>(&As[buf][kr][q4]) = ra[h];
+            *reinterpret_cast<float4 *>(&Bs[buf][kr][q4]) = rb[h];
         }
-        *reinterpret_cast<float4 *>(&Bs[bk][bc]) = bv;
-        __syncthreads();
+    };
+    float acc[8][4] = {};
+    load(0);
+    store(0);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < g.nh; k0 += kBK) {
+        const bool more = k0 + kBK < g.nh;
+        if (more) load(k0 + kBK);
 #pragma unroll
         for (int k = 0; k < kBK; k++) {
-            const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
-            const float ai[4] = {a.x, a.y, a.z, a.w}, bj[4] = {b.x, b.y, b.z, b.w};
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+            const float ai[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bj[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-            for (int i = 0; i < 4; i++)
+            for (int i = 0; i < 8; i++)
 #pragma unroll
                 for (int jj = 0; jj < 4; jj++) acc[i][jj] = fmaf(ai[i], bj[jj], acc[i][jj]);
         }
+        if (more) store(buf ^ 1);
         __syncthreads();
+        buf ^= 1;
     }
     const int64_t base = tri_offset(it.m, g.T) + it.p;     // l = m + p + 2 (r0 + row)
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int row = ty * 4 + i;
+    for (int i = 0; i < 8; i++) {
+        const int row = ty * 8 + i;
         if (row >= it.nr) continue;
         const int64_t o = base + 2 * (int64_t)(it.r0 + row);
 #pragma unroll
@@ -214,21 +237,26 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
     *out = nullptr;
     if (nlat < 2 || nlat % 2 || nlat > 1 << 15 || T < 0 || T + 1 > nlat) return ZFPX_EINVAL;   // grid z = nlat
     auto *p = new zfpx_legendre_s();
-    p->nlat = nlat; p->T = T; p->nh = nlat / 2; p->lda = (p->nh + 3) / 4 * 4;
+    p->nlat = nlat; p->T = T; p->nh = nlat / 2;
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ZFPX_ECUDA; }
     std::vector<double> mu, w;
     gauss_legendre(nlat, mu, w);
     const int nh = p->nh;
     std::vector<double> s(nh);
     for (int j = 0; j < nh; j++) s[j] = std::sqrt(std::max(0.0, 1.0 - mu[j] * mu[j]));
-    // rows: for m = 0..T, parity 0 then 1, l = m + p, m + p + 2, ... <= T
-    int64_t nrows = 0;
-    for (int m = 0; m <= T; m++) nrows += T - m + 1;
-    std::vector<float> tab((size_t)nrows * p->lda, 0.0f);
+    // blocks: for m = 0..T, parity 0 then 1, a [nh][ldm] block whose column i
+    // is the row l = m + p + 2 i (ldm = that parity's row count rounded up to 4)
+    int64_t total = 0;
+    for (int m = 0; m <= T; m++)
+        for (int par = 0; par < 2; par++) {
+            const int cnt = (T - m - par) >= 0 ? (T - m - par) / 2 + 1 : 0;
+            total += (int64_t)nh * ((cnt + 3) / 4 * 4);
+        }
+    std::vector<float> tab((size_t)total, 0.0f);
     std::vector<LegItem> items;
     std::vector<double> pmm(nh, std::sqrt(0.5)), P0(nh), P1(nh), P2(nh);
     std::vector<std::vector<double>> rows;
-    int64_t row = 0;
+    int64_t blk = 0;
     for (int m = 0; m <= T; m++) {
         if (m > 0) {
             const double f = -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
@@ -246,12 +274,14 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
             for (int j = 0; j < nh; j++) rows[i][j] = a * (mu[j] * rows[i - 1][j] - b * rows[i - 2][j]);
         }
         for (int par = 0; par < 2; par++) {
-            const int64_t first = row;
-            int cnt = 0;
-            for (int i = par; i < L; i += 2, cnt++, row++)
-                for (int j = 0; j < nh; j++) tab[(size_t)row * p->lda + j] = (float)(w[j] * rows[i][j]);
+            const int cnt = par < L ? (L - 1 - par) / 2 + 1 : 0;
+            const int ldm = (cnt + 3) / 4 * 4;
+            for (int c = 0; c < cnt; c++)
+                for (int j = 0; j < nh; j++)
+                    tab[(size_t)(blk + (int64_t)j * ldm + c)] = (float)(w[j] * rows[par + 2 * c][j]);
             for (int r0 = 0; r0 < cnt; r0 += kBM)
-                items.push_back(LegItem{m, par, r0, std::min(kBM, cnt - r0), (first + r0) * (int64_t)p->lda});
+                items.push_back(LegItem{m, par, r0, std::min(kBM, cnt - r0), ldm, 0, blk});
+            blk += (int64_t)nh * ldm;
         }
     }
     p->nitems = (int)items.size();
@@ -296,7 +326,7 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
         return ZFPX_EINVAL;
     if (work_bytes < zfpx_legendre_workspace_bytes(p, n[2])) return ZFPX_ESIZE;
     LegGeom g{};
-    g.nlat = p->nlat; g.nh = p->nh; g.lda = p->lda; g.T = p->T; g.nlev = (int)n[2];
+    g.nlat = p->nlat; g.nh = p->nh; g.T = p->T; g.nlev = (int)n[2];
     g.ldc = (2 * g.nlev + 3) / 4 * 4;
     g.nct = (2 * g.nlev + kBN - 1) / kBN;
     g.is1 = stride[1]; g.is2 = stride[2]; g.os = out_stride;
@@ -308,7 +338,8 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
     if (rc) return rc;
     const int64_t nblk = (int64_t)p->nitems * g.nct;
     if (nblk > 0x7fffffff) return ZFPX_EINVAL;
-    legendre_gemm_kernel<<<(unsigned)nblk, 256, 0, (cudaStream_t)stream>>>(p->d_table, G, p->d_items, g, d_are, d_aim);
+    legendre_gemm_kernel<<<(unsigned)nblk, kGemmThreads, 0, (cudaStream_t)stream>>>(p->d_table, G, p->d_items, g, d_are,
+                                                                                 d_aim);
     count_launch();
     return check_launch();
 }
