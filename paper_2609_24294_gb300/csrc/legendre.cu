@@ -96,7 +96,8 @@ __global__ void __launch_bounds__(256) legendre_fold_kernel(const float *__restr
     }
 }
 
-// 64 x 64 outputs per CTA of 128 threads, each 8 rows x 4 columns; 16-deep k
+// 64 x 64 outputs per CTA of 128 threads (2 x 2 warps of 32 x 32), each thread
+// 8 rows x 4 columns; 16-deep k
 // steps, the next step's tiles loaded into registers while the current one is
 // multiplied out of the other shared-memory buffer (one barrier per step).
 // A tiles come from the latitude-major table block ([j][row], rows of one
@@ -117,7 +118,12 @@ __global__ void __launch_bounds__(kGemmThreads) legendre_gemm_kernel(const float
     const float *A = table + it.aoff;
     const float *B = G + ((int64_t)it.m * 2 + it.p) * g.nh * g.ldc;
     const int N = 2 * g.nlev;
-    const int ty = tid >> 4, tx = tid & 15;                 // rows 8 ty .. 8 ty + 7, columns 4 tx .. 4 tx + 3
+    // warp w holds rows 32 (w >> 1) .. + 31 and columns 32 (w & 1) .. + 31; lane
+    // (ly, lx) rows 8 ly .. + 7 and columns 4 lx .. + 3 of those.  A warp whose
+    // rows or columns all lie past the tile's edge skips the multiply-adds.
+    const int w = tid >> 5, lane = tid & 31;
+    const int r_base = 32 * (w >> 1) + 8 * (lane >> 3), c_base = 32 * (w & 1) + 4 * (lane & 7);
+    const bool active = 32 * (w >> 1) < it.nr && c0 + 32 * (w & 1) < N;
     // loaders: two float4 of A and two of B per thread; element e = tid + 128 h
     // covers k-row e / 16 and the four rows / columns 4 (e % 16) .. + 3
     float4 ra[2], rb[2];
@@ -155,11 +161,12 @@ __global__ void __launch_bounds__(kGemmThreads) legendre_gemm_kernel(const float
     for (int k0 = 0; k0 < g.nh; k0 += kBK) {
         const bool more = k0 + kBK < g.nh;
         if (more) load(k0 + kBK);
+        if (active)
 #pragma unroll
         for (int k = 0; k < kBK; k++) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 8 + 4]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][r_base]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][r_base + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][c_base]);
             const float ai[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bj[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
             for (int i = 0; i < 8; i++)
@@ -173,12 +180,12 @@ __global__ void __launch_bounds__(kGemmThreads) legendre_gemm_kernel(const float
     const int64_t base = tri_offset(it.m, g.T) + it.p;     // l = m + p + 2 (r0 + row)
 #pragma unroll
     for (int i = 0; i < 8; i++) {
-        const int row = ty * 8 + i;
+        const int row = r_base + i;
         if (row >= it.nr) continue;
         const int64_t o = base + 2 * (int64_t)(it.r0 + row);
 #pragma unroll
         for (int jj = 0; jj < 4; jj++) {
-            const int c = c0 + tx * 4 + jj;
+            const int c = c0 + c_base + jj;
             if (c >= N) continue;
             const int part = c >= g.nlev, lev = part ? c - g.nlev : c;
             (part ? aim : are)[(int64_t)lev * g.os + o] = acc[i][jj];
