@@ -299,21 +299,6 @@ def _events_ms(fn, reps, warmup=2):
 
 def _octahedral_fields():
     import torch
-    if args.profile_case == "sht":
-        xd = torch.from_numpy(make_field()).cuda()
-        nz, ny, nx = xd.shape
-        re = torch.empty((nz, ny, nx // 2), device="cuda")
-        im = torch.empty_like(re)
-        leg = z.Legendre(ny, nx // 2 - 1)
-        a_re = torch.empty((nz, leg.ncoeffs), device="cuda")
-        a_im = torch.empty_like(a_re)
-        for _ in range(max(1, args.steps)):
-            z.zfpx_rfft_lon(xd, re, im)
-            leg.forward(re, im, a_re, a_im)
-        torch.cuda.synchronize()
-        leg.close()
-        print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": 3 * max(1, args.steps)}))
-        return 0
     from fieldgen import octahedral as og
     fields = []
     for i, (nlev, kind, dims, rate) in enumerate(og.O1280_TEN_FIELDS):
