@@ -96,3 +96,41 @@ def test_calls_reject_bad_arguments_before_any_launch(zfpx):
     assert zfpx.zfpx_stream_bytes(3, 8, (8, 8, 8)) == 8 * 64
     assert zfpx.zfpx_stream_bytes(1, 8, (9, 2, 3)) == 3 * 2 * 3 * 4
     assert zfpx.zfpx_stream_bytes(2, 8, (9, 6, 3)) == 3 * 2 * 3 * 16
+
+
+def test_float64_and_spectral_calls_reject_bad_arguments_before_any_launch(zfpx):
+    """float64 codec, longitude FFT and Legendre transform: argument checks run
+    on the host before any CUDA call (so here, without a GPU, they answer)."""
+    L = zfpx.lib()
+    before = zfpx.zfpx_launch_count()
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    s = (ctypes.c_int64 * 3)(1, 8, 64)
+    p, q = ctypes.c_void_p(256), ctypes.c_void_p(4096)
+    # float64 codec (rates 1..32, 8-byte alignment, capacity)
+    assert zfpx.zfpx_stream_bytes_f64(16, (9, 6, 5)) == 3 * 2 * 2 * 8 * 16
+    assert zfpx.zfpx_stream_bytes_f64(0, (4, 4, 4)) == 0 and zfpx.zfpx_stream_bytes_f64(33, (4, 4, 4)) == 0
+    for rate in (0, 33):
+        assert L.zfpx_encode_f64(rate, p, n, s, q, 1 << 20, None) == -1
+        assert L.zfpx_decode_f64(rate, q, 1 << 20, n, s, p, None) == -1
+    assert L.zfpx_encode_f64(16, None, n, s, q, 1 << 20, None) == -1
+    assert L.zfpx_encode_f64(16, p, n, s, ctypes.c_void_p(4097), 1 << 20, None) == -1
+    assert L.zfpx_encode_f64(16, p, n, s, q, 8 * 16 * 8 - 1, None) == -2
+    assert L.zfpx_decode_f64(16, q, 8 * 16 * 8 - 1, n, s, p, None) == -2
+    # longitude FFT: N even with N/2 = 2^a 3^b 5^c, N <= 8192, 1 <= K <= N/2 + 1, rows contiguous
+    for nx, K in [(7, 1), (14, 1), (16386, 1), (16, 0), (16, 10)]:
+        nn = (ctypes.c_int64 * 3)(nx, 2, 2)
+        ss = (ctypes.c_int64 * 3)(1, nx + nx % 2, 2 * (nx + nx % 2))
+        os_ = (ctypes.c_int64 * 3)(1, 16, 32)
+        assert L.zfpx_rfft_lon(p, nn, ss, K, q, q, os_, None) == -1, (nx, K)
+    nn = (ctypes.c_int64 * 3)(16, 2, 2)
+    assert L.zfpx_rfft_lon(p, nn, (ctypes.c_int64 * 3)(2, 32, 64), 8, q, q, (ctypes.c_int64 * 3)(1, 8, 16), None) == -1
+    assert L.zfpx_rfft_lon(ctypes.c_void_p(260), nn, (ctypes.c_int64 * 3)(1, 16, 32), 8, q, q,
+                           (ctypes.c_int64 * 3)(1, 8, 16), None) == -1                     # rows off 8 bytes
+    assert L.zfpx_rfft_lon(p, nn, (ctypes.c_int64 * 3)(1, 17, 34), 8, q, q, (ctypes.c_int64 * 3)(1, 8, 16), None) == -1
+    # Legendre plan: nlat even, at most 32768, 0 <= T <= nlat - 1
+    h = ctypes.c_void_p()
+    for nlat, T in [(3, 1), (0, 0), (8, 8), (8, -1), (1 << 16, 10)]:
+        assert L.zfpx_legendre_create(ctypes.byref(h), nlat, T) == -1, (nlat, T)
+    assert L.zfpx_legendre_workspace_bytes(None, 5) == 0
+    assert L.zfpx_legendre_forward(None, p, p, n, s, q, q, 64, q, 1 << 20, None) == -1
+    assert zfpx.zfpx_launch_count() == before
