@@ -283,9 +283,10 @@ ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t 
  * nodes and weights and the table w_j Pbar_l^m(mu_j) over the northern half
  * (computed in double, rounded once; about (T+1)(T+2) nlat bytes of device
  * memory, a synchronous upload); nlat even, at most 32768, T + 1 <= nlat.
- * zfpx_legendre_forward needs caller-owned device scratch d_work (16-byte
- * aligned) of zfpx_legendre_workspace_bytes(plan, levels) bytes; calls that
- * share d_work must not overlap on the GPU.  Single precision throughout.
+ * zfpx_legendre_forward takes n[1] equal to the plan's nlat and 1 .. 2^20
+ * levels, and needs caller-owned device scratch d_work (16-byte aligned) of
+ * zfpx_legendre_workspace_bytes(plan, levels) bytes; calls that share d_work
+ * must not overlap on the GPU.  Single precision throughout.
  * Errors: ZFPX_EINVAL (NULL, sizes, strides, alignment), ZFPX_ESIZE,
  * ZFPX_ECUDA. */
 typedef struct zfpx_legendre_s *zfpx_legendre;
