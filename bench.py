@@ -787,6 +787,38 @@ def extra_network_model(z, xd, reps):
             "paper_speedup_N121": nm.PAPER_SPEEDUP_N121}
 
 
+def extra_sht_step(net, sht):
+    """One forward spectral-transform step of the Table 1 grid (2560 x 1280 x 137,
+    T1279) at the node counts of Table 1, from this run's measurements: the row
+    transposition's per-rank kernel times and modelled exchange (extras
+    network_model), the column transposition taken to cost the same, and one
+    rank's FFT and Legendre shares at the rates measured on the 1280 x 640 x 137
+    field (extras sht_fourier; values per second for the FFT, folded flops per
+    second for the Legendre transform).  Serial, as the paper's model."""
+    from paper_2609_24294_gb300 import netmodel as nm
+    fft_rate = 1280 * 640 * 137 / (sht["fft_ms"] / 1e3)
+    leg_rate = 2.0 * 2 * 137 * 320 * 640 * 641 / 2 / (sht["legendre_ms"] / 1e3)
+    tr, fft_s, leg_s = {}, {}, {}
+    for N in nm.TABLE1_N:
+        row = net["per_N"][N]
+        tr[N] = {s: (row[s]["pack_us"] / 1e6, row[s]["comm_us"] / 1e6, row[s]["unpack_us"] / 1e6)
+                 for s in nm.STRATEGIES}
+        fft_s[N] = nm.fft_values_per_rank(N) / fft_rate
+        leg_s[N] = nm.legendre_flops_per_rank(N) / leg_rate
+    res = nm.sht_step(nm.TABLE1_N, tr, fft_s, leg_s)
+    table = {}
+    for N in nm.TABLE1_N:
+        table[N] = {"fft_us": round(1e6 * fft_s[N], 1), "legendre_us": round(1e6 * leg_s[N], 1)}
+        for s in nm.STRATEGIES:
+            table[N][s] = {"step_us": round(1e6 * res[N][s]["step_s"], 1),
+                           "speedup_step": round(res[N][s]["speedup_step"], 3),
+                           "speedup_transposition": round(res[N][s]["speedup_transposition"], 3)}
+    return {"workload": "forward SHT step of 2560x1280x137 (T1279) at N = 4..121: row transposition, FFT, "
+                        "column transposition (taken equal to the row one), Legendre; serial; compute scaled "
+                        "from the rates measured on the 1280x640x137 field",
+            "per_N": table}
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(args):
     import torch
@@ -1020,6 +1052,10 @@ def run_gpu(args):
             extras["sht_fourier"] = extra_sht_fourier(z, xd, reps, peak)
         except Exception as e:
             extras["sht_fourier"] = {"error": repr(e)}
+        try:
+            extras["sht_step_model"] = extra_sht_step(extras["network_model"], extras["sht_fourier"])
+        except Exception as e:
+            extras["sht_step_model"] = {"error": repr(e)}
         torch.cuda.empty_cache()
         try:
             lens, ofields = _octahedral_fields()

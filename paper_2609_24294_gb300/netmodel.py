@@ -181,3 +181,49 @@ def model(N_list, sizes, per_rank, topo: Dragonfly = Dragonfly(), pieces=(1, 2, 
             row[s]["speedup_pipelined"] = row["float32"]["pipelined_s"] / row[s]["pipelined_s"]
         res[N] = row
     return res
+
+
+# The forward spectral transform of the Table 1 grid: 2560 longitudes, 1280
+# Gaussian latitudes, 137 levels, linear truncation T = 1279.
+SHT_GRID = (2560, 1280, 137)
+SHT_T = 1279
+
+
+def fft_values_per_rank(N: int, grid=SHT_GRID) -> float:
+    """Grid-point values of one rank's lambda-pencil (the longitude FFT's input)."""
+    nlon, nlat, nlev = grid
+    return nlon * nlat * nlev / N
+
+
+def legendre_flops_per_rank(N: int, grid=SHT_GRID, T: int = SHT_T) -> float:
+    """Folded float32 flops of one rank's share of the Legendre transform: every
+    coefficient takes nlat/2 multiply-adds for each of its real and imaginary
+    parts and each level; shared evenly over the N ranks."""
+    _, nlat, nlev = grid
+    return 2.0 * 2 * nlev * (nlat // 2) * (T + 1) * (T + 2) / 2 / N
+
+
+def sht_step(N_list, transposition, fft_s, legendre_s):
+    """One forward spectral-transform step per node count, in series (Sec. II-B's
+    order): the row transposition, the longitude FFT, the column transposition,
+    the Legendre transform.
+
+    transposition[N][strategy] = (pack-side s, exchange s, unpack-side s) of the
+    row transposition; the column transposition is taken to cost the same (in a
+    p x p grid its messages carry the same number of values, now wavenumbers).
+    fft_s[N], legendre_s[N]: one rank's compute, the same for every strategy.
+    Returns per N and strategy the four terms, the step time and the speedup of
+    the step over float32, beside the speedup of the transposition alone."""
+    res = {}
+    for N in N_list:
+        row = {}
+        for s in STRATEGIES:
+            tp, tc, tu = transposition[N][s]
+            t1 = tp + tc + tu
+            step = t1 + fft_s[N] + t1 + legendre_s[N]
+            row[s] = {"transposition_s": t1, "fft_s": fft_s[N], "legendre_s": legendre_s[N], "step_s": step}
+        for s in STRATEGIES:
+            row[s]["speedup_step"] = row["float32"]["step_s"] / row[s]["step_s"]
+            row[s]["speedup_transposition"] = row["float32"]["transposition_s"] / row[s]["transposition_s"]
+        res[N] = row
+    return res

@@ -115,3 +115,36 @@ def test_codec_time_is_added_in_series_and_pipelining_helps(sizes):
     # (its messages are as large or larger, Table 1)
     assert all(res[N]["float16"]["speedup_serial"] > res[N]["zfp16"]["speedup_serial"] for N in nm.TABLE1_N)
     assert math.isfinite(res[121]["zfp8"]["speedup_pipelined"])
+
+
+def test_sht_step_sums_and_dilutes_the_speedup():
+    from paper_2609_24294_gb300 import netmodel as nm
+    Ns = (16, 64)
+    tr = {N: {"float32": (1e-4, 4e-3, 1e-4), "float16": (1e-4, 2e-3, 1e-4),
+              "zfp16": (2e-4, 2e-3, 2e-4), "zfp8": (2e-4, 1e-3, 2e-4)} for N in Ns}
+    zero = {N: 0.0 for N in Ns}
+    r0 = nm.sht_step(Ns, tr, zero, zero)
+    for N in Ns:
+        for s in nm.STRATEGIES:
+            assert abs(r0[N][s]["step_s"] - 2 * sum(tr[N][s])) < 1e-15
+            # no local compute: the step's speedup is the transposition's
+            assert abs(r0[N][s]["speedup_step"] - r0[N][s]["speedup_transposition"]) < 1e-12
+    prev = None
+    for c in (1e-4, 1e-3, 1e-2):
+        r = nm.sht_step(Ns, tr, {N: c for N in Ns}, {N: 2 * c for N in Ns})
+        sp = r[64]["zfp8"]["speedup_step"]
+        assert abs(r[64]["zfp8"]["step_s"] - (2 * sum(tr[64]["zfp8"]) + 3 * c)) < 1e-15
+        assert 1.0 < sp < r[64]["zfp8"]["speedup_transposition"]        # diluted, still faster
+        if prev is not None:
+            assert sp < prev                                             # more compute, less speedup
+        prev = sp
+        assert r[64]["float32"]["speedup_step"] == 1.0
+
+
+def test_per_rank_work_of_the_t1279_grid():
+    from paper_2609_24294_gb300 import netmodel as nm
+    assert nm.fft_values_per_rank(1) == 2560 * 1280 * 137
+    assert nm.fft_values_per_rank(64) * 64 == 2560 * 1280 * 137
+    # T1279 on 1280 latitudes: (T+1)(T+2)/2 coefficients, 640 multiply-adds each per part and level
+    assert nm.legendre_flops_per_rank(1) == 4 * 137 * 640 * 1280 * 1281 / 2
+    assert abs(nm.legendre_flops_per_rank(121) * 121 - nm.legendre_flops_per_rank(1)) < 1e-3
