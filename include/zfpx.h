@@ -289,6 +289,11 @@ ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t 
  * must not overlap on the GPU.  Single precision throughout.
  * Errors: ZFPX_EINVAL (NULL, sizes, strides, alignment), ZFPX_ESIZE,
  * ZFPX_ECUDA. */
+/* The Gauss-Legendre latitudes the transform expects: mu[i] = sin(latitude),
+ * north to south, and the weights w[i] (sum 2), for n = 1 .. 32768 points, by
+ * Newton's iteration on P_n in double precision (the nodes the plan uses).
+ * Host arrays of n doubles each; no GPU work.  Errors: ZFPX_EINVAL. */
+ZFPX_API int zfpx_gauss_legendre(int n, double *mu, double *w);
 typedef struct zfpx_legendre_s *zfpx_legendre;
 ZFPX_API int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T);
 ZFPX_API void zfpx_legendre_destroy(zfpx_legendre plan);

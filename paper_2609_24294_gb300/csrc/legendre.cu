@@ -211,7 +211,7 @@ void gauss_legendre(int n, std::vector<double> &mu, std::vector<double> &w)
                 p1 = p2;
             }
             if (n == 1) { p1 = x; p0 = 1.0; }
-            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            dp = n * (x * p1 - p0) / -((1.0 - x) * (1.0 + x));
             const double dx = p1 / dp;
             x -= dx;
             if (std::fabs(dx) < 1e-16) break;
@@ -224,10 +224,10 @@ void gauss_legendre(int n, std::vector<double> &mu, std::vector<double> &w)
             p1 = p2;
         }
         if (n == 1) { p1 = x; p0 = 1.0; }
-        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        dp = n * (x * p1 - p0) / -((1.0 - x) * (1.0 + x));
         mu[i] = x;
         mu[n - 1 - i] = -x;
-        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - x * x) * dp * dp);
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - x) * (1.0 + x) * dp * dp);   // 1 - x^2 without cancellation
     }
 }
 
@@ -302,6 +302,15 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
         return ZFPX_ECUDA;
     }
     *out = p;
+    return ZFPX_OK;
+}
+
+int zfpx_gauss_legendre(int n, double *mu, double *w)
+{
+    if (n < 1 || n > (1 << 15) || !mu || !w) return ZFPX_EINVAL;
+    std::vector<double> m, ww;
+    gauss_legendre(n, m, ww);
+    for (int i = 0; i < n; i++) { mu[i] = m[i]; w[i] = ww[i]; }
     return ZFPX_OK;
 }
 

@@ -122,6 +122,8 @@ def lib():
         "zfpx_encode_f64": ([ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_decode_f64": ([ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
         "zfpx_rfft_lon": ([vp, i64p, i64p, ctypes.c_int, vp, vp, i64p, vp], ctypes.c_int),
+        "zfpx_gauss_legendre": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                                ctypes.c_int),
         "zfpx_legendre_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_legendre_destroy": ([vp], None),
         "zfpx_legendre_workspace_bytes": ([vp, ctypes.c_int64], sz),
@@ -399,6 +401,15 @@ def zfpx_rfft_lon(src, re, im, stream=None):
     _, os_ = field_view(re)
     _check(lib().zfpx_rfft_lon(_dev(src, "src"), _i64x3(n), _i64x3(s), int(re.shape[-1]), _dev(re, "re"),
                                _dev(im, "im"), _i64x3(os_), _stream(stream)), "zfpx_rfft_lon")
+
+
+def zfpx_gauss_legendre(n):
+    """(mu, w): the Gauss-Legendre latitudes (sin of latitude, north to south) and
+    weights the Legendre plan uses, as two lists of n floats (host computation)."""
+    mu = (ctypes.c_double * int(n))()
+    w = (ctypes.c_double * int(n))()
+    _check(lib().zfpx_gauss_legendre(int(n), mu, w), "zfpx_gauss_legendre")
+    return list(mu), list(w)
 
 
 class Legendre:

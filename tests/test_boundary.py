@@ -134,3 +134,37 @@ def test_float64_and_spectral_calls_reject_bad_arguments_before_any_launch(zfpx)
     assert L.zfpx_legendre_workspace_bytes(None, 5) == 0
     assert L.zfpx_legendre_forward(None, p, p, n, s, q, q, 64, q, 1 << 20, None) == -1
     assert zfpx.zfpx_launch_count() == before
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 32, 640, 1280, 2560])
+def test_gauss_legendre_nodes_of_the_library(zfpx, n):
+    """The nodes and weights behind the Legendre plan's table (host code, no GPU)
+    against numpy's Gauss-Legendre routine, north to south."""
+    import numpy as np
+    mu, w = zfpx.zfpx_gauss_legendre(n)
+    x, ww = np.polynomial.legendre.leggauss(n)
+    np.testing.assert_allclose(mu, x[::-1], rtol=0, atol=4e-15)
+    # numpy's weights near the poles carry relative errors up to ~1e-7 at n = 2560
+    np.testing.assert_allclose(w, ww[::-1], rtol=5e-7, atol=0)
+    assert abs(sum(w) - 2.0) < 1e-12
+    with pytest.raises(zfpx.ZfpxError):
+        zfpx.zfpx_gauss_legendre(0)
+    # the outermost weights against a 40-digit Newton iteration on P_n
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+
+    def pn(t):
+        p0, p1 = mp.mpf(1), t
+        for k in range(2, n + 1):
+            p0, p1 = p1, ((2 * k - 1) * t * p1 - (k - 1) * p0) / k
+        return p1, p0
+
+    for i in range(min(n, 2)):
+        t = mp.mpf(mu[i])
+        for _ in range(4):
+            p, pm = pn(t)
+            t = t - p / (n * (t * p - pm) / (t * t - 1))
+        p, pm = pn(t)
+        d = n * (t * p - pm) / (t * t - 1)
+        assert abs(mu[i] - t) < 1e-16
+        assert abs((w[i] - 2 / ((1 - t * t) * d * d)) / w[i]) < 1e-9
