@@ -168,3 +168,36 @@ def test_gauss_legendre_nodes_of_the_library(zfpx, n):
         d = n * (t * p - pm) / (t * t - 1)
         assert abs(mu[i] - t) < 1e-16
         assert abs((w[i] - 2 / ((1 - t * t) * d * d)) / w[i]) < 1e-9
+
+
+def test_header_is_plain_c_and_links(zfpx, tmp_path):
+    """A C99 program includes include/zfpx.h with every warning on, links the
+    library and calls host-only entry points (no GPU)."""
+    import os
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "t.c"
+    src.write_text(
+        '#include "zfpx.h"\n#include <stdio.h>\n'
+        "int main(void) {\n"
+        "    double mu[4], w[4];\n"
+        "    int64_t n[3] = {9, 6, 5};\n"
+        "    zfpx_legendre p = 0;\n"
+        "    if (zfpx_gauss_legendre(4, mu, w) != ZFPX_OK) return 1;\n"
+        '    printf("%.17g %.17g %zu %d\\n", mu[0], w[0], zfpx_stream_bytes_f64(16, n),\n'
+        "           zfpx_legendre_create(&p, 3, 1));\n"
+        "    return 0;\n}\n")
+    lib = zfpx.library_path()
+    exe = tmp_path / "t"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(root, "include"),
+                        str(src), "-o", str(exe), lib, "-Wl,-rpath," + os.path.dirname(lib)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    assert abs(float(out[0]) - 0.8611363115940526) < 1e-15          # the 4-point Gauss-Legendre node
+    assert abs(float(out[1]) - 0.34785484513745385) < 1e-15         # and its weight
+    assert int(out[2]) == 3 * 2 * 2 * 8 * 16 and int(out[3]) == -1
