@@ -1096,13 +1096,56 @@ def run_gpu(args):
             "gpu_launches": int(launches),
             "clocks": clk,
             "kernels": kern,
-            "comparators": comp,
-            "error": err,
-            "extras": extras,
         }
-        print(json.dumps(line), flush=True)
+        detail = dict(line, comparators=comp, error=err, extras=extras)
+        emit(line, detail, args.detail_file)
     multirank.finalize()
     return 0
+
+
+HEADLINE_MAX_BYTES = 3800
+
+
+def _round_floats(o, digits=4):
+    if isinstance(o, float):
+        return float("%.*g" % (digits, o))
+    if isinstance(o, dict):
+        return {k: _round_floats(v, digits) for k, v in o.items()}
+    if isinstance(o, (list, tuple)):
+        return [_round_floats(v, digits) for v in o]
+    return o
+
+
+def headline(line, detail_file):
+    """The one-line result: the headline keys with floats kept to four significant
+    digits, the per-kernel table reduced to ms / GB/s / fraction, and the name of the
+    file that holds the full record (comparators, errors, extras)."""
+    out = dict(line)
+    if out.get("kernels"):
+        out["kernels"] = {k: {"ms": v["ms"], "GBps": v["GBps"], "frac": v["frac_of_measured_hbm"]}
+                          for k, v in out["kernels"].items()}
+    out["detail_file"] = detail_file
+    out = _round_floats(out)
+    s = json.dumps(out, separators=(",", ":"))
+    if len(s) > HEADLINE_MAX_BYTES:          # keep the parseable line short whatever it holds
+        out.pop("kernels", None)
+        if isinstance(out.get("roofline"), dict):
+            out["roofline"].pop("limiter", None)
+        s = json.dumps(out, separators=(",", ":"))
+    return s
+
+
+def emit(line, detail, detail_file):
+    """Writes the full record to `detail_file` and to stderr, then prints the compact
+    headline as the last line of stdout."""
+    full = json.dumps(detail, indent=1, default=str)
+    try:
+        with open(detail_file, "w") as f:
+            f.write(full + "\n")
+    except OSError as e:
+        log("could not write %s: %r" % (detail_file, e))
+    log(full)
+    print(headline(line, detail_file), flush=True)
 
 
 def run_profile_case(args):
@@ -1180,6 +1223,8 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--detail-file", default="bench_detail.json",
+                    help="where the full record (comparators, errors, extras) is written")
     ap.add_argument("--profile-case", choices=["batch", "blocks12", "sht"], default=None,
                     help="run a reduced workload for an ncu capture and exit")
     args = ap.parse_args()
