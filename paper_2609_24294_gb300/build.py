@@ -1,12 +1,17 @@
 """Build libzfpx.so in-tree with nvcc for sm_103a.
 
 Each translation unit is compiled in parallel to an object file, then linked
-into ``paper_2609_24294_gb300/libzfpx.so``.  Rebuilds only when a source or
-header is newer than the library.  ``python -m paper_2609_24294_gb300.build``
-does the same from the command line.
+into ``paper_2609_24294_gb300/libzfpx.so``.  The library is rebuilt unless a
+stamp beside it records the same hash of every source and header, the compiler
+flags, the nvcc version and the host machine (a library compiled on another
+machine, or from other sources, is never reused).  One line on stderr says
+whether it compiled.  ``python -m paper_2609_24294_gb300.build`` does the same
+from the command line.
 """
 import glob
+import hashlib
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -38,18 +43,45 @@ def _deps():
         [os.path.join(ROOT, "include", "zfpx.h"), os.path.abspath(__file__)]
 
 
-def up_to_date():
-    if not os.path.exists(LIB):
+STAMP = LIB + ".sha256"
+
+
+def _nvcc_version(nvcc):
+    try:
+        return subprocess.run([nvcc, "--version"], capture_output=True, text=True).stdout
+    except OSError:
+        return "nvcc not found"
+
+
+def source_hash(nvcc=None):
+    """Hash of everything the library is built from, and of where it is built."""
+    nvcc = nvcc or _nvcc()
+    h = hashlib.sha256()
+    for d in sorted(_deps()):
+        h.update(os.path.relpath(d, ROOT).encode() + b"\0")
+        h.update(open(d, "rb").read())
+    h.update(" ".join(ARCH + FLAGS[:-1]).encode())
+    h.update(_nvcc_version(nvcc).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+def up_to_date(digest=None):
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in _deps())
+    try:
+        return open(STAMP).read().strip() == (digest or source_hash())
+    except OSError:
+        return False
 
 
 def build(force=False, verbose=False):
-    if not force and up_to_date():
+    nvcc = _nvcc()
+    digest = source_hash(nvcc)
+    if not force and up_to_date(digest):
+        sys.stderr.write("libzfpx: up to date (sources sha256 %s, %s)\n" % (digest[:12], platform.machine()))
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
 
     def compile_one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -69,6 +101,10 @@ def build(force=False, verbose=False):
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(digest + "\n")
+    sys.stderr.write("libzfpx: compiled %d translation units for sm_103a (sources sha256 %s, %s)\n"
+                     % (len(objs), digest[:12], platform.machine()))
     return LIB
 
 
