@@ -7,7 +7,7 @@ its error by a round trip float32 -> float16 -> float32).
 * ``to_f16_rn``: IEEE 754 round-to-nearest-even, overflow to +-inf, subnormal
   halves kept -- this is numpy's float32 -> float16 conversion, used as is
   (a library routine; pinned against the definition in
-  tests/test_oracle_fp16.py).
+  tests/test_oracle_packs.py, test_fp16_rn_definition).
 * ``to_f16_rz``: round toward zero (the paper calls the cast a truncation): the
   float16 of largest magnitude not above |x|, same sign; finite values beyond
   the float16 range give +-65504 (IEEE round-toward-zero overflow), inf stays
