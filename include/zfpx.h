@@ -151,17 +151,19 @@ ZFPX_API int zfpx_pack_compress(zfpx_plan plan, int rate, const float *d_src, ui
  * chosen layout) and scatters the values into d_dst through the plan's dst
  * view; padding values are dropped.  Errors as above.
  *
- * For dims = 3 the kernels hand out work through counters kept with the
- * plan's device table of that rate (one pair for compression, one for
- * decompression), which each launch leaves at zero when it ends.  So calls
- * with the same plan, rate and direction must not overlap on the GPU (use
- * one stream, or order the streams); different plans, rates or directions
- * may run concurrently.  The same holds for zfpx_encode / zfpx_decode with
- * the same extents, strides and rate, and the counters are never reset by
- * the host: a launch that fails mid-kernel leaves the context unusable
- * anyway. */
+ * Neither call keeps state on the device between launches (the work split is
+ * fixed by the launch shape), so launches with the same plan may run on
+ * several streams at once, and graph replays need no reset. */
 ZFPX_API int zfpx_decompress_unpack(zfpx_plan plan, int rate, const uint8_t *d_in, size_t len,
                            float *d_dst, int layout, void *stream);
+
+/* Launch shape of the 3-D codec kernels: every warp codes `upw` consecutive
+ * units of 32 blocks (encode != 0: compression, else decompression; rate 8
+ * or 16); 0 restores the library's default.  Process-wide; results never
+ * depend on it (the autotuner sets it).  Errors: ZFPX_EINVAL.
+ * zfpx_get_units_per_warp returns the value in use. */
+ZFPX_API int zfpx_set_units_per_warp(int encode, int rate, int upw);
+ZFPX_API int zfpx_get_units_per_warp(int encode, int rate);
 
 /* ---- comparators (Sec. I; Sec. IV-D, Table 1 columns Float32/Float16) ----- */
 /* float32 -> float16 cast of every message (round_mode ZFPX_ROUND_*). */
@@ -415,7 +417,7 @@ ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
  * allocator, in loops that must not pay for an allocation, with a fixed
  * device memory map.  It does what zfpx_pack_compress (ZFPX_LAYOUT_RECV)
  * followed by zfpx_decompress_unpack do, d_src -> d_dst through the plan at
- * `rate` (8 or 16), with the same result, but it keeps its work counters,
+ * `rate` (8 or 16), with the same result, but it keeps
  * the plan's message table and the compressed messages in one library-owned
  * device array of ZFPX_NOALLOC_SCRATCH_BYTES (64 MiB), reserved on every GPU
  * that loads the library until the process exits, and calls no allocation
@@ -423,9 +425,11 @@ ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
  * needs no zfpx_plan_prepare.  The first call on each device looks the array
  * up with that device current.  Every call shares the array, so calls that
  * overlap on the GPU (other streams, other host threads) race; calls in order
- * on one stream do not.  The message table is copied from host memory, so the
- * call returns after the copy has read it.  Errors: ZFPX_EINVAL, ZFPX_ESIZE
- * (table plus compressed messages larger than the array), ZFPX_ECUDA. */
+ * on one stream do not.  The message table is copied from pageable host
+ * memory, so the call returns after the copy has read it, and the call
+ * cannot be recorded into a CUDA graph: on a capturing stream it returns
+ * ZFPX_EINVAL and enqueues nothing.  Errors: ZFPX_EINVAL, ZFPX_ESIZE (table
+ * plus compressed messages larger than the array), ZFPX_ECUDA. */
 #define ZFPX_NOALLOC_SCRATCH_BYTES (64u << 20)
 ZFPX_API int zfpx_transpose_noalloc(zfpx_plan plan, int rate, const float *d_src, float *d_dst, void *stream);
 

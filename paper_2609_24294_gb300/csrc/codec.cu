@@ -19,6 +19,7 @@
 // which each plane is one 64-bit word and group testing is a find-first-set
 // per newly significant coefficient.  Each warp processes a contiguous range
 // of 32-block chunks, so the message lookup is a forward scan.
+#include <atomic>
 #include <climits>
 #include <cuda_runtime.h>
 
@@ -75,27 +76,17 @@ struct MsgWalk {
     }
 };
 
-// Dynamic work split of the 3-D kernels: whole warps claim 32-block units
-// from a counter, issuing the next claim before coding the current unit so
-// that its latency hides.  The last warp to run dry resets the counters for
-// the next launch, so no launch needs a memset; two launches that share
-// counters must not overlap on the GPU.
-struct UnitClaim {
-    uint32_t *ctr;                                   // [claim, done]
-    int lane;
-    __device__ __forceinline__ uint32_t next() const
+// Work split of the 3-D kernels: warp w of the grid codes the upw consecutive
+// 32-block units starting at w * upw (the grid has ceil(units / (upw * warps))
+// CTAs), and the hardware's CTA scheduler balances the CTAs over the SMs.  No
+// counters in device memory: launches on any streams may overlap, and a CUDA
+// graph replays a launch as it was recorded.
+struct UnitRange {
+    int64_t c, c1;
+    __device__ __forceinline__ UnitRange(const LaunchGeom &g, int warps, int wid)
     {
-        uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(ctr, 1u);
-        return __shfl_sync(0xffffffffu, u, 0);
-    }
-    __device__ __forceinline__ void finish() const
-    {
-        const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
-        if (lane == 0 && atomicAdd(ctr + 1, 1u) == nwarps - 1) {
-            ctr[0] = 0u;
-            ctr[1] = 0u;
-        }
+        c = ((int64_t)blockIdx.x * warps + wid) * g.upw;
+        c1 = min(c + (int64_t)g.upw, g.nunits);
     }
 };
 
@@ -114,11 +105,13 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *wsm = smem[wid];
     SmemPlanes pl{splanes[wid], lane};
-    const UnitClaim cl{g.ctr, lane};
-    for (uint32_t u = cl.next(); (int64_t)u < g.nunits;) {
-        const int64_t c = u;
-        u = cl.next();
-        const MsgDev &m = g.msgs[find_msg(g.msgs, g.nmsg, c)];
+    const UnitRange ur(g, kEnc3Warps<RATE>, wid);
+    if (ur.c >= ur.c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, ur.c);
+    for (int64_t c = ur.c; c < ur.c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
         const int64_t unit0 = m.unit0, nblocks = m.nblocks, src_off = m.src_off;
         const int64_t boff = layout ? m.off[1] : m.off[0];
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
@@ -181,7 +174,6 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         }
         __syncwarp();
     }
-    cl.finish();
 }
 
 template <int RATE, bool VEC>
@@ -196,11 +188,13 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
     const StreamTile tile{t32, lane};
 #pragma unroll
     for (int r = 0; r < kTileZeroRows<RATE>; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
-    const UnitClaim cl{g.ctr + 2, lane};
-    for (uint32_t u = cl.next(); (int64_t)u < g.nunits;) {
-        const int64_t c = u;
-        u = cl.next();
-        const MsgDev &m = g.msgs[find_msg(g.msgs, g.nmsg, c)];
+    const UnitRange ur(g, kDec3Warps<RATE>, wid);
+    if (ur.c >= ur.c1) return;
+    MsgWalk walk;
+    walk.start(g.msgs, g.nmsg, ur.c);
+    for (int64_t c = ur.c; c < ur.c1; c++) {
+        walk.advance(c);
+        const MsgDev &m = g.msgs[walk.mi];
         const int64_t unit0 = m.unit0, nblocks = m.nblocks, dst_off = m.dst_off;
         const int64_t boff = layout ? m.off[1] : m.off[0];
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
@@ -262,7 +256,6 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         }
         __syncwarp();
     }
-    cl.finish();
 }
 
 // ================================================================= 1-D kernels
@@ -486,12 +479,22 @@ int grid_for(K kernel, int64_t nunits, int warps = kWarps)
 
 bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
-// One launch of a 3-D codec kernel (either alignment instantiation).
+// Consecutive 32-block units per warp of the 3-D kernels, [encode][rate 16?];
+// 0 = default.  The default was picked by timing on GB300 (the autotuner can
+// override it); results never depend on it.
+std::atomic<int> g_upw[2][2] = {{{0}, {0}}, {{0}, {0}}};
+constexpr int kDefaultUpw = 2;
+
+// One launch of a 3-D codec kernel (either alignment instantiation): one
+// warp per upw consecutive units.
 template <class In, class Out>
-void launch3(void (*kernel)(In, Out, LaunchGeom, int), int warps, const LaunchGeom &g, cudaStream_t st, In in,
-             Out out, int layout)
+void launch3(void (*kernel)(In, Out, LaunchGeom, int), int warps, int encode, int rate, LaunchGeom g,
+             cudaStream_t st, In in, Out out, int layout)
 {
-    kernel<<<grid_for(kernel, g.nunits, warps), 32 * warps, 0, st>>>(in, out, g, layout);
+    g.upw = units_per_warp(encode, rate);
+    const int64_t per_cta = (int64_t)g.upw * warps;
+    const int64_t grid = (g.nunits + per_cta - 1) / per_cta;
+    kernel<<<(unsigned)grid, 32 * warps, 0, st>>>(in, out, g, layout);
 }
 
 // vec: rows start on 16 bytes wherever a block starts (x0 multiple of 4).
@@ -510,9 +513,11 @@ int launch_encode(int dims, int rate, const float *src, uint8_t *out, const Laun
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
         if (rate == 8)
-            launch3(vec ? encode3_kernel<8, true> : encode3_kernel<8, false>, kEnc3Warps<8>, g, st, src, out, layout);
+            launch3(vec ? encode3_kernel<8, true> : encode3_kernel<8, false>, kEnc3Warps<8>, 1, 8, g, st, src, out,
+                    layout);
         else
-            launch3(vec ? encode3_kernel<16, true> : encode3_kernel<16, false>, kEnc3Warps<16>, g, st, src, out, layout);
+            launch3(vec ? encode3_kernel<16, true> : encode3_kernel<16, false>, kEnc3Warps<16>, 1, 16, g, st, src, out,
+                    layout);
     } else if (dims == 2) {
         if (rate == 8) encode2_kernel<8><<<grid_for(encode2_kernel<8>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
         else encode2_kernel<16><<<grid_for(encode2_kernel<16>, g.nunits), kThreads, 0, st>>>(src, out, g, layout, vec);
@@ -530,9 +535,11 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
     if (g.nunits == 0) return ZFPX_OK;
     if (dims == 3) {
         if (rate == 8)
-            launch3(vec ? decode3_kernel<8, true> : decode3_kernel<8, false>, kDec3Warps<8>, g, st, in, dst, layout);
+            launch3(vec ? decode3_kernel<8, true> : decode3_kernel<8, false>, kDec3Warps<8>, 0, 8, g, st, in, dst,
+                    layout);
         else
-            launch3(vec ? decode3_kernel<16, true> : decode3_kernel<16, false>, kDec3Warps<16>, g, st, in, dst, layout);
+            launch3(vec ? decode3_kernel<16, true> : decode3_kernel<16, false>, kDec3Warps<16>, 0, 16, g, st, in, dst,
+                    layout);
     } else if (dims == 2) {
         if (rate == 8) decode2_kernel<8><<<grid_for(decode2_kernel<8>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
         else decode2_kernel<16><<<grid_for(decode2_kernel<16>, g.nunits), kThreads, 0, st>>>(in, dst, g, layout, vec);
@@ -545,11 +552,30 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
 }
 
 }  // namespace
+
+int units_per_warp(int encode, int rate)
+{
+    const int v = g_upw[encode ? 1 : 0][rate == 16 ? 1 : 0].load(std::memory_order_relaxed);
+    return v > 0 ? v : kDefaultUpw;
+}
 }  // namespace zfpx
 
 using namespace zfpx;
 
 extern "C" {
+
+int zfpx_set_units_per_warp(int encode, int rate, int upw)
+{
+    if (!valid_codec_rate(rate) || upw < 0 || upw > 4096) return ZFPX_EINVAL;
+    g_upw[encode ? 1 : 0][rate == 16 ? 1 : 0].store(upw, std::memory_order_relaxed);
+    return ZFPX_OK;
+}
+
+int zfpx_get_units_per_warp(int encode, int rate)
+{
+    if (!valid_codec_rate(rate)) return ZFPX_EINVAL;
+    return units_per_warp(encode, rate);
+}
 
 int zfpx_pack_compress(zfpx_plan p, int rate, const float *d_src, uint8_t *d_out, size_t cap, int layout,
                        void *stream)
@@ -562,7 +588,7 @@ int zfpx_pack_compress(zfpx_plan p, int rate, const float *d_src, uint8_t *d_out
     int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
     if (rc) return rc;
     LaunchGeom g{};
-    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits; g.ctr = t->d_ctr;
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
     const int vec = vec_ok(d_src, p->ss, p, 0) ? 1 : 0;
     return launch_encode(p->dims, rate, d_src, d_out, g, layout, vec, (cudaStream_t)stream);
@@ -579,7 +605,7 @@ int zfpx_decompress_unpack(zfpx_plan p, int rate, const uint8_t *d_in, size_t le
     int rc = get_table(p, rate, UNIT_BLOCKS32, &t);
     if (rc) return rc;
     LaunchGeom g{};
-    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits; g.ctr = t->d_ctr;
+    g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }
     const int vec = vec_ok(d_dst, p->ds, p, 1) ? 1 : 0;
     return launch_decode(p->dims, rate, d_in, d_dst, g, layout, vec, (cudaStream_t)stream);
@@ -739,23 +765,25 @@ extern "C" int zfpx_transpose_noalloc(zfpx_plan p, int rate, const float *d_src,
     }
     const size_t table_bytes = (M * sizeof(MsgDev) + 255) / 256 * 256;
     const size_t stream_bytes = (size_t)ro;
-    // layout of the array: 256 bytes of work counters (zero between calls),
-    // the message table, the compressed messages
-    constexpr size_t kCtrBytes = 256;
-    if (kCtrBytes + table_bytes + stream_bytes > ZFPX_NOALLOC_SCRATCH_BYTES) return ZFPX_ESIZE;
+    // layout of the array: the message table, then the compressed messages
+    if (table_bytes + stream_bytes > ZFPX_NOALLOC_SCRATCH_BYTES) return ZFPX_ESIZE;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the table is copied from pageable host memory, which a stream capture
+    // cannot record: refuse while the stream is capturing
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) return ZFPX_ECUDA;
+    if (cs != cudaStreamCaptureStatusNone) return ZFPX_EINVAL;
     void *scratch = nullptr;
     int rc = noalloc_scratch(&scratch);
     if (rc) return rc;
     if (units == 0) return ZFPX_OK;
-    cudaStream_t st = (cudaStream_t)stream;
     // pageable source: the copy has read h before this call returns
     uint8_t *base = static_cast<uint8_t *>(scratch);
-    if (cudaMemcpyAsync(base + kCtrBytes, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (cudaMemcpyAsync(base, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return ZFPX_ECUDA;
-    uint8_t *buf = base + kCtrBytes + table_bytes;
+    uint8_t *buf = base + table_bytes;
     LaunchGeom g{};
-    g.msgs = reinterpret_cast<const MsgDev *>(base + kCtrBytes);
-    g.ctr = reinterpret_cast<uint32_t *>(base);
+    g.msgs = reinterpret_cast<const MsgDev *>(base);
     g.nmsg = (int)M;
     g.nunits = units;
     for (int a = 0; a < 3; a++) { g.ss[a] = p->ss[a]; g.ds[a] = p->ds[a]; }

@@ -149,10 +149,8 @@ int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out)
     t.nunits = units;
     if (M > 0) {
         const size_t tb = (M * sizeof(MsgDev) + 255) / 256 * 256;
-        if (cudaMalloc((void **)&t.d_msgs, tb + 256) != cudaSuccess) return ZFPX_ENOMEM;
-        t.d_ctr = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(t.d_msgs) + tb);
-        if (cudaMemcpy(t.d_msgs, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemset(t.d_ctr, 0, 256) != cudaSuccess) {
+        if (cudaMalloc((void **)&t.d_msgs, tb) != cudaSuccess) return ZFPX_ENOMEM;
+        if (cudaMemcpy(t.d_msgs, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice) != cudaSuccess) {
             cudaFree(t.d_msgs);
             return ZFPX_ECUDA;
         }

@@ -32,7 +32,7 @@ struct LaunchGeom {
     int64_t nunits;     // total work units
     int64_t ss[3];      // source strides (elements)
     int64_t ds[3];      // destination strides (elements)
-    uint32_t *ctr;      // 3-D codec work counters: encode claim / done, decode claim / done (zero between launches)
+    int32_t upw;        // 3-D codec kernels: consecutive work units per warp (grid = units / (upw * warps))
 };
 
 struct HostMsg {
@@ -42,8 +42,7 @@ struct HostMsg {
 
 // Device tables of one (rate, unit kind, device) for a plan.
 struct DevTable {
-    MsgDev *d_msgs = nullptr;   // one allocation: the table, then 4 work counters (zeroed)
-    uint32_t *d_ctr = nullptr;
+    MsgDev *d_msgs = nullptr;   // the message table
     int64_t nunits = 0;
 };
 
@@ -76,5 +75,8 @@ void count_launch();
 void uncount_launches(uint64_t n);   // launches recorded into a graph, not run
 bool valid_codec_rate(int rate);
 int check_launch();   // cudaGetLastError -> ZFPX_OK / ZFPX_ECUDA
+// Work units per warp of the 3-D codec kernels for (direction, rate); 0 = the
+// library's default.  Set through zfpx_set_units_per_warp (the autotuner).
+int units_per_warp(int encode, int rate);
 
 }  // namespace zfpx

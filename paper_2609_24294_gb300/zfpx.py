@@ -83,6 +83,8 @@ def lib():
                                    ctypes.c_int),
         "zfpx_graph_launch": ([vp, vp], ctypes.c_int),
         "zfpx_transpose_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "zfpx_set_units_per_warp": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_get_units_per_warp": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_capture_begin": ([vp], ctypes.c_int),
         "zfpx_server_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, sz, ctypes.c_int, ctypes.c_int],
                                ctypes.c_int),
@@ -650,6 +652,15 @@ class Batch:
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+def zfpx_set_units_per_warp(encode, rate, upw):
+    """Launch shape of the 3-D codec kernels: 32-block units per warp (0 = default)."""
+    _check(lib().zfpx_set_units_per_warp(int(bool(encode)), rate, upw), "zfpx_set_units_per_warp")
+
+
+def zfpx_get_units_per_warp(encode, rate):
+    return int(lib().zfpx_get_units_per_warp(int(bool(encode)), rate))
 
 
 def zfpx_transpose_noalloc(plan, rate, src, dst, stream=None):

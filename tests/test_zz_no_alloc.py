@@ -39,10 +39,14 @@ def _allocating_path(z, plan, rate, src):
     return out
 
 
-def test_noalloc_matches_allocating_path_two_calls(z):
+def test_noalloc_matches_allocating_path_calls_in_a_row(z):
+    # five calls in a row, each on a different plan: 3-D, 2-D and 1-D blocks, both rates,
+    # both transpositions, and a 2 x 8 x 8 field over 4 x 4 ranks whose longitude split
+    # leaves some messages empty
     cases = [((20, 36, 52), 2, 3, 0, 16, 250.0, 1, 3), ((17, 26, 37), 3, 2, 1, 8, 0.0, 2, 3),
-             ((9, 30, 44), 2, 2, 0, 8, 5.0, 3, 2)]
-    for shape, pr, pc, t, rate, offset, seed, dims in cases:     # calls in a row, different plans and rates
+             ((9, 30, 44), 2, 2, 0, 8, 5.0, 3, 2), ((6, 10, 37), 2, 3, 0, 8, 1.0, 4, 1),
+             ((8, 8, 2), 4, 4, 0, 16, 3.0, 5, 3)]
+    for shape, pr, pc, t, rate, offset, seed, dims in cases:
         src = _field(shape, seed, offset)
         plan = z.Plan.for_fields(src, pr, pc, t, dims)
         ref = _allocating_path(z, plan, rate, src)
@@ -61,3 +65,26 @@ def test_noalloc_rejects_oversize(z):
     rc = z.lib().zfpx_transpose_noalloc(plan.handle, 16, ctypes.c_void_p(src.data_ptr()),
                                         ctypes.c_void_p(src.data_ptr()), None)
     assert rc == -2                                      # ZFPX_ESIZE, nothing launched
+
+
+def test_noalloc_refuses_stream_capture(z):
+    # the message table comes from pageable host memory, which a capture cannot record
+    import ctypes
+    src = _field((8, 16, 16), 6, 0.0)
+    dst = torch.empty_like(src)
+    plan = z.Plan.for_fields(src, 2, 2, 0, 3)
+    s = torch.cuda.Stream()
+    h = ctypes.c_void_p(s.cuda_stream)
+    assert z.lib().zfpx_capture_begin(h) == 0
+    rc = z.lib().zfpx_transpose_noalloc(plan.handle, 8, ctypes.c_void_p(src.data_ptr()),
+                                        ctypes.c_void_p(dst.data_ptr()), h)
+    g = ctypes.c_void_p()
+    assert z.lib().zfpx_capture_end(ctypes.byref(g), h) == 0
+    z.lib().zfpx_graph_destroy(g)
+    assert rc == -1                                      # ZFPX_EINVAL, nothing recorded
+    # and the same call outside a capture still works
+    ref = _allocating_path(z, plan, 8, src)
+    got = torch.full_like(src, float("nan"))
+    z.zfpx_transpose_noalloc(plan, 8, src, got)
+    torch.cuda.synchronize()
+    assert torch.equal(got.view(torch.int32), ref.view(torch.int32))
