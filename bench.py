@@ -731,18 +731,33 @@ def _flushed_ms(fn, reps, flush):
     return sum(a.elapsed_time(b) for a, b in ev) / reps
 
 
+PIECES = (1, 2, 4, 8)
+
+
+def _strategy_fns(z, plan, s, r, pen, buf, out):
+    if s == "float32":
+        return (lambda: z.zfpx_pack(plan, pen, buf)), (lambda: z.zfpx_unpack(plan, buf, out))
+    if s == "float16":
+        return (lambda: z.zfpx_cast_fp16_pack(plan, z.ROUND_NEAREST, pen, buf),
+                lambda: z.zfpx_fp16_unpack(plan, buf, out))
+    return (lambda: z.zfpx_pack_compress(plan, r, pen, buf)), (lambda: z.zfpx_decompress_unpack(plan, r, buf, out))
+
+
 def extra_network_model(z, xd, reps):
     """The row transposition of the 2560 x 1280 x 137 grid at the node counts of
     Table 1: one rank's pack-side and unpack-side kernels timed on this GPU on
     that rank's z-pencil (lon/p x lat/p x 137, cut from the benchmark field, rows
     padded to a multiple of 4 values, L2 flushed before each launch), the Table 1 message sizes from the plan, and
     the communication-time model of netmodel (Dragonfly, 200 Gb/s, 1 us per
-    hop), serial as in the paper and pipelined per piece."""
+    hop), serial as in the paper and pipelined per piece.  For the pipelined
+    figure the pencil is also cut into k = 2, 4, 8 longitude pieces (starts on
+    multiples of 4 values), each piece's kernels timed alone, and the measured
+    pieces flow through the three-stage model."""
     import torch
     from paper_2609_24294_gb300 import netmodel as nm
     sizes = nm.message_sizes()
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")     # 256 MB > L2
-    per_rank = {}
+    per_rank, per_pieces = {}, {}
     for N in nm.TABLE1_N:
         p = nm.grid_side(N)
         nlat, nlon = 1280 // p, 2560 // p
@@ -750,27 +765,30 @@ def extra_network_model(z, xd, reps):
         pen = torch.empty(137, nlat, pitch, device="cuda")[:, :, :nlon]
         pen.copy_(xd[:, :nlat, :nlon])
         out = torch.empty(137, nlat, pitch, device="cuda")[:, :, :nlon]
-        plan = z.Plan.for_fields(pen, 1, 1, 0, 3)
-        t = {}
+        t, tk = {}, {}
         for s in nm.STRATEGIES:
             r = nm.RATE_OF[s]
-            plan.prepare(r)
-            buf = torch.empty(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
-            if s == "float32":
-                fp, fu = (lambda: z.zfpx_pack(plan, pen, buf)), (lambda: z.zfpx_unpack(plan, buf, out))
-            elif s == "float16":
-                fp = lambda: z.zfpx_cast_fp16_pack(plan, z.ROUND_NEAREST, pen, buf)
-                fu = lambda: z.zfpx_fp16_unpack(plan, buf, out)
-            else:
-                fp = lambda: z.zfpx_pack_compress(plan, r, pen, buf)
-                fu = lambda: z.zfpx_decompress_unpack(plan, r, buf, out)
-            t[s] = (_flushed_ms(fp, reps, flush) / 1e3, _flushed_ms(fu, reps, flush) / 1e3)
-            del buf
+            tk[s] = {}
+            for k in PIECES:
+                cuts = [min(nlon, (nlon * i // k + 3) // 4 * 4) for i in range(k)] + [nlon]
+                meas = []
+                for a, b in zip(cuts[:-1], cuts[1:]):
+                    if b <= a:
+                        continue
+                    plan = z.Plan.for_fields(pen[:, :, a:b], 1, 1, 0, 3, dst=out[:, :, a:b])
+                    plan.prepare(r)
+                    buf = torch.empty(plan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+                    fp, fu = _strategy_fns(z, plan, s, r, pen[:, :, a:b], buf, out[:, :, a:b])
+                    meas.append((_flushed_ms(fp, reps, flush) / 1e3, _flushed_ms(fu, reps, flush) / 1e3))
+                    plan.close()
+                    del buf
+                tk[s][len(meas)] = meas
+            t[s] = tk[s][1][0]
         per_rank[N] = t
-        plan.close()
+        per_pieces[N] = tk
         del pen, out
     del flush
-    res = nm.model(nm.TABLE1_N, sizes, per_rank)
+    res = nm.model(nm.TABLE1_N, sizes, per_rank, per_rank_pieces=per_pieces)
     table = {}
     for N in nm.TABLE1_N:
         table[N] = {s: {"MiB": round(res[N][s]["message_bytes"] / 2 ** 20, 2),
@@ -779,12 +797,53 @@ def extra_network_model(z, xd, reps):
                         "unpack_us": round(1e6 * res[N][s]["unpack_s"], 1),
                         "speedup_serial": round(res[N][s]["speedup_serial"], 3),
                         "speedup_pipelined": round(res[N][s]["speedup_pipelined"], 3),
-                        "pieces": res[N][s]["pieces"]} for s in nm.STRATEGIES}
+                        "pieces": res[N][s]["pieces"],
+                        "piece_pack_us": {k: [round(1e6 * a, 1) for a, _ in v] for k, v in per_pieces[N][s].items()
+                                          if k > 1}} for s in nm.STRATEGIES}
     return {"workload": "row transposition of 2560x1280x137 f32 at N = 4..121 (p x p ranks); per-rank "
                         "kernels timed on one rank's lon/p x lat/p x 137 pencil (row pitch a multiple of 4), L2 flushed; alpha-beta "
-                        "Dragonfly model (200 Gb/s links, 1 us/hop, injection-bound, no contention)",
+                        "Dragonfly model (200 Gb/s links, 1 us/hop, injection-bound, no contention); pipelined = "
+                        "measured pieces (1, 2, 4, 8 longitude cuts) through a three-stage flow shop",
             "per_N": table,
             "paper_speedup_N121": nm.PAPER_SPEEDUP_N121}
+
+
+def extra_pipeline(z, xd, plan, reps):
+    """The benchmark plan (1280 x 640 x 137, 8 x 8 ranks) transposed by the
+    per-piece pipeline on this GPU (compress, all-to-all and decompress of
+    successive pieces on three streams) against the same three kernels in
+    series: device time per transposition, and the pipeline's result checked
+    byte for byte against the serial one."""
+    import torch
+    res = {}
+    for rate in RATES:
+        nb = plan.buffer_bytes(rate)
+        send = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        recv = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        out = torch.empty_like(xd)
+
+        def serial():
+            z.zfpx_pack_compress(plan, rate, xd, send)
+            z.zfpx_permute(plan, rate, send, recv)
+            z.zfpx_decompress_unpack(plan, rate, recv, out)
+        ser = _events_ms(serial, reps, warmup=3)
+        ref = (recv.clone(), out.clone())
+        row = {"serial_ms": round(ser, 4)}
+        for k in PIECES[1:]:
+            pl = z.Pipeline(plan, rate, k)
+            send.zero_()
+            recv.zero_()
+            out.fill_(float("nan"))
+            ms = _events_ms(lambda: pl.run(xd, send, recv, out), reps, warmup=3)
+            torch.cuda.synchronize()
+            same = bool(torch.equal(recv, ref[0]) and torch.equal(out.view(torch.int32), ref[1].view(torch.int32)))
+            row["pieces_%d" % pl.pieces] = {"ms": round(ms, 4), "vs_serial": round(ser / ms, 3), "identical": same}
+            pl.close()
+        res["rate_%d" % rate] = row
+        del send, recv, out
+    return {"workload": "1280x640x137 f32, 8x8 ranks, z->lambda: pack+compress, all-to-all, decompress+unpack; "
+                        "pieces by destination peer on three streams vs serial",
+            "per_rate": res}
 
 
 def extra_sht_step(net, sht):
@@ -1036,6 +1095,10 @@ def run_gpu(args):
             extras["network_model"] = extra_network_model(z, xd, reps)
         except Exception as e:
             extras["network_model"] = {"error": repr(e)}
+        try:
+            extras["pipeline"] = extra_pipeline(z, xd, plan, reps)
+        except Exception as e:
+            extras["pipeline"] = {"error": repr(e)}
         try:
             extras["blocks_2d"] = extra_blocks_2d(z, xd, reps, peak)
         except Exception as e:

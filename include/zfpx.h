@@ -433,6 +433,32 @@ ZFPX_API int zfpx_capture_end(zfpx_graph *out, void *stream);
 #define ZFPX_NOALLOC_SCRATCH_BYTES (64u << 20)
 ZFPX_API int zfpx_transpose_noalloc(zfpx_plan plan, int rate, const float *d_src, float *d_dst, void *stream);
 
+/* ---- a transposition pipelined per piece (Sec. III-E, Sec. V-B) ----------
+ * The paper's time model adds compression, exchange and decompression in
+ * series and notes that pipelining them per block would do better.  A
+ * pipeline splits the plan's messages into `pieces` pieces by destination
+ * peer (piece k: peers d of the communicator with floor(d K / P) = k, K =
+ * min(pieces, P)), and zfpx_pipeline_run compresses piece k+1 (stream A)
+ * while piece k is moved to the receive layout (stream B, the device-local
+ * all-to-all) and piece k-1 is decompressed and unpacked (stream C), ordered
+ * by events.  The stream `stream` waits for the last piece; the streams of the
+ * pipeline wait for what `stream` had enqueued before the call.  Results are
+ * byte for byte those of zfpx_pack_compress (send layout), zfpx_permute and
+ * zfpx_decompress_unpack: d_send and d_recv (buf_bytes each, >=
+ * zfpx_buffer_bytes) end up as they would, and d_dst gets the same values.
+ * Creation allocates the pieces' device tables, three streams and events
+ * (run allocates nothing); one pipeline's runs must not overlap on the GPU
+ * (they share its streams and events; runs in order on one stream do not).
+ * The plan must outlive the pipeline.  Errors: ZFPX_EINVAL, ZFPX_ESIZE,
+ * ZFPX_ECUDA, ZFPX_ENOMEM. */
+typedef struct zfpx_pipeline_s *zfpx_pipeline;
+ZFPX_API int zfpx_pipeline_create(zfpx_pipeline *out, zfpx_plan plan, int rate, int pieces);
+/* Pieces actually used (K above). */
+ZFPX_API int zfpx_pipeline_pieces(zfpx_pipeline pipeline);
+ZFPX_API int zfpx_pipeline_run(zfpx_pipeline pipeline, const float *d_src, uint8_t *d_send, uint8_t *d_recv,
+                               size_t buf_bytes, float *d_dst, void *stream);
+ZFPX_API void zfpx_pipeline_destroy(zfpx_pipeline pipeline);
+
 /* ---- the transposition pair as one CUDA graph (Sec. II-B; Sec. VI) -------
  * Records, on a private stream, pack+compress -> all-to-all -> decompress+
  * unpack with `first` (src field -> d_mid) and then with `second` (d_mid ->

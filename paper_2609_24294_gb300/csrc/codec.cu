@@ -507,6 +507,10 @@ bool vec_ok(const void *ptr, const int64_t s[3], const zfpx_plan_s *p, int which
     return true;
 }
 
+}  // namespace
+
+bool codec_vec_ok(const void *ptr, const int64_t s[3], const zfpx_plan_s *p) { return vec_ok(ptr, s, p, 0); }
+
 int launch_encode(int dims, int rate, const float *src, uint8_t *out, const LaunchGeom &g, int layout, int vec,
                   cudaStream_t st)
 {
@@ -550,8 +554,6 @@ int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const Launc
     count_launch();
     return check_launch();
 }
-
-}  // namespace
 
 int units_per_warp(int encode, int rate)
 {

@@ -232,6 +232,14 @@ int run_quads(zfpx_plan p, int mode, int rate, const void *in, void *out, int la
 }
 
 }  // namespace
+
+int launch_permute(const uint8_t *send, uint8_t *recv, const LaunchGeom &g, int rate, int dims, cudaStream_t st)
+{
+    if (g.nunits == 0) return ZFPX_OK;
+    permute_kernel<<<grid_for(permute_kernel, g.nunits), kThreads, 0, st>>>(send, recv, g, rate, dims);
+    count_launch();
+    return check_launch();
+}
 }  // namespace zfpx
 
 using namespace zfpx;
@@ -278,13 +286,9 @@ int zfpx_permute(zfpx_plan p, int rate, const void *d_send, void *d_recv, size_t
     DevTable *t = nullptr;
     int rc = get_table(p, rate, UNIT_CHUNK16, &t);
     if (rc) return rc;
-    if (t->nunits == 0) return ZFPX_OK;
     LaunchGeom g{};
     g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
-    cudaStream_t st = (cudaStream_t)stream;
-    permute_kernel<<<grid_for(permute_kernel, g.nunits), kThreads, 0, st>>>(a, (uint8_t *)d_recv, g, rate, p->dims);
-    count_launch();
-    return check_launch();
+    return launch_permute(a, (uint8_t *)d_recv, g, rate, p->dims, (cudaStream_t)stream);
 }
 
 }  // extern "C"

@@ -114,23 +114,19 @@ static void split(int64_t extent, int parts, int mode, std::vector<int64_t> &sta
     }
 }
 
-int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out)
+int64_t host_table(const zfpx_plan_s *p, int rate, UnitKind kind, const std::vector<int> &subset,
+                   std::vector<MsgDev> &h)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return ZFPX_ECUDA;
-    const long long key = ((long long)dev << 32) | ((long long)(rate + 1024) << 4) | (long long)kind;
-    std::lock_guard<std::mutex> g(p->mu);
-    auto it = p->tables.find(key);
-    if (it != p->tables.end()) { *out = &it->second; return ZFPX_OK; }
-
     const size_t M = p->msgs.size();
-    std::vector<MsgDev> h(M);
     const std::vector<int64_t> so = layout_offsets(p, rate, ZFPX_LAYOUT_SEND, nullptr);
     const std::vector<int64_t> ro = layout_offsets(p, rate, ZFPX_LAYOUT_RECV, nullptr);
+    const size_t n = subset.empty() ? M : subset.size();
+    h.assign(n, MsgDev{});
     int64_t units = 0;
-    for (size_t i = 0; i < M; i++) {
+    for (size_t j = 0; j < n; j++) {
+        const size_t i = subset.empty() ? j : (size_t)subset[j];
         const HostMsg &m = p->msgs[i];
-        MsgDev &d = h[i];
+        MsgDev &d = h[j];
         int64_t b[3];
         block_counts(p->dims, m, b);
         d.src_off = m.x0 * p->ss[0] + m.y0 * p->ss[1] + m.z0 * p->ss[2];
@@ -145,16 +141,37 @@ int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out)
         else if (kind == UNIT_QUADS) units += ceil4(m.nx) * m.ny * m.nz;
         else units += (message_bytes(p, m, rate) + 15) / 16;
     }
-    DevTable t;
-    t.nunits = units;
-    if (M > 0) {
-        const size_t tb = (M * sizeof(MsgDev) + 255) / 256 * 256;
-        if (cudaMalloc((void **)&t.d_msgs, tb) != cudaSuccess) return ZFPX_ENOMEM;
-        if (cudaMemcpy(t.d_msgs, h.data(), M * sizeof(MsgDev), cudaMemcpyHostToDevice) != cudaSuccess) {
-            cudaFree(t.d_msgs);
-            return ZFPX_ECUDA;
-        }
+    return units;
+}
+
+int upload_table(const std::vector<MsgDev> &h, int64_t units, DevTable *t)
+{
+    t->d_msgs = nullptr;
+    t->nunits = units;
+    if (h.empty()) return ZFPX_OK;
+    const size_t tb = (h.size() * sizeof(MsgDev) + 255) / 256 * 256;
+    if (cudaMalloc((void **)&t->d_msgs, tb) != cudaSuccess) return ZFPX_ENOMEM;
+    if (cudaMemcpy(t->d_msgs, h.data(), h.size() * sizeof(MsgDev), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(t->d_msgs);
+        t->d_msgs = nullptr;
+        return ZFPX_ECUDA;
     }
+    return ZFPX_OK;
+}
+
+int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ZFPX_ECUDA;
+    const long long key = ((long long)dev << 32) | ((long long)(rate + 1024) << 4) | (long long)kind;
+    std::lock_guard<std::mutex> g(p->mu);
+    auto it = p->tables.find(key);
+    if (it != p->tables.end()) { *out = &it->second; return ZFPX_OK; }
+    std::vector<MsgDev> h;
+    const int64_t units = host_table(p, rate, kind, {}, h);
+    DevTable t;
+    const int rc = upload_table(h, units, &t);
+    if (rc) return rc;
     auto res = p->tables.emplace(key, t);
     *out = &res.first->second;
     return ZFPX_OK;

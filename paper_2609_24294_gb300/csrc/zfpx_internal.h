@@ -67,6 +67,23 @@ int64_t message_bytes(const zfpx_plan_s *p, const HostMsg &m, int rate);
 int64_t buffer_bytes(const zfpx_plan_s *p, int rate);
 // Fetches (building on first use) the device table; returns ZFPX_OK or an error.
 int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out);
+// Host copy of the table of the messages `subset` (send-order indices; empty
+// = every message), work units numbered from 0 within it; returns the units.
+// Offsets stay those of the whole plan's layouts.
+int64_t host_table(const zfpx_plan_s *p, int rate, UnitKind kind, const std::vector<int> &subset,
+                   std::vector<MsgDev> &h);
+// Uploads a host table into a new device allocation (t->d_msgs, freed by the owner).
+int upload_table(const std::vector<MsgDev> &h, int64_t units, DevTable *t);
+
+// Kernel launchers over a table (geometry g: table, units, view strides).
+// vec: every row the kernel touches starts on 16 bytes.
+int launch_encode(int dims, int rate, const float *src, uint8_t *out, const LaunchGeom &g, int layout, int vec,
+                  cudaStream_t st);
+int launch_decode(int dims, int rate, const uint8_t *in, float *dst, const LaunchGeom &g, int layout, int vec,
+                  cudaStream_t st);
+int launch_permute(const uint8_t *send, uint8_t *recv, const LaunchGeom &g, int rate, int dims, cudaStream_t st);
+// vec test of the codec kernels for a pointer and view strides over the plan's messages.
+bool codec_vec_ok(const void *ptr, const int64_t s[3], const zfpx_plan_s *p);
 
 int num_sms();
 // Resident CTAs per SM of `fn` at `threads` threads (cached per kernel).

@@ -136,6 +136,21 @@ def pipelined_total(t_pack: float, t_comm_k: float, t_unpack: float, k: int) -> 
     return sum(stages) + (k - 1) * max(stages)
 
 
+def flowshop(stage_times) -> float:
+    """Makespan of pieces flowing in order through three stages (pack-side codec,
+    exchange, unpack-side codec), each stage serving one piece at a time:
+    stage_times[i] = (pack s, exchange s, unpack s) of piece i.  A piece enters a
+    stage when the stage has finished the previous piece and the piece has left
+    the previous stage."""
+    done = [0.0, 0.0, 0.0]
+    for t in stage_times:
+        prev = 0.0
+        for s in range(3):
+            done[s] = max(done[s], prev) + t[s]
+            prev = done[s]
+    return done[2]
+
+
 def message_sizes(N_list=TABLE1_N, grid=TABLE1_GRID, split=None):
     """Per-pair message bytes of the row transposition for each strategy, from
     the library's plan (the Table 1 split by default: every extent divided by p
@@ -154,13 +169,20 @@ def message_sizes(N_list=TABLE1_N, grid=TABLE1_GRID, split=None):
     return out
 
 
-def model(N_list, sizes, per_rank, topo: Dragonfly = Dragonfly(), pieces=(1, 2, 4, 8, 16, 32)):
+def model(N_list, sizes, per_rank, topo: Dragonfly = Dragonfly(), pieces=(1, 2, 4, 8, 16, 32),
+          per_rank_pieces=None):
     """Time breakdown and speedups per node count.
 
     sizes[N][strategy]: per-pair message bytes.  per_rank[N][strategy] =
     (pack-side seconds, unpack-side seconds) for one rank's pencil.  Returns,
     per N and strategy: the three serial terms, the serial total, the best
     pipelined total and its piece count, and the speedups over float32 of both.
+
+    per_rank_pieces[N][strategy][k], when given, is the measured list of k
+    (pack s, unpack s) of the rank's pencil cut into k pieces; the pipelined
+    total is then the flow shop of those measured pieces (each piece's exchange
+    time the k-piece exchange over k), over the k it holds, in place of the
+    equal-piece formula.
     """
     res = {}
     for N in N_list:
@@ -170,8 +192,13 @@ def model(N_list, sizes, per_rank, topo: Dragonfly = Dragonfly(), pieces=(1, 2, 
             tc = exchange_time(N, sizes[N][s], topo)
             ser = serial_total(tp, tc, tu)
             best_k, best = 1, ser
-            for k in pieces:
-                t = pipelined_total(tp, exchange_time(N, sizes[N][s], topo, k), tu, k)
+            measured = (per_rank_pieces or {}).get(N, {}).get(s)
+            for k in (sorted(measured) if measured else pieces):
+                tck = exchange_time(N, sizes[N][s], topo, k)
+                if measured:
+                    t = flowshop([(a, tck / k, b) for a, b in measured[k]])
+                else:
+                    t = pipelined_total(tp, tck, tu, k)
                 if t < best:
                     best_k, best = k, t
             row[s] = {"message_bytes": sizes[N][s], "pack_s": tp, "comm_s": tc, "unpack_s": tu,

@@ -83,6 +83,10 @@ def lib():
                                    ctypes.c_int),
         "zfpx_graph_launch": ([vp, vp], ctypes.c_int),
         "zfpx_transpose_noalloc": ([vp, ctypes.c_int, vp, vp, vp], ctypes.c_int),
+        "zfpx_pipeline_create": ([ctypes.POINTER(vp), vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
+        "zfpx_pipeline_pieces": ([vp], ctypes.c_int),
+        "zfpx_pipeline_run": ([vp, vp, vp, vp, sz, vp, vp], ctypes.c_int),
+        "zfpx_pipeline_destroy": ([vp], None),
         "zfpx_set_units_per_warp": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_get_units_per_warp": ([ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_capture_begin": ([vp], ctypes.c_int),
@@ -652,6 +656,37 @@ class Batch:
 
 
 NOALLOC_SCRATCH_BYTES = 64 << 20
+
+
+class Pipeline:
+    """A transposition pipelined per piece (zfpx_pipeline_create): compression,
+    the device-local all-to-all and decompression of successive pieces of the
+    plan's messages overlap on three streams."""
+
+    def __init__(self, plan, rate, pieces):
+        h = ctypes.c_void_p()
+        _check(lib().zfpx_pipeline_create(ctypes.byref(h), plan.handle, int(rate), int(pieces)),
+               "zfpx_pipeline_create")
+        self._h, self.plan, self.rate = h, plan, int(rate)
+        self.pieces = int(lib().zfpx_pipeline_pieces(h))
+
+    def run(self, src, send, recv, dst, stream=None):
+        self.plan._check_field(src, self.plan.src_strides, "src")
+        self.plan._check_field(dst, self.plan.dst_strides, "dst")
+        nb = min(_nbytes(send), _nbytes(recv))
+        _check(lib().zfpx_pipeline_run(self._h, _dev(src, "src"), _dev(send, "send"), _dev(recv, "recv"), nb,
+                                       _dev(dst, "dst"), _stream(stream)), "zfpx_pipeline_run")
+
+    def close(self):
+        if self._h:
+            lib().zfpx_pipeline_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def zfpx_set_units_per_warp(encode, rate, upw):

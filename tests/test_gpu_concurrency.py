@@ -63,7 +63,7 @@ def test_units_per_warp_does_not_change_results(z):
         for rate in (8, 16):
             nb = plan.buffer_bytes(rate)
             got = []
-            for upw in (0, 1, 3, 64, 100000):
+            for upw in (0, 1, 3, 64, 4096):
                 z.zfpx_set_units_per_warp(True, rate, upw)
                 z.zfpx_set_units_per_warp(False, rate, upw)
                 assert z.zfpx_get_units_per_warp(True, rate) == (upw or z.zfpx_get_units_per_warp(True, rate))
@@ -82,3 +82,5 @@ def test_units_per_warp_does_not_change_results(z):
             z.zfpx_set_units_per_warp(False, rate, 0)
     with pytest.raises(z.ZfpxError):
         z.zfpx_set_units_per_warp(True, 12, 1)
+    with pytest.raises(z.ZfpxError):
+        z.zfpx_set_units_per_warp(True, 8, 4097)

@@ -90,6 +90,40 @@ def test_pipeline_bounds():
         assert nm.pipelined_total(tp, tc, tu, 10 ** 7) == pytest.approx(max(tp, tc, tu), rel=1e-5)
 
 
+def test_flowshop_equal_pieces_is_the_closed_form():
+    # k equal pieces through three stages: the first piece passes every stage, the
+    # rest follow one slowest-stage time apart
+    for tp, tc, tu in ((1.0, 2.0, 0.5), (3.0, 0.2, 3.0), (0.4, 0.4, 0.4)):
+        for k in (1, 2, 5, 8):
+            pieces = [(tp / k, tc / k, tu / k)] * k
+            assert nm.flowshop(pieces) == pytest.approx(nm.pipelined_total(tp, tc, tu, k), rel=1e-12)
+
+
+def test_flowshop_by_hand():
+    # pieces (pack, exchange, unpack): (1,3,1), (2,1,2), (1,1,1)
+    # stage ends: piece 0: 1, 4, 5; piece 1: 3, 5, 7; piece 2: 4, 6, 8
+    assert nm.flowshop([(1, 3, 1), (2, 1, 2), (1, 1, 1)]) == pytest.approx(8.0)
+    assert nm.flowshop([(2.0, 0.0, 0.0)]) == 2.0 and nm.flowshop([]) == 0.0
+
+
+def test_model_with_measured_pieces(sizes):
+    per = {N: {s: (40e-6, 40e-6) for s in nm.STRATEGIES} for N in nm.TABLE1_N}
+    # pieces as fast as an equal split: the same result as the formula; pieces that
+    # cost more than their share (launch overheads) make pipelining worth less
+    even = {N: {s: {k: [(40e-6 / k, 40e-6 / k)] * k for k in (1, 2, 4)} for s in nm.STRATEGIES}
+            for N in nm.TABLE1_N}
+    slow = {N: {s: {k: [(40e-6 / k + 10e-6, 40e-6 / k + 10e-6)] * k for k in (1, 2, 4)} for s in nm.STRATEGIES}
+            for N in nm.TABLE1_N}
+    a = nm.model(nm.TABLE1_N, sizes, per, pieces=(1, 2, 4))
+    b = nm.model(nm.TABLE1_N, sizes, per, per_rank_pieces=even)
+    c = nm.model(nm.TABLE1_N, sizes, per, per_rank_pieces=slow)
+    for N in nm.TABLE1_N:
+        for s in nm.STRATEGIES:
+            assert b[N][s]["pipelined_s"] == pytest.approx(a[N][s]["pipelined_s"], rel=1e-12)
+            assert c[N][s]["pipelined_s"] >= b[N][s]["pipelined_s"] - 1e-15
+            assert c[N][s]["pipelined_s"] <= c[N][s]["serial_s"] + 1e-15
+
+
 def test_speedups_reduce_to_size_ratios_without_overheads(sizes):
     zero = {N: {s: (0.0, 0.0) for s in nm.STRATEGIES} for N in nm.TABLE1_N}
     res = nm.model(nm.TABLE1_N, sizes, zero, nm.Dragonfly(hop_s=0.0), pieces=(1,))
