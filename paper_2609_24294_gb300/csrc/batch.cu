@@ -29,6 +29,7 @@
 #include "zfpx_internal.h"
 #include "zfpx_block.cuh"
 #include "zfpx_smem.cuh"
+#include "zfpx_enc3.cuh"
 
 namespace zfpx {
 namespace {
@@ -206,26 +207,24 @@ __device__ __forceinline__ void scatter_quad(const FieldDevB &f, const GridDev &
     }
 }
 
+// Every lane of the warp calls it (the encoder's loops are warp-wide); the
+// tile of `v` is zero on entry and left zero.
 template <int RATE>
 __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                           int nact, int lane, uint64_t *wsm, uint64_t *wpl, uint8_t *out)
+                                           int nact, int lane, const enc3::View &v, uint8_t *out)
 {
-    if (lane < nact) {
-        const int64_t bg = b0 + lane + f.b0;
+    const bool valid = lane < nact;
+    float x[64];
+    {
+        // lanes past the unit's last block load that block and code nothing
+        const int64_t bg = b0 + (valid ? lane : nact - 1) + f.b0;
         const int q = upper_index(g.qpre, g.nq + 1, bg);
         const int bxi = (int)(bg - __ldg(g.qpre + q));
-        float x[64];
         gather_quad(f, g, q, bxi, it.z0, it.nz, x);
-        SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
-        SmemPlanes pl{wpl, lane};
-        encode_block3<RATE>(x, wr, pl);
     }
+    enc3::encode<RATE>(x, valid, v, lane);
     __syncwarp();
-    uint64_t *dst = reinterpret_cast<uint64_t *>(out + it.out_off) + b0 * RATE;
-    for (int idx = lane; idx < nact * RATE; idx += 32) {
-        const int l = idx / RATE, w = idx % RATE;
-        dst[idx] = wsm[w * 32 + (l ^ w)];
-    }
+    enc3::store_stream<RATE>(v, lane, valid, out + it.out_off + (b0 + lane) * RATE * 8);
     __syncwarp();
 }
 
@@ -257,17 +256,19 @@ template <int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
 batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
 {
-    __shared__ uint64_t sout[WARPS][(16 + 2) * 32];
-    __shared__ uint64_t splanes[WARPS][32 * 32];
+    __shared__ enc3::Shared<16> sh[WARPS];             // rate-16 sized, shared by both rates
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const enc3::View v = sh[wid].view();
+    enc3::clear(v, lane, enc3::kWords<16>);
+    __syncwarp();
     for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
         const ItemDevB it = bg.items[ii];
         const FieldDevB f = bg.fields[it.field];
         const int64_t b0 = (c - it.unit0) * 32;
         const int nact = (int)min((int64_t)32, it.nblocks - b0);
         if (G.dims == 3) {
-            if (G.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
-            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, sout[wid], splanes[wid], out);
+            if (G.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, v, out);
+            else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, v, out);
         } else {
             if (G.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
             else enc1_chunk<16>(f, bg.grid, it, b0, nact, lane, out);

@@ -26,6 +26,7 @@
 #include "zfpx_internal.h"
 #include "zfpx_block.cuh"
 #include "zfpx_smem.cuh"
+#include "zfpx_enc3.cuh"
 
 namespace zfpx {
 namespace {
@@ -34,13 +35,16 @@ using namespace blk;
 
 constexpr int kWarps = 4;
 constexpr int kThreads = 32 * kWarps;
-// Launch shapes of the 3-D kernels, chosen by measurement on GB300: 4 warps
-// per CTA, except the rate-16 decoder, whose 3-warp CTAs fit six to an SM
-// (two zero rows after its stream tile make the shared memory fit); the
-// rate-8 decoder is compiled for five resident CTAs, which its shared memory
-// allows and capping its registers to match pays for.
+// Launch shapes of the 3-D kernels, chosen by measurement on GB300: encoder
+// CTAs of 2 warps (rate 8) and 3 warps (rate 16), whose shared memory packs
+// the SMs best; decoder CTAs of 4 warps, except the rate-16 decoder, whose
+// 3-warp CTAs fit six to an SM (two zero rows after its stream tile make the
+// shared memory fit); the rate-8 decoder is compiled for five resident CTAs,
+// which its shared memory allows and capping its registers to match pays for.
 template <int RATE>
-constexpr int kEnc3Warps = 4;
+constexpr int kEnc3Warps = RATE == 16 ? 3 : 2;
+template <int RATE>
+constexpr int kEnc3MinBlocks = RATE == 16 ? 5 : 8;     // what the shared memory allows
 template <int RATE>
 constexpr int kDec3Warps = RATE == 16 ? 3 : 4;
 template <int RATE>
@@ -97,16 +101,16 @@ struct UnitRange {
 // instantiation reads and writes the rows of x-complete blocks as four scalar
 // accesses each, unrolled, keeping the vector kernel's code as it is.
 template <int RATE, bool VEC>
-__global__ void __launch_bounds__(32 * kEnc3Warps<RATE>)
+__global__ void __launch_bounds__(32 * kEnc3Warps<RATE>, kEnc3MinBlocks<RATE>)
 encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout)
 {
-    __shared__ uint64_t smem[kEnc3Warps<RATE>][(RATE + 2) * 32];
-    __shared__ uint64_t splanes[kEnc3Warps<RATE>][32 * 32];
+    __shared__ enc3::Shared<RATE> sh[kEnc3Warps<RATE>];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t *wsm = smem[wid];
-    SmemPlanes pl{splanes[wid], lane};
+    const enc3::View v = sh[wid].view();
     const UnitRange ur(g, kEnc3Warps<RATE>, wid);
     if (ur.c >= ur.c1) return;
+    enc3::clear(v, lane, enc3::kWords<RATE>);
+    __syncwarp();
     MsgWalk walk;
     walk.start(g.msgs, g.nmsg, ur.c);
     for (int64_t c = ur.c; c < ur.c1; c++) {
@@ -117,13 +121,15 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         const int nx = m.nx, ny = m.ny, nz = m.nz, bxn = m.bx, byn = m.by;
         const int64_t b0 = (c - unit0) * 32;
         const int nact = (int)min((int64_t)32, nblocks - b0);
-        if (lane < nact) {
-            const int b = (int)b0 + lane;
+        const bool valid = lane < nact;
+        float x[64];
+        {
+            // lanes past the unit's last block load that block and code nothing
+            const int b = (int)b0 + (valid ? lane : nact - 1);
             const int bxi = b % bxn, t = b / bxn;
             const int byi = t % byn, bzi = t / byn;
             const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
             const float *base = src + src_off;
-            float x[64];
             if (VEC && x0 + 4 <= nx) {
                 // the common case: sixteen 16-byte row loads (rows past the
                 // end of the box repeat its last row)
@@ -163,15 +169,10 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
 #pragma unroll
                 for (int r = 0; r < 64; r++) x[r] = t[r];
             }
-            SmemWriter<RATE> wr{wsm, 0ull, 0, 0, lane};
-            encode_block3<RATE>(x, wr, pl);
         }
+        enc3::encode<RATE>(x, valid, v, lane);
         __syncwarp();
-        uint64_t *dst = reinterpret_cast<uint64_t *>(out + boff) + b0 * RATE;
-        for (int idx = lane; idx < nact * RATE; idx += 32) {
-            const int l = idx / RATE, w = idx % RATE;
-            dst[idx] = wsm[w * 32 + (l ^ w)];
-        }
+        enc3::store_stream<RATE>(v, lane, valid, out + boff + (b0 + lane) * RATE * 8);
         __syncwarp();
     }
 }
