@@ -1220,7 +1220,9 @@ def run_profile_case(args):
     1-D blocks, rates 8 and 16, pack+compress and decompress+unpack per repetition.
     `sht`: the benchmark field's longitude FFT (1280 -> 640 wavenumbers) and the T639
     Legendre transform of its wavenumber fields, one of each per repetition.
-    Prints one line; times nothing."""
+    `f64`: the benchmark field widened to float64 (898 MB) as one array, the
+    float64 3-D codec at rates 8 and 16, one encode and one decode per rate and
+    repetition.  Prints one line; times nothing."""
     import torch
     from paper_2609_24294_gb300 import build, zfpx as z
     build.build()
@@ -1240,6 +1242,21 @@ def run_profile_case(args):
                 plan.close()
         torch.cuda.synchronize()
         print(json.dumps({"profile_case": args.profile_case, "values": xd.numel(), "launches": n}))
+        return 0
+    if args.profile_case == "f64":
+        x64 = torch.from_numpy(make_field()).cuda().double()
+        n = tuple(reversed(x64.shape))
+        out = torch.empty_like(x64)
+        launches = 0
+        for _ in range(max(1, args.steps)):
+            for r in RATES:
+                st = torch.empty(z.zfpx_stream_bytes_f64(r, n), dtype=torch.uint8, device="cuda")
+                z.zfpx_encode_f64(r, x64, st)
+                z.zfpx_decode_f64(r, st, out)
+                launches += 2
+                del st
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": args.profile_case, "values": x64.numel(), "launches": launches}))
         return 0
     if args.profile_case == "sht":
         xd = torch.from_numpy(make_field()).cuda()
@@ -1288,7 +1305,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--detail-file", default="bench_detail.json",
                     help="where the full record (comparators, errors, extras) is written")
-    ap.add_argument("--profile-case", choices=["batch", "blocks12", "sht"], default=None,
+    ap.add_argument("--profile-case", choices=["batch", "blocks12", "sht", "f64"], default=None,
                     help="run a reduced workload for an ncu capture and exit")
     args = ap.parse_args()
     if args.profile_case:
