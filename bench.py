@@ -115,7 +115,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-CODEC_SOURCES = ("codec.cu", "zfpx_block.cuh", "zfpx_internal.h", "zfpx_smem.cuh")
+CODEC_SOURCES = ("codec.cu", "zfpx_block.cuh", "zfpx_enc3.cuh", "zfpx_internal.h", "zfpx_smem.cuh")
 
 
 def kernel_source_sha():
