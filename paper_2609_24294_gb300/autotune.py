@@ -7,9 +7,13 @@ repetitions) and keeps the fastest.  Choices are cached in a JSON file keyed
 by the workload's signature, the GPU name and its SM count, so a workload is
 tuned once per machine type.
 
-Candidates: warps per CTA (4 or 8: the per-warp shared-memory tiles and the
-scheduling granularity) x CTAs per SM (1..as many as fit: fewer CTAs leave
-more L1 per block, more CTAs hide latency).
+Candidates:
+* batched ragged kernels: warps per CTA (4 or 8: the per-warp shared-memory
+  tiles and the scheduling granularity) x CTAs per SM (1..as many as fit: fewer
+  CTAs leave more L1 per block, more CTAs hide latency);
+* plan codec kernels (3-D blocks): consecutive 32-block units per warp (the
+  blocks-per-warp knob; each CTA of the grid codes units-per-warp x warps
+  units, so it also sets the grid size), per direction and rate.
 """
 import hashlib
 import json
@@ -21,6 +25,7 @@ import torch
 CACHE = os.environ.get("ZFPX_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "zfpx", "tune.json"))
 
 BATCH_CANDIDATES = [(4, 0), (4, 3), (4, 2), (8, 0), (8, 1)]
+UPW_CANDIDATES = (1, 2, 3, 4, 8)
 
 
 def _device_key():
@@ -90,3 +95,37 @@ def tune_batch(batch, specs, out, candidates=None, reps=3, use_cache=True):
         cache[key] = {"choice": [w, c], "timings": timings}
         _store(cache)
     return (w, c), timings
+
+
+def plan_signature(plan, rate):
+    return "codec:%s/%s/%s/%d,%d,%d,%d/r%d" % (tuple(plan.n), tuple(plan.src_strides), tuple(plan.dst_strides),
+                                              plan.pr, plan.pc, plan.transposition, plan.dims, rate)
+
+
+def tune_codec(plan, rate, src, buf, dst, candidates=None, reps=3, use_cache=True):
+    """Picks units per warp for the plan's pack+compress and decompress+unpack
+    at `rate` (3-D blocks) and sets them; returns ({"encode": upw, "decode":
+    upw}, {direction: {upw: ms}})."""
+    from . import zfpx as z
+    key = plan_signature(plan, rate) + "@" + _device_key()
+    cache = _load() if use_cache else {}
+    if use_cache and key in cache:
+        ch = cache[key]["choice"]
+        z.zfpx_set_units_per_warp(True, rate, ch["encode"])
+        z.zfpx_set_units_per_warp(False, rate, ch["decode"])
+        return ch, cache[key].get("timings", {})
+    calls = {"encode": lambda: z.zfpx_pack_compress(plan, rate, src, buf),
+             "decode": lambda: z.zfpx_decompress_unpack(plan, rate, buf, dst, layout=z.LAYOUT_SEND)}
+    choice, timings = {}, {}
+    for d, fn in calls.items():
+        timings[d] = {}
+        for u in (candidates or UPW_CANDIDATES):
+            z.zfpx_set_units_per_warp(d == "encode", rate, u)
+            timings[d][str(u)] = time_call(fn, reps=reps)
+        best = min(timings[d], key=timings[d].get)
+        choice[d] = int(best)
+        z.zfpx_set_units_per_warp(d == "encode", rate, choice[d])
+    if use_cache:
+        cache[key] = {"choice": choice, "timings": timings}
+        _store(cache)
+    return choice, timings

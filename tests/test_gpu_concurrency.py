@@ -84,3 +84,27 @@ def test_units_per_warp_does_not_change_results(z):
         z.zfpx_set_units_per_warp(True, 12, 1)
     with pytest.raises(z.ZfpxError):
         z.zfpx_set_units_per_warp(True, 8, 4097)
+
+
+def test_autotuner_picks_a_candidate_and_results_stay(z):
+    from paper_2609_24294_gb300 import autotune
+    x = _field((37, 96, 200), 14, 2.0)
+    plan = z.Plan.for_fields(x, 2, 2, 0, 3)
+    try:
+        for rate in (8, 16):
+            nb = plan.buffer_bytes(rate)
+            b0 = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+            z.zfpx_pack_compress(plan, rate, x, b0)
+            b, v = torch.zeros_like(b0), torch.empty_like(x)
+            choice, timings = autotune.tune_codec(plan, rate, x, b, v, candidates=(1, 2, 5), reps=1, use_cache=False)
+            assert choice["encode"] in (1, 2, 5) and choice["decode"] in (1, 2, 5)
+            assert set(timings) == {"encode", "decode"} and all(len(t) == 3 for t in timings.values())
+            assert z.zfpx_get_units_per_warp(True, rate) == choice["encode"]
+            b.zero_()
+            z.zfpx_pack_compress(plan, rate, x, b)
+            torch.cuda.synchronize()
+            assert torch.equal(b, b0)
+    finally:
+        for rate in (8, 16):
+            z.zfpx_set_units_per_warp(True, rate, 0)
+            z.zfpx_set_units_per_warp(False, rate, 0)
