@@ -564,9 +564,35 @@ def extra_float64(z, xd, reps, peak):
     return res
 
 
-# float32 FMA peak from the unit counts and the clock (152 SMs x 128 FP32 lanes x
-# 2 flops x 2.07 GHz maximum SM clock), for the SIMT kernels
-FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# dense TF32 tensor peak: the measured dense BF16 peak (MEASURED_PEAKS.json) times
+# the nominal TF32 / BF16 ratio of GB300 (1.1 / 2.25 PFLOP/s dense)
+TF32_OVER_BF16 = 1.1 / 2.25
+
+
+def tf32_peak_tflops():
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(d["bf16_tflops"]) * TF32_OVER_BF16, "measured bf16 x 1.1/2.25"
+    except Exception:
+        return 1900.0 * TF32_OVER_BF16, "fallback bf16 x 1.1/2.25"
+
+
+def legendre_mma_flops(nlat, T, nlev):
+    """Flops the tensor cores execute for the Legendre transform: every
+    128-row x nt-column tile of every (order, parity) block runs K rounded up
+    to 32 in 8-deep steps, three TF32 products per step (hi x hi, hi x lo,
+    lo x hi)."""
+    nh = nlat // 2
+    N = 2 * nlev
+    ntiles = (N + 255) // 256
+    nt = ((N + ntiles - 1) // ntiles + 15) // 16 * 16
+    kp = (nh + 31) // 32 * 32
+    tiles = 0
+    for m in range(T + 1):
+        for p in range(2):
+            cnt = (T - m - p) // 2 + 1 if T - m - p >= 0 else 0
+            tiles += (cnt + 127) // 128
+    return 3 * 2.0 * 128 * nt * kp * tiles * ntiles
 
 
 def extra_sht_fourier(z, xd, reps, peak):
@@ -595,9 +621,16 @@ def extra_sht_fourier(z, xd, reps, peak):
     tl = _events_ms(lambda: leg.forward(re, im, a_re, a_im), reps)
     nh = ny // 2
     flops = 2.0 * 2 * nz * nh * leg.ncoeffs                   # folded: nh multiply-adds per coefficient and part
+    leg.status()
+    tpk, tpk_kind = tf32_peak_tflops()
+    mma = legendre_mma_flops(ny, T, nz)
     res.update({"legendre_ms": tl, "legendre_TFLOPs": flops / (tl / 1e3) / 1e12,
-                "legendre_frac_of_fp32_simt_peak": flops / (tl / 1e3) / 1e12 / FP32_SIMT_TFLOPS,
-                "fp32_simt_peak_TFLOPs": FP32_SIMT_TFLOPS})
+                "legendre_tensor_TFLOPs": mma / (tl / 1e3) / 1e12,
+                "legendre_frac_of_tf32_peak": mma / (tl / 1e3) / 1e12 / tpk,
+                "tf32_peak_TFLOPs": tpk, "tf32_peak_kind": tpk_kind,
+                "legendre_note": "fold + tcgen05 kernel; TFLOPs = useful folded flops / time; tensor_TFLOPs = the "
+                                 "three-term TF32 products the tensor cores execute (tiles padded to 128 rows, "
+                                 "K to 32) / time"})
     exact = torch.complex(re.double(), im.double())
     enorm = float(exact.norm())
     a_exact = torch.complex(a_re.double(), a_im.double())

@@ -288,9 +288,14 @@ ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t 
  * zfpx_legendre_forward takes n[1] equal to the plan's nlat and 1 .. 2^20
  * levels, and needs caller-owned device scratch d_work (16-byte aligned) of
  * zfpx_legendre_workspace_bytes(plan, levels) bytes; calls that share d_work
- * must not overlap on the GPU.  Single precision throughout.
- * Errors: ZFPX_EINVAL (NULL, sizes, strides, alignment), ZFPX_ESIZE,
- * ZFPX_ECUDA. */
+ * must not overlap on the GPU.  Float32 in and out; the contraction runs on
+ * the tensor cores (TF32 operands split into high and low parts, three
+ * products per term, float32 accumulation), which keeps float32 accuracy.
+ * Errors: ZFPX_EINVAL (NULL, sizes, strides, alignment, another device),
+ * ZFPX_ESIZE, ZFPX_ECUDA.
+ * zfpx_legendre_status reads (synchronously) whether any earlier forward on
+ * the plan gave up on a bounded wait inside its kernel: ZFPX_OK, or
+ * ZFPX_ETIMEOUT (that call's coefficients are incomplete). */
 /* The Gauss-Legendre latitudes the transform expects: mu[i] = sin(latitude),
  * north to south, and the weights w[i] (sum 2), for n = 1 .. 32768 points, by
  * Newton's iteration on P_n in double precision (the nodes the plan uses).
@@ -303,6 +308,7 @@ ZFPX_API size_t zfpx_legendre_workspace_bytes(zfpx_legendre plan, int64_t levels
 ZFPX_API int zfpx_legendre_forward(zfpx_legendre plan, const float *d_re, const float *d_im, const int64_t n[3],
                                    const int64_t stride[3], float *d_are, float *d_aim, int64_t out_stride,
                                    void *d_work, size_t work_bytes, void *stream);
+ZFPX_API int zfpx_legendre_status(zfpx_legendre plan);
 
 /* The accuracy mode on a transposition plan (dims 3): every message's box is
  * coded as above, so messages vary in size and the exchange becomes an

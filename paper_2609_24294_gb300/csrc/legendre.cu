@@ -18,43 +18,65 @@
 // The plan holds the table w_j Pbar_l^m(mu_j), j < nlat/2, built on the host
 // in double precision (Newton iteration for the nodes, the three-term
 // recurrences for Pbar) and rounded once to float; values below the double
-// range near the poles for large m are 0.  A fold kernel writes S and A per
-// order (a transpose through shared memory, into the caller's workspace);
-// a tiled single-precision GEMM kernel (64 x 64 outputs per CTA, 16-deep
-// k steps through double-buffered shared memory, 8 x 4 per thread) forms the
-// products and scatters them into the triangular output.  Tensor cores are not used: the
-// transform needs float32 accuracy, which TF32 and BF16 do not give.
+// range near the poles for large m are 0.  Both operands are stored K-major
+// (the latitude index j contiguous): the table as rows l of each (m, p)
+// block, and the folded operand, which a fold kernel writes per call into the
+// caller's workspace, as rows (m, p, column).
+//
+// The products run on the tensor cores (tcgen05.mma, kind::tf32) with float32
+// accuracy from a three-term split: a = a_hi + a_lo with a_hi = a truncated
+// to TF32 (what the MMA reads of a float32 operand) and a_lo = a - a_hi rounded
+// to TF32, and a b = a_hi b_hi + a_hi b_lo + a_lo b_hi, accumulated in float32
+// in tensor memory; the dropped a_lo b_lo and the TF32 rounding of the lo
+// parts leave about 2^-21 of sum |a b| per product, far below the float32
+// dot-product bound the transform is held to.  A CTA of four warps computes a
+// 128-row x Nt-column tile of one (m, p) block: TMA loads 32-deep K slices of
+// both operands (128-byte swizzled, two stages in flight), the warps derive
+// the lo tiles in place, one thread issues the MMAs (three per 8-deep K step)
+// and commits them to an mbarrier, and after the last slice each warp reads
+// its 32 rows of the accumulator from tensor memory and scatters them into
+// the triangular output.  Every wait is bounded; a wait that runs out sets
+// the plan's status word and the CTA stops.
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include "zfpx_internal.h"
 
 struct LegItem {
     int32_t m, p, r0, nr;   // order, parity of l + m, first row (of that parity), rows in this tile
-    int32_t ldm;            // row length of this (m, p) table block: its row count rounded up to 4
-    int32_t pad;
-    int64_t aoff;           // float offset of the (m, p) table block ([nlat/2][ldm], latitude-major)
+    int64_t arow;           // first table row of this (m, p) block (rows of the K-major table tensor)
 };
 
 struct zfpx_legendre_s {
-    int nlat = 0, T = 0, nh = 0, device = 0;
-    float *d_table = nullptr;
+    int nlat = 0, T = 0, nh = 0, nhs = 0, device = 0;
+    int64_t table_rows = 0;
+    float *d_table = nullptr;   // K-major: [table_rows][nhs] floats, columns >= nh zero
     LegItem *d_items = nullptr;
+    int *d_status = nullptr;    // 0, or the code of a wait that ran out
     int nitems = 0;
+    CUtensorMap tmap_table;     // TMA view of the table: {nh, table_rows}, boxes {32, 128}
 };
 
 namespace zfpx {
 namespace {
 
-constexpr int kBM = 64, kBN = 64, kBK = 16;
+constexpr int kBM = 128;        // rows per CTA tile (the MMA's M)
+constexpr int kBK = 32;         // K per stage: one 128-byte swizzle row of float32
+constexpr int kStages = 2;
+constexpr int kThreads = 128;
+constexpr int kTmemCols = 256;
+constexpr long long kSpinLimit = 1ll << 26;   // about a second of polling
 
 struct LegGeom {
-    int nlat, nh, T, nlev;
-    int ldc;                 // columns of the folded operand per row (2 nlev rounded up to 4)
-    int nct;                 // column tiles
-    int64_t is1, is2;        // input strides: latitude, level (floats; longitude/wavenumber stride 1)
+    int nlat, nh, nhs, T, nlev;
+    int N;                   // columns: 2 nlev
+    int nt, ntiles;          // columns per tile (a multiple of 16, <= 256), tiles
+    int ncp;                 // column rows per (m, p) in the workspace: ntiles * nt
+    int64_t is1, is2;        // input strides: latitude, level (floats; wavenumber stride 1)
     int64_t os;              // output level stride (floats)
 };
 
@@ -63,135 +85,267 @@ __host__ __device__ __forceinline__ int64_t tri_offset(int m, int T)
     return (int64_t)m * (T + 1) - (int64_t)m * (m - 1) / 2;
 }
 
-// G[m][p][j][c], c = part * nlev + lev: S (p = 0) and A (p = 1) of part
-// `part` of F at level lev, latitude pair (j, nlat - 1 - j), order m.
-// Block (32, 8) over 32 orders x 32 levels of one (j, part).
+// G[((m * 2 + p) * ncp + c) * nhs + j], c = part * nlev + lev: S (p = 0) and A
+// (p = 1) of part `part` of F at level lev, latitude pair (j, nlat - 1 - j),
+// order m; columns j in [nh, nhs) are written as zeros.  Block (32, 8) over 32
+// orders x 32 latitudes of one (level, part).
 __global__ void __launch_bounds__(256) legendre_fold_kernel(const float *__restrict__ re, const float *__restrict__ im,
                                                             float *__restrict__ G, LegGeom g)
 {
     __shared__ float sS[32][33], sA[32][33];
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int m0 = blockIdx.x * 32, lev0 = blockIdx.y * 32;
-    const int j = blockIdx.z >> 1, part = blockIdx.z & 1;
-    const float *F = part ? im : re;
-    const int jn = g.nlat - 1 - j;
+    const int m0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int lev = blockIdx.z >> 1, part = blockIdx.z & 1;
+    const float *F = (part ? im : re) + lev * g.is2;
     for (int i = ty; i < 32; i += 8) {
-        const int lev = lev0 + i, m = m0 + tx;
+        const int j = j0 + i, m = m0 + tx;
         float a = 0.f, b = 0.f;
-        if (lev < g.nlev && m <= g.T) {
-            a = __ldg(F + lev * g.is2 + (int64_t)j * g.is1 + m);
-            b = __ldg(F + lev * g.is2 + (int64_t)jn * g.is1 + m);
+        if (j < g.nh && m <= g.T) {
+            a = __ldg(F + (int64_t)j * g.is1 + m);
+            b = __ldg(F + (int64_t)(g.nlat - 1 - j) * g.is1 + m);
         }
-        sS[i][tx] = a + b;
+        sS[i][tx] = a + b;                            // [j][m]
         sA[i][tx] = a - b;
     }
     __syncthreads();
+    const int c = part * g.nlev + lev;
     for (int i = ty; i < 32; i += 8) {
-        const int m = m0 + i, lev = lev0 + tx;
-        if (m <= g.T && lev < g.nlev) {
-            const int64_t row = ((int64_t)m * 2 * g.nh + j) * g.ldc + part * g.nlev + lev;
+        const int m = m0 + i, j = j0 + tx;
+        if (m <= g.T && j < g.nhs) {
+            const int64_t row = ((int64_t)m * 2 * g.ncp + c) * g.nhs + j;
             G[row] = sS[tx][i];
-            G[row + (int64_t)g.nh * g.ldc] = sA[tx][i];
+            G[row + (int64_t)g.ncp * g.nhs] = sA[tx][i];
         }
     }
 }
 
-// 64 x 64 outputs per CTA of 128 threads (2 x 2 warps of 32 x 32), each thread
-// 8 rows x 4 columns; 16-deep k
-// steps, the next step's tiles loaded into registers while the current one is
-// multiplied out of the other shared-memory buffer (one barrier per step).
-// A tiles come from the latitude-major table block ([j][row], rows of one
-// parity contiguous), B tiles from the folded operand ([j][column]): both are
-// float4 rows copied into shared memory as they are.
-constexpr int kGemmThreads = 128;
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__global__ void __launch_bounds__(kGemmThreads) legendre_gemm_kernel(const float *__restrict__ table,
-                                                                     const float *__restrict__ G,
-                                                                     const LegItem *__restrict__ items, LegGeom g,
-                                                                     float *__restrict__ are, float *__restrict__ aim)
+// tcgen05 shared-memory descriptor of a K-major, 128-byte-swizzled operand
+// tile starting at `saddr` (8-row groups 1024 bytes apart)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
 {
-    __shared__ __align__(16) float As[2][kBK][kBM];
-    __shared__ __align__(16) float Bs[2][kBK][kBN];
-    const int tid = threadIdx.x;
-    const LegItem it = items[blockIdx.x / g.nct];
-    const int c0 = (blockIdx.x % g.nct) * kBN;
-    const float *A = table + it.aoff;
-    const float *B = G + ((int64_t)it.m * 2 + it.p) * g.nh * g.ldc;
-    const int N = 2 * g.nlev;
-    // warp w holds rows 32 (w >> 1) .. + 31 and columns 32 (w & 1) .. + 31; lane
-    // (ly, lx) rows 8 ly .. + 7 and columns 4 lx .. + 3 of those.  A warp whose
-    // rows or columns all lie past the tile's edge skips the multiply-adds.
-    const int w = tid >> 5, lane = tid & 31;
-    const int r_base = 32 * (w >> 1) + 8 * (lane >> 3), c_base = 32 * (w & 1) + 4 * (lane & 7);
-    const bool active = 32 * (w >> 1) < it.nr && c0 + 32 * (w & 1) < N;
-    // loaders: two float4 of A and two of B per thread; element e = tid + 128 h
-    // covers k-row e / 16 and the four rows / columns 4 (e % 16) .. + 3
-    float4 ra[2], rb[2];
-    auto load = [&](int k0) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);           // start address / 16
+    d |= (uint64_t)1u << 16;                             // leading byte offset (not used by swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;                   // stride byte offset / 16
+    d |= (uint64_t)1u << 46;                             // descriptor version
+    d |= (uint64_t)2u << 61;                             // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (long long i = 0; i < kSpinLimit; i++) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 :: "r"(dst), "l"(map), "r"(x), "r"(y), "r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
+}
+
+// lo = round_to_tf32(a - trunc_to_tf32(a)) over n 16-byte chunks
+__device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nchunks, int tid)
+{
+    for (int i = tid; i < nchunks; i += kThreads) {
+        const float4 a = reinterpret_cast<const float4 *>(raw)[i];
+        float v[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int e = tid + kGemmThreads * h, kr = e >> 4, q4 = (e & 15) * 4;
-            const bool kin = k0 + kr < g.nh;
-            ra[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (kin && it.r0 + q4 < it.ldm)
-                ra[h] = __ldg(reinterpret_cast<const float4 *>(A + (int64_t)(k0 + kr) * it.ldm + it.r0 + q4));
-            rb[h] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int c = c0 + q4;
-            if (kin && c < N) {
-                rb[h] = __ldg(reinterpret_cast<const float4 *>(B + (int64_t)(k0 + kr) * g.ldc + c));
-                if (c + 1 >= N) rb[h].y = 0.f;
-                if (c + 2 >= N) rb[h].z = 0.f;
-                if (c + 3 >= N) rb[h].w = 0.f;
+        for (int q = 0; q < 4; q++) {
+            const float h = __uint_as_float(__float_as_uint(v[q]) & 0xffffe000u);
+            uint32_t t;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v[q] - h));
+            v[q] = __uint_as_float(t);
+        }
+        reinterpret_cast<float4 *>(lo)[i] = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// One 128 x nt tile of one (m, p) block.  Dynamic shared memory: kStages
+// stages of {A raw, A lo, B raw, B lo}, each tile 1024-byte aligned.
+__global__ void __launch_bounds__(kThreads, 1)
+legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+                    const LegItem *__restrict__ items, LegGeom g, float *__restrict__ are, float *__restrict__ aim,
+                    int *__restrict__ status)
+{
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[kStages], mma_bar[kStages];
+    __shared__ uint32_t tmem_base;
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const LegItem it = items[blockIdx.x / g.ntiles];
+    const int ct = blockIdx.x % g.ntiles;                // column tile
+    const int nt = g.nt;
+    const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)nt * 128;
+    const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+    auto a_raw = [&](int s) { return smem + s * stage_bytes; };
+    auto a_lo = [&](int s) { return smem + s * stage_bytes + a_bytes; };
+    auto b_raw = [&](int s) { return smem + s * stage_bytes + 2 * a_bytes; };
+    auto b_lo = [&](int s) { return smem + s * stage_bytes + 2 * a_bytes + b_bytes; };
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&tmem_base)), "n"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; s++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full_bar[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[s])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_a) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_b) : "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+    const int nk = (g.nh + kBK - 1) / kBK;
+    const int arow = (int)(it.arow + it.r0);
+    const int brow = (int)(((int64_t)it.m * 2 + it.p) * g.ncp + (int64_t)ct * nt);
+    auto issue = [&](int i) {                            // slice i -> stage i % 2 (one thread)
+        const int s = i % kStages;
+        const uint32_t fb = smem_u32(&full_bar[s]);
+        mbar_expect(fb, a_bytes + b_bytes);
+        tma_load_2d(smem_u32(a_raw(s)), &tmap_a, i * kBK, arow, fb);
+        tma_load_2d(smem_u32(b_raw(s)), &tmap_b, i * kBK, brow, fb);
+    };
+    bool ok = true;
+    if (tid == 0)
+        for (int i = 0; i < nk && i < kStages; i++) issue(i);
+    for (int i = 0; i < nk; i++) {
+        const int s = i % kStages;
+        const uint32_t par = (uint32_t)(i / kStages) & 1u;
+        if (!mbar_wait(smem_u32(&full_bar[s]), par)) ok = false;
+        if (!__syncthreads_and(ok)) { ok = false; break; }
+        split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), tid);
+        split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah = smem_u32(a_raw(s)), al = smem_u32(a_lo(s));
+            const uint32_t bh = smem_u32(b_raw(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+            for (int k = 0; k < kBK / 8; k++) {            // 8-deep K steps, 32 bytes apart in the swizzle row
+                const uint64_t dah = sw128_desc(ah + 32 * k), dal = sw128_desc(al + 32 * k);
+                const uint64_t dbh = sw128_desc(bh + 32 * k), dbl = sw128_desc(bl + 32 * k);
+#pragma unroll
+                for (int t = 0; t < 3; t++) {
+                    const uint64_t da = t == 2 ? dal : dah, db = t == 1 ? dbl : dbh;
+                    const uint32_t acc = (i > 0 || k > 0 || t > 0) ? 1u : 0u;
+                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                                 :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(&mma_bar[s])) : "memory");
+            // refill this stage once its MMAs are done with it
+            if (i + kStages < nk) {
+                if (mbar_wait(smem_u32(&mma_bar[s]), par)) issue(i + kStages);
+                else ok = false;
             }
         }
-    };
-    auto store = [&](int buf) {
+    }
+    // the last slice's MMAs (and so all of them) complete
+    if (ok && nk > 0) {
+        const int s = (nk - 1) % kStages;
+        if (!mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)((nk - 1) / kStages) & 1u)) ok = false;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (__syncthreads_and(ok)) {
+        // warp w holds rows 32 w .. 32 w + 31 of the tile in its TMEM lanes
+        const int row = 32 * warp + (tid & 31);
+        const bool live = row < it.nr;
+        const int64_t o = tri_offset(it.m, g.T) + it.p + 2 * (int64_t)(it.r0 + row);
+        for (int c0 = 0; c0 < nt; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                         : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (live) {
 #pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int e = tid + kGemmThreads * h, kr = e >> 4, q4 = (e & 15) * 4;
-            *reinterpret_cast<float4 *>(&As[buf][kr][q4]) = ra[h];
-            *reinterpret_cast<float4 *>(&Bs[buf][kr][q4]) = rb[h];
+                for (int q = 0; q < 16; q++) {
+                    const int c = ct * nt + c0 + q;
+                    if (c < g.N) {
+                        const int part = c >= g.nlev, lev = part ? c - g.nlev : c;
+                        (part ? aim : are)[(int64_t)lev * g.os + o] = __uint_as_float(v[q]);
+                    }
+                }
+            }
         }
-    };
-    float acc[8][4] = {};
-    load(0);
-    store(0);
+    } else if (tid == 0) {
+        atomicExch(status, 1);
+        // let copies and MMAs still in flight land before the CTA leaves
+        for (int s = 0; s < kStages; s++) {
+            mbar_wait(smem_u32(&full_bar[s]), 0u);
+            mbar_wait(smem_u32(&mma_bar[s]), 0u);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    int buf = 0;
-    for (int k0 = 0; k0 < g.nh; k0 += kBK) {
-        const bool more = k0 + kBK < g.nh;
-        if (more) load(k0 + kBK);
-        if (active)
-#pragma unroll
-        for (int k = 0; k < kBK; k++) {
-            const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][r_base]);
-            const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][r_base + 4]);
-            const float4 b = *reinterpret_cast<const float4 *>(&Bs[buf][k][c_base]);
-            const float ai[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w}, bj[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-            for (int i = 0; i < 8; i++)
-#pragma unroll
-                for (int jj = 0; jj < 4; jj++) acc[i][jj] = fmaf(ai[i], bj[jj], acc[i][jj]);
-        }
-        if (more) store(buf ^ 1);
-        __syncthreads();
-        buf ^= 1;
-    }
-    const int64_t base = tri_offset(it.m, g.T) + it.p;     // l = m + p + 2 (r0 + row)
-#pragma unroll
-    for (int i = 0; i < 8; i++) {
-        const int row = r_base + i;
-        if (row >= it.nr) continue;
-        const int64_t o = base + 2 * (int64_t)(it.r0 + row);
-#pragma unroll
-        for (int jj = 0; jj < 4; jj++) {
-            const int c = c0 + c_base + jj;
-            if (c >= N) continue;
-            const int part = c >= g.nlev, lev = part ? c - g.nlev : c;
-            (part ? aim : are)[(int64_t)lev * g.os + o] = acc[i][jj];
-        }
-    }
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(kTmemCols));
 }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, []() {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA view of a K-major float32 matrix: `rows` rows of `k` values (`ld`
+// floats apart, ld * 4 a multiple of 16), read as {32 x box_rows} boxes with
+// 128-byte swizzle; values past k or rows read as zero.
+int make_tmap(CUtensorMap *map, const float *base, int64_t k, int64_t rows, int64_t ld, int box_rows)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return ZFPX_ECUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)k, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ZFPX_OK : ZFPX_ECUDA;
+}
+
+// columns per tile for N = 2 nlev columns: the fewest tiles of at most 256
+// columns, each a multiple of 16
+void column_tiles(int N, int &nt, int &ntiles)
+{
+    ntiles = (N + 255) / 256;
+    nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
+}
+
+size_t mma_smem_bytes(int nt) { return 1024 + (size_t)kStages * (2 * kBM * 128 + 2 * (size_t)nt * 128); }
 
 // Gauss-Legendre nodes (north to south) and weights: Newton's iteration on
 // P_n from the initial guesses cos(pi (i + 3/4) / (n + 1/2)), the upper half
@@ -245,59 +399,59 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
     if (nlat < 2 || nlat % 2 || nlat > 1 << 15 || T < 0 || T + 1 > nlat) return ZFPX_EINVAL;   // grid z = nlat
     auto *p = new zfpx_legendre_s();
     p->nlat = nlat; p->T = T; p->nh = nlat / 2;
+    p->nhs = (p->nh + 3) / 4 * 4;                        // row pitch: a multiple of 16 bytes
     if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ZFPX_ECUDA; }
     std::vector<double> mu, w;
     gauss_legendre(nlat, mu, w);
-    const int nh = p->nh;
+    const int nh = p->nh, nhs = p->nhs;
     std::vector<double> s(nh);
     for (int j = 0; j < nh; j++) s[j] = std::sqrt(std::max(0.0, 1.0 - mu[j] * mu[j]));
-    // blocks: for m = 0..T, parity 0 then 1, a [nh][ldm] block whose column i
-    // is the row l = m + p + 2 i (ldm = that parity's row count rounded up to 4)
-    int64_t total = 0;
+    // rows: for m = 0..T, parity 0 then 1, one row per l = m + p + 2 i, K-major
+    int64_t rows = 0;
     for (int m = 0; m <= T; m++)
-        for (int par = 0; par < 2; par++) {
-            const int cnt = (T - m - par) >= 0 ? (T - m - par) / 2 + 1 : 0;
-            total += (int64_t)nh * ((cnt + 3) / 4 * 4);
-        }
-    std::vector<float> tab((size_t)total, 0.0f);
+        for (int par = 0; par < 2; par++) rows += (T - m - par) >= 0 ? (T - m - par) / 2 + 1 : 0;
+    p->table_rows = rows;
+    std::vector<float> tab((size_t)std::max<int64_t>(rows, 1) * nhs, 0.0f);
     std::vector<LegItem> items;
-    std::vector<double> pmm(nh, std::sqrt(0.5)), P0(nh), P1(nh), P2(nh);
-    std::vector<std::vector<double>> rows;
-    int64_t blk = 0;
+    std::vector<double> pmm(nh, std::sqrt(0.5));
+    std::vector<std::vector<double>> prow;
+    int64_t r = 0;
     for (int m = 0; m <= T; m++) {
         if (m > 0) {
             const double f = -std::sqrt((2.0 * m + 1.0) / (2.0 * m));
             for (int j = 0; j < nh; j++) pmm[j] *= f * s[j];
         }
         const int L = T - m + 1;
-        rows.assign(L, std::vector<double>(nh));
-        rows[0] = pmm;
+        prow.assign(L, std::vector<double>(nh));
+        prow[0] = pmm;
         if (L > 1)
-            for (int j = 0; j < nh; j++) rows[1][j] = std::sqrt(2.0 * m + 3.0) * mu[j] * pmm[j];
+            for (int j = 0; j < nh; j++) prow[1][j] = std::sqrt(2.0 * m + 3.0) * mu[j] * pmm[j];
         for (int i = 2; i < L; i++) {
             const double l = m + i;
             const double a = std::sqrt((4.0 * l * l - 1.0) / (l * l - (double)m * m));
             const double b = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
-            for (int j = 0; j < nh; j++) rows[i][j] = a * (mu[j] * rows[i - 1][j] - b * rows[i - 2][j]);
+            for (int j = 0; j < nh; j++) prow[i][j] = a * (mu[j] * prow[i - 1][j] - b * prow[i - 2][j]);
         }
         for (int par = 0; par < 2; par++) {
             const int cnt = par < L ? (L - 1 - par) / 2 + 1 : 0;
-            const int ldm = (cnt + 3) / 4 * 4;
             for (int c = 0; c < cnt; c++)
-                for (int j = 0; j < nh; j++)
-                    tab[(size_t)(blk + (int64_t)j * ldm + c)] = (float)(w[j] * rows[par + 2 * c][j]);
+                for (int j = 0; j < nh; j++) tab[(size_t)(r + c) * nhs + j] = (float)(w[j] * prow[par + 2 * c][j]);
             for (int r0 = 0; r0 < cnt; r0 += kBM)
-                items.push_back(LegItem{m, par, r0, std::min(kBM, cnt - r0), ldm, 0, blk});
-            blk += (int64_t)nh * ldm;
+                items.push_back(LegItem{m, par, r0, std::min(kBM, cnt - r0), r});
+            r += cnt;
         }
     }
     p->nitems = (int)items.size();
     if (cudaMalloc(&p->d_table, tab.size() * sizeof(float)) != cudaSuccess ||
-        cudaMalloc(&p->d_items, items.size() * sizeof(LegItem)) != cudaSuccess ||
+        cudaMalloc(&p->d_items, std::max<size_t>(items.size(), 1) * sizeof(LegItem)) != cudaSuccess ||
+        cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
         cudaMemcpy(p->d_table, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(LegItem), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(LegItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess ||
+        make_tmap(&p->tmap_table, p->d_table, nh, std::max<int64_t>(rows, 1), nhs, kBM) != ZFPX_OK) {
         cudaFree(p->d_table);
         cudaFree(p->d_items);
+        cudaFree(p->d_status);
         delete p;
         return ZFPX_ECUDA;
     }
@@ -319,14 +473,24 @@ void zfpx_legendre_destroy(zfpx_legendre p)
     if (!p) return;
     cudaFree(p->d_table);
     cudaFree(p->d_items);
+    cudaFree(p->d_status);
     delete p;
 }
 
 size_t zfpx_legendre_workspace_bytes(zfpx_legendre p, int64_t nlev)
 {
-    if (!p || nlev < 1) return 0;
-    const int64_t ldc = (2 * nlev + 3) / 4 * 4;
-    return (size_t)((int64_t)(p->T + 1) * 2 * p->nh * ldc * (int64_t)sizeof(float));
+    if (!p || nlev < 1 || nlev > (1 << 20)) return 0;
+    int nt, ntiles;
+    column_tiles((int)(2 * nlev), nt, ntiles);
+    return (size_t)((int64_t)(p->T + 1) * 2 * ntiles * nt * p->nhs * (int64_t)sizeof(float));
+}
+
+int zfpx_legendre_status(zfpx_legendre p)
+{
+    if (!p) return ZFPX_EINVAL;
+    int v = 0;
+    if (cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return ZFPX_ECUDA;
+    return v ? ZFPX_ETIMEOUT : ZFPX_OK;
 }
 
 int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im, const int64_t n[3],
@@ -341,21 +505,36 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
         ((uintptr_t)d_work & 15u))
         return ZFPX_EINVAL;
     if (work_bytes < zfpx_legendre_workspace_bytes(p, n[2])) return ZFPX_ESIZE;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return ZFPX_ECUDA;
+    if (dev != p->device) return ZFPX_EINVAL;
     LegGeom g{};
-    g.nlat = p->nlat; g.nh = p->nh; g.T = p->T; g.nlev = (int)n[2];
-    g.ldc = (2 * g.nlev + 3) / 4 * 4;
-    g.nct = (2 * g.nlev + kBN - 1) / kBN;
+    g.nlat = p->nlat; g.nh = p->nh; g.nhs = p->nhs; g.T = p->T; g.nlev = (int)n[2];
+    g.N = 2 * g.nlev;
+    column_tiles(g.N, g.nt, g.ntiles);
+    g.ncp = g.nt * g.ntiles;
     g.is1 = stride[1]; g.is2 = stride[2]; g.os = out_stride;
+    const int64_t grows = (int64_t)(p->T + 1) * 2 * g.ncp;
+    if (grows > 0x7fffffff || p->table_rows > 0x7fffffff) return ZFPX_EINVAL;
     float *G = static_cast<float *>(d_work);
-    const dim3 fgrid((p->T + 1 + 31) / 32, (g.nlev + 31) / 32, 2 * p->nh);
-    legendre_fold_kernel<<<fgrid, dim3(32, 8), 0, (cudaStream_t)stream>>>(d_re, d_im, G, g);
-    count_launch();
-    int rc = check_launch();
+    CUtensorMap tmap_g;
+    int rc = make_tmap(&tmap_g, G, p->nh, grows, p->nhs, g.nt);
     if (rc) return rc;
-    const int64_t nblk = (int64_t)p->nitems * g.nct;
+    cudaStream_t st = (cudaStream_t)stream;
+    const dim3 fgrid((p->T + 1 + 31) / 32, (p->nhs + 31) / 32, 2 * g.nlev);
+    if (fgrid.z > 65535) return ZFPX_EINVAL;
+    legendre_fold_kernel<<<fgrid, dim3(32, 8), 0, st>>>(d_re, d_im, G, g);
+    count_launch();
+    rc = check_launch();
+    if (rc) return rc;
+    const int64_t nblk = (int64_t)p->nitems * g.ntiles;
     if (nblk > 0x7fffffff) return ZFPX_EINVAL;
-    legendre_gemm_kernel<<<(unsigned)nblk, kGemmThreads, 0, (cudaStream_t)stream>>>(p->d_table, G, p->d_items, g, d_are,
-                                                                                 d_aim);
+    if (nblk == 0) return ZFPX_OK;
+    const size_t smem = mma_smem_bytes(g.nt);
+    if (cudaFuncSetAttribute(legendre_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return ZFPX_ECUDA;
+    legendre_mma_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, d_are, d_aim,
+                                                                p->d_status);
     count_launch();
     return check_launch();
 }

@@ -132,6 +132,7 @@ def lib():
                                 ctypes.c_int),
         "zfpx_legendre_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_legendre_destroy": ([vp], None),
+        "zfpx_legendre_status": ([vp], ctypes.c_int),
         "zfpx_legendre_workspace_bytes": ([vp, ctypes.c_int64], sz),
         "zfpx_legendre_forward": ([vp, vp, vp, i64p, i64p, vp, vp, ctypes.c_int64, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
@@ -443,6 +444,11 @@ class Legendre:
 
     def workspace_bytes(self, nlev):
         return int(lib().zfpx_legendre_workspace_bytes(self._h, int(nlev)))
+
+    def status(self):
+        """Synchronously checks that no earlier forward gave up on a bounded
+        device-side wait (raises ZfpxError(ZFPX_ETIMEOUT) if one did)."""
+        _check(lib().zfpx_legendre_status(self._h), "zfpx_legendre_status")
 
     def forward(self, re, im, are, aim, stream=None):
         """re, im: float32 [lev][nlat][K] wavenumber fields (same strides); are, aim:
