@@ -615,6 +615,33 @@ def extra_sht_fourier(z, xd, reps, peak):
     res = {"workload": "1280x640x137 f32, rows of 1280 longitudes -> 640 wavenumbers -> T639 coefficients; 8x8 ranks",
            "fft_ms": t, "fft_GBps": moved / (t / 1e3) / 1e9,
            "fft_frac_of_measured_hbm": moved / (t / 1e3) / 1e9 / peak}
+    # the decode fused with the FFT against decompress+unpack then FFT, from the
+    # received streams of the benchmark plan
+    fplan = z.Plan.for_fields(xd, PR, PC, 0, 3)
+    dec = torch.empty_like(xd)
+    fre, fim = torch.empty_like(re), torch.empty_like(im)
+    work = None
+    for r in RATES:
+        recv = torch.zeros(fplan.buffer_bytes(r), dtype=torch.uint8, device="cuda")
+        z.zfpx_pack_compress(fplan, r, xd, recv, z.LAYOUT_RECV)
+        work = z.zfpx_decompress_rfft(fplan, r, recv, fre, fim, work=work)
+
+        def sep():
+            z.zfpx_decompress_unpack(fplan, r, recv, dec)
+            z.zfpx_rfft_lon(dec, re, im)
+        t_sep = _events_ms(sep, reps)
+        t_fus = _events_ms(lambda: z.zfpx_decompress_rfft(fplan, r, recv, fre, fim, work=work), reps)
+        torch.cuda.synchronize()
+        same = bool(torch.equal(fre.view(torch.int32), re.view(torch.int32)) and
+                    torch.equal(fim.view(torch.int32), im.view(torch.int32)))
+        moved = recv.numel() + 8 * re.numel()                 # streams in, wavenumbers out
+        res["decode_fft_r%d" % r] = {"separate_ms": t_sep, "fused_ms": t_fus, "identical": same,
+                                     "fused_GBps_f32_equiv": 4 * xd.numel() / (t_fus / 1e3) / 1e9,
+                                     "fused_frac_of_measured_hbm": moved / (t_fus / 1e3) / 1e9 / peak}
+        del recv
+    del dec, fre, fim, work
+    fplan.close()
+    z.zfpx_rfft_lon(xd, re, im)                              # the spectra of the uncompressed field again
     leg = z.Legendre(ny, T)
     a_re = torch.empty((nz, leg.ncoeffs), device="cuda")
     a_im = torch.empty_like(a_re)

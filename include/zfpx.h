@@ -268,6 +268,29 @@ ZFPX_API int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const in
 ZFPX_API int zfpx_rfft_lon(const float *d_in, const int64_t n[3], const int64_t stride[3], int K, float *d_re,
                            float *d_im, const int64_t ostride[3], void *stream);
 
+/* ---- decompression fused with the longitude FFT (Sec. II-A; Sec. VI) ------
+ * For a z -> lambda plan (transposition 0, dims 3): decodes the received
+ * messages d_recv (len bytes, the receive layout of zfpx_pack_compress /
+ * zfpx_permute at `rate` 8 or 16) and transforms every longitude row of the
+ * assembled field straight into wavenumbers F_m = (1/N) sum_j x_j
+ * exp(-2 pi i j m / N), m < K <= N/2 + 1 (N = the plan's n[0], even, at most
+ * 8192, with prime factors 2, 3 and 5 only), real parts to d_re and imaginary
+ * parts to d_im, float32 [n2][n1][>= K] with element strides ostride
+ * (ostride[0] == 1).  The values equal, bit for bit, zfpx_decompress_unpack
+ * followed by zfpx_rfft_lon on the decoded field; the float32 field is never
+ * written to memory in between.  d_work: caller-owned device scratch
+ * (16-byte aligned) of zfpx_decompress_rfft_workspace_bytes(plan) bytes, row
+ * buffers that stay in L2; calls that share d_work must not overlap on the
+ * GPU.  The first call per (plan, rate) uploads the plan's unit table (an
+ * allocation, so make that first call before any stream capture).  Errors:
+ * ZFPX_EINVAL (NULL, plan kind, sizes, strides, alignment, or a plan whose
+ * messages to one receiver do not tile its rows), ZFPX_ESIZE, ZFPX_ECUDA,
+ * ZFPX_ENOMEM. */
+ZFPX_API size_t zfpx_decompress_rfft_workspace_bytes(zfpx_plan plan);
+ZFPX_API int zfpx_decompress_rfft(zfpx_plan plan, int rate, const uint8_t *d_recv, size_t len, int K, float *d_re,
+                                  float *d_im, const int64_t ostride[3], void *d_work, size_t work_bytes,
+                                  void *stream);
+
 /* ---- the Legendre transform (the latitude transform after the second
  * transposition) -------------------------------------------------------------
  * The spectral transform's latitude half (Sec. II-A: associated Legendre

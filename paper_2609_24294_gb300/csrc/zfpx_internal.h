@@ -64,6 +64,8 @@ namespace zfpx {
 enum UnitKind { UNIT_BLOCKS32 = 0, UNIT_QUADS = 1, UNIT_CHUNK16 = 2 };
 
 int64_t message_bytes(const zfpx_plan_s *p, const HostMsg &m, int rate);
+// Offsets of every message (send-order index) in the given layout; the total in *total.
+std::vector<int64_t> layout_offsets(const zfpx_plan_s *p, int rate, int layout, int64_t *total);
 int64_t buffer_bytes(const zfpx_plan_s *p, int rate);
 // Fetches (building on first use) the device table; returns ZFPX_OK or an error.
 int get_table(zfpx_plan_s *p, int rate, UnitKind kind, DevTable **out);

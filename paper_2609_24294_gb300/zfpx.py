@@ -133,6 +133,8 @@ def lib():
         "zfpx_legendre_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_legendre_destroy": ([vp], None),
         "zfpx_legendre_status": ([vp], ctypes.c_int),
+        "zfpx_decompress_rfft_workspace_bytes": ([vp], sz),
+        "zfpx_decompress_rfft": ([vp, ctypes.c_int, vp, sz, ctypes.c_int, vp, vp, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_legendre_workspace_bytes": ([vp, ctypes.c_int64], sz),
         "zfpx_legendre_forward": ([vp, vp, vp, i64p, i64p, vp, vp, ctypes.c_int64, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_destroy": ([vp], None),
@@ -693,6 +695,25 @@ class Pipeline:
             self.close()
         except Exception:
             pass
+
+
+def zfpx_decompress_rfft(plan, rate, recv, re, im, work=None, stream=None):
+    """Decodes the received messages of a z -> lambda plan and transforms every
+    longitude row into wavenumbers: re, im float32 [lev][lat][K] (unit inner
+    stride).  `work`: scratch of zfpx_decompress_rfft_workspace_bytes bytes
+    (allocated here if None).  Returns the work tensor for reuse."""
+    if re.dtype != torch.float32 or im.dtype != torch.float32 or re.shape != im.shape or re.stride() != im.stride():
+        raise ValueError("re and im must be float32 with the same shape and strides")
+    if re.dim() != 3 or re.stride(2) != 1:
+        raise ValueError("re and im must be [lev][lat][K] with unit inner stride")
+    nbytes = int(lib().zfpx_decompress_rfft_workspace_bytes(plan.handle))
+    if work is None or _nbytes(work) < nbytes:
+        work = torch.empty(max(16, nbytes), dtype=torch.uint8, device=re.device)
+    os_ = (1, re.stride(1), re.stride(0))
+    _check(lib().zfpx_decompress_rfft(plan.handle, int(rate), _dev(recv, "recv"), _nbytes(recv), int(re.shape[2]),
+                                      _dev(re, "re"), _dev(im, "im"), _i64x3(os_), _dev(work, "work"), _nbytes(work),
+                                      _stream(stream)), "zfpx_decompress_rfft")
+    return work
 
 
 def zfpx_set_units_per_warp(encode, rate, upw):
