@@ -30,13 +30,15 @@
 // in tensor memory; the dropped a_lo b_lo and the TF32 rounding of the lo
 // parts leave about 2^-21 of sum |a b| per product, far below the float32
 // dot-product bound the transform is held to.  A CTA of four warps computes a
-// 128-row x Nt-column tile of one (m, p) block: TMA loads 32-deep K slices of
-// both operands (128-byte swizzled, two stages in flight), the warps derive
-// the lo tiles in place, one thread issues the MMAs (three per 8-deep K step)
-// and commits them to an mbarrier, and after the last slice each warp reads
-// its 32 rows of the accumulator from tensor memory and scatters them into
-// the triangular output.  Every wait is bounded; a wait that runs out sets
-// the plan's status word and the CTA stops.
+// 128-row x Nt-column tile of one (m, p) block: one lane of warp 0 keeps TMA
+// loads of 32-deep K slices of both operands (128-byte swizzled) up to four
+// stages ahead, the other three warps derive the lo tiles in place, one of
+// their threads issues the MMAs (three per 8-deep K step) and commits them to
+// the stage's mbarrier, which frees the stage for the next load; after the
+// last slice each warp reads its 32 rows of the accumulator from tensor
+// memory and scatters them into the triangular output.  Every wait is
+// bounded; a wait that runs out sets the plan's status word and the CTA
+// stops.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -66,7 +68,6 @@ namespace {
 
 constexpr int kBM = 128;        // rows per CTA tile (the MMA's M)
 constexpr int kBK = 32;         // K per stage: one 128-byte swizzle row of float32
-constexpr int kStages = 2;
 constexpr int kThreads = 128;
 constexpr int kTmemCols = 256;
 constexpr long long kSpinLimit = 1ll << 26;   // about a second of polling
@@ -156,33 +157,43 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
 }
 
-// lo = round_to_tf32(a - trunc_to_tf32(a)) over n 16-byte chunks
-__device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nchunks, int tid)
+// lo = round_to_tf32(a - trunc_to_tf32(a)) over n 16-byte chunks, by the
+// `nthr` threads numbered t
+__device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nchunks, int t, int nthr)
 {
-    for (int i = tid; i < nchunks; i += kThreads) {
+    for (int i = t; i < nchunks; i += nthr) {
         const float4 a = reinterpret_cast<const float4 *>(raw)[i];
         float v[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
             const float h = __uint_as_float(__float_as_uint(v[q]) & 0xffffe000u);
-            uint32_t t;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t) : "f"(v[q] - h));
-            v[q] = __uint_as_float(t);
+            uint32_t r;
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v[q] - h));
+            v[q] = __uint_as_float(r);
         }
         reinterpret_cast<float4 *>(lo)[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
 }
 
-// One 128 x nt tile of one (m, p) block.  Dynamic shared memory: kStages
-// stages of {A raw, A lo, B raw, B lo}, each tile 1024-byte aligned.
+// One 128 x nt tile of one (m, p) block, warp-specialised: warp 0 (one lane)
+// keeps the TMA loads of the K slices `stages` ahead, refilling a stage as
+// soon as the MMAs that read it have completed; warps 1-3 wait for a slice,
+// derive its lo tiles and meet at a named barrier, after which one of their
+// threads issues the slice's MMAs and commits them to the stage's mbarrier
+// (nobody waits for the MMAs until the accumulator is read).  Dynamic shared
+// memory: `stages` x {A raw, A lo, B raw, B lo}, each tile 1024-byte aligned.
+constexpr int kMaxStages = 4;
+constexpr int kConsumers = kThreads - 32;
+
 __global__ void __launch_bounds__(kThreads, 1)
 legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-                    const LegItem *__restrict__ items, LegGeom g, float *__restrict__ are, float *__restrict__ aim,
-                    int *__restrict__ status)
+                    const LegItem *__restrict__ items, LegGeom g, int stages, float *__restrict__ are,
+                    float *__restrict__ aim, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kStages], mma_bar[kStages];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], mma_bar[kMaxStages];
     __shared__ uint32_t tmem_base;
+    __shared__ int fail;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
     const LegItem it = items[blockIdx.x / g.ntiles];
@@ -201,7 +212,8 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; s++) {
+        fail = 0;
+        for (int s = 0; s < stages; s++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full_bar[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[s])));
         }
@@ -213,59 +225,68 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
     const int nk = (g.nh + kBK - 1) / kBK;
-    const int arow = (int)(it.arow + it.r0);
-    const int brow = (int)(((int64_t)it.m * 2 + it.p) * g.ncp + (int64_t)ct * nt);
-    auto issue = [&](int i) {                            // slice i -> stage i % 2 (one thread)
-        const int s = i % kStages;
-        const uint32_t fb = smem_u32(&full_bar[s]);
-        mbar_expect(fb, a_bytes + b_bytes);
-        tma_load_2d(smem_u32(a_raw(s)), &tmap_a, i * kBK, arow, fb);
-        tma_load_2d(smem_u32(b_raw(s)), &tmap_b, i * kBK, brow, fb);
-    };
     bool ok = true;
-    if (tid == 0)
-        for (int i = 0; i < nk && i < kStages; i++) issue(i);
-    for (int i = 0; i < nk; i++) {
-        const int s = i % kStages;
-        const uint32_t par = (uint32_t)(i / kStages) & 1u;
-        if (!mbar_wait(smem_u32(&full_bar[s]), par)) ok = false;
-        if (!__syncthreads_and(ok)) { ok = false; break; }
-        split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), tid);
-        split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), tid);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
+    if (warp == 0) {
+        // ---- producer
         if (tid == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t ah = smem_u32(a_raw(s)), al = smem_u32(a_lo(s));
-            const uint32_t bh = smem_u32(b_raw(s)), bl = smem_u32(b_lo(s));
-#pragma unroll
-            for (int k = 0; k < kBK / 8; k++) {            // 8-deep K steps, 32 bytes apart in the swizzle row
-                const uint64_t dah = sw128_desc(ah + 32 * k), dal = sw128_desc(al + 32 * k);
-                const uint64_t dbh = sw128_desc(bh + 32 * k), dbl = sw128_desc(bl + 32 * k);
-#pragma unroll
-                for (int t = 0; t < 3; t++) {
-                    const uint64_t da = t == 2 ? dal : dah, db = t == 1 ? dbl : dbh;
-                    const uint32_t acc = (i > 0 || k > 0 || t > 0) ? 1u : 0u;
-                    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                                 :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+            const int arow = (int)(it.arow + it.r0);
+            const int brow = (int)(((int64_t)it.m * 2 + it.p) * g.ncp + (int64_t)ct * nt);
+            for (int i = 0; i < nk; i++) {
+                const int s = i % stages;
+                if (i >= stages && !mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)(i / stages - 1) & 1u)) {
+                    ok = false;
+                    break;
                 }
+                const uint32_t fb = smem_u32(&full_bar[s]);
+                mbar_expect(fb, a_bytes + b_bytes);
+                tma_load_2d(smem_u32(a_raw(s)), &tmap_a, i * kBK, arow, fb);
+                tma_load_2d(smem_u32(b_raw(s)), &tmap_b, i * kBK, brow, fb);
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         :: "r"(smem_u32(&mma_bar[s])) : "memory");
-            // refill this stage once its MMAs are done with it
-            if (i + kStages < nk) {
-                if (mbar_wait(smem_u32(&mma_bar[s]), par)) issue(i + kStages);
-                else ok = false;
+        }
+    } else {
+        // ---- consumers: lo tiles, then the MMAs (thread 32)
+        const int ct_ = tid - 32;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
+                               ((uint32_t)(kBM >> 4) << 24);
+        for (int i = 0; i < nk; i++) {
+            const int s = i % stages;
+            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(i / stages) & 1u)) ok = false;
+            split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), ct_, kConsumers);
+            split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), ct_, kConsumers);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (!ok) atomicExch(&fail, 1);
+            asm volatile("bar.sync 1, %0;" :: "n"(kConsumers) : "memory");
+            if (*(volatile int *)&fail) { ok = false; break; }
+            if (tid == 32) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t ah = smem_u32(a_raw(s)), al = smem_u32(a_lo(s));
+                const uint32_t bh = smem_u32(b_raw(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+                for (int k = 0; k < kBK / 8; k++) {        // 8-deep K steps, 32 bytes apart in the swizzle row
+                    const uint64_t dah = sw128_desc(ah + 32 * k), dal = sw128_desc(al + 32 * k);
+                    const uint64_t dbh = sw128_desc(bh + 32 * k), dbl = sw128_desc(bl + 32 * k);
+#pragma unroll
+                    for (int t = 0; t < 3; t++) {
+                        const uint64_t da = t == 2 ? dal : dah, db = t == 1 ? dbl : dbh;
+                        const uint32_t acc = (i > 0 || k > 0 || t > 0) ? 1u : 0u;
+                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             :: "r"(smem_u32(&mma_bar[s])) : "memory");
             }
         }
     }
-    // the last slice's MMAs (and so all of them) complete
+    if (!ok) atomicExch(&fail, 1);
+    __syncthreads();
+    ok = !fail;
+    // every MMA has completed once the last slice's commit has arrived
     if (ok && nk > 0) {
-        const int s = (nk - 1) % kStages;
-        if (!mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)((nk - 1) / kStages) & 1u)) ok = false;
+        const int s = (nk - 1) % stages;
+        if (!mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)((nk - 1) / stages) & 1u)) ok = false;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (__syncthreads_and(ok)) {
@@ -295,7 +316,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
     } else if (tid == 0) {
         atomicExch(status, 1);
         // let copies and MMAs still in flight land before the CTA leaves
-        for (int s = 0; s < kStages; s++) {
+        for (int s = 0; s < stages; s++) {
             mbar_wait(smem_u32(&full_bar[s]), 0u);
             mbar_wait(smem_u32(&mma_bar[s]), 0u);
         }
@@ -345,7 +366,16 @@ void column_tiles(int N, int &nt, int &ntiles)
     nt = ((N + ntiles - 1) / ntiles + 15) / 16 * 16;
 }
 
-size_t mma_smem_bytes(int nt) { return 1024 + (size_t)kStages * (2 * kBM * 128 + 2 * (size_t)nt * 128); }
+size_t stage_bytes(int nt) { return 2 * kBM * 128 + 2 * (size_t)nt * 128; }
+
+// as many stages (2 .. 4) as fit beside one CTA's static shared memory
+int mma_stages(int nt)
+{
+    const size_t budget = 220 * 1024 - 1024;
+    return (int)std::max<size_t>(2, std::min<size_t>(kMaxStages, budget / stage_bytes(nt)));
+}
+
+size_t mma_smem_bytes(int nt) { return 1024 + (size_t)mma_stages(nt) * stage_bytes(nt); }
 
 // Gauss-Legendre nodes (north to south) and weights: Newton's iteration on
 // P_n from the initial guesses cos(pi (i + 3/4) / (n + 1/2)), the upper half
@@ -533,8 +563,8 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
     const size_t smem = mma_smem_bytes(g.nt);
     if (cudaFuncSetAttribute(legendre_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return ZFPX_ECUDA;
-    legendre_mma_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, d_are, d_aim,
-                                                                p->d_status);
+    legendre_mma_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, mma_stages(g.nt),
+                                                                d_are, d_aim, p->d_status);
     count_launch();
     return check_launch();
 }
