@@ -407,20 +407,25 @@ def extra_serving(z, peak, lens, fields, n=2000, rate_hz=50e3, arena=40 << 30):
         calls.append(dict(src=ptr, lev_stride=f.stride(0), nlev=r["nz"], dims=r["dims"], rate=r["rate"],
                           row0=r["row0"], row1=r["row1"]))
     srv = serve.Server(lens, arena_bytes=arena, nstreams=4, max_batch=64)
-    serve.run_requests(srv, calls[:50])                                   # warm-up
+    serve.run_requests_native(srv, calls[:50])                            # warm-up
     arrivals = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate_hz, n))
-    lat, wall, busy_max, _ = serve.run_requests(srv, calls, arrivals=arrivals)
-    st = srv.stats()
+    lat, wall, busy_max, nbatch = serve.run_requests_native(srv, calls, arrivals=arrivals)
     total = float(sum(r["bytes"] for r in reqs))
     res = {"workload": "%d O1280 slabs, lognormal sizes (median %.2f MB, max %.1f MB), Poisson %.0f/s, rates 8/16, "
-                       "40 GB arena, 4 streams" % (n, np.median([r["bytes"] for r in reqs]) / 1e6,
-                                                  max(r["bytes"] for r in reqs) / 1e6, rate_hz),
+                       "40 GB arena, 4 streams, request loop in the library" % (
+                           n, np.median([r["bytes"] for r in reqs]) / 1e6, max(r["bytes"] for r in reqs) / 1e6,
+                           rate_hz),
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
            "mean_ms": float(lat.mean() * 1e3), "wall_ms": wall * 1e3, "f32_GBps_sustained": total / wall / 1e9,
-           "offered_GBps": total * rate_hz / n / 1e9, "batches": st["batches"], "max_streams_busy": busy_max}
+           "offered_GBps": total * rate_hz / n / 1e9, "batches": nbatch, "requests_per_batch": n / max(nbatch, 1),
+           "max_streams_busy": busy_max}
     # capacity: every request submitted at once, the engine batching as fast as it can
-    _, wall_cap, _, _ = serve.run_requests(srv, calls)
+    _, wall_cap, _, nb_cap = serve.run_requests_native(srv, calls)
     res["capacity_f32_GBps"] = total / wall_cap / 1e9
+    res["capacity_requests_per_batch"] = n / max(nb_cap, 1)
+    # the same loop driven from Python (ctypes per submit, pump and poll), for comparison
+    _, wall_py, _, _ = serve.run_requests(srv, calls)
+    res["capacity_f32_GBps_python_loop"] = total / wall_py / 1e9
     srv.close()
     # comparators: the same slabs through float32 / float16 pack + unpack, back to back, replayed
     # from a CUDA graph (one launch per slab and direction would otherwise be host-bound)

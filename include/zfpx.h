@@ -430,6 +430,18 @@ ZFPX_API int zfpx_server_copy_result(zfpx_server server, int64_t id, uint8_t *h_
                                      float *h_values, size_t values_cap);
 ZFPX_API int zfpx_server_release(zfpx_server server, int64_t id);
 ZFPX_API int zfpx_server_stats(zfpx_server server, int64_t out[6]);
+/* The request loop in native code: submits request i once arrivals[i]
+ * seconds have passed since the call began (all at once if arrivals is NULL),
+ * and between arrivals pumps (a batch on every free stream), polls and
+ * releases finished requests, until every request has finished.  t_done[i]:
+ * the time from the start at which the loop saw request i finished, or -1 if
+ * it was refused (ZFPX_ENOMEM_BUDGET: larger than the arena).  info (may be
+ * NULL): [wall seconds from the first arrival to the last completion, batches
+ * launched, most streams busy at once, requests refused].  The results are
+ * released as they finish (use submit / pump / poll to keep them).  Errors:
+ * ZFPX_EINVAL, and those of submit, pump and poll. */
+ZFPX_API int zfpx_server_run(zfpx_server server, const zfpx_field *reqs, int n, const double *arrivals,
+                             double *t_done, double *info);
 
 /* ---- capturing any sequence of calls into a CUDA graph ---------------------
  * zfpx_capture_begin starts stream capture on `stream` (which must not be the

@@ -17,6 +17,7 @@
 // are contiguous, and each warp of the persistent grid takes a contiguous
 // range of chunks.  The class is uniform across a warp.
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstring>
 #include <deque>
@@ -991,6 +992,78 @@ int zfpx_server_stats(zfpx_server s, int64_t out[6])
     out[3] = s->arena.total;
     out[4] = s->batches;
     out[5] = (int64_t)s->completed.size();
+    return ZFPX_OK;
+}
+
+// The request loop in native code: request i is submitted once `arrivals[i]`
+// seconds have passed since the call began (all at once when arrivals is
+// NULL); between arrivals the loop pumps (a batch on every free stream) and
+// polls, releasing every finished request.  t_done[i] receives the time from
+// the start at which the loop saw request i finished (-1 if it was refused as
+// larger than the arena).  info, if not NULL: [wall seconds from the first
+// arrival to the last completion, batches launched, most streams busy at once,
+// requests refused].
+int zfpx_server_run(zfpx_server s, const zfpx_field *reqs, int n, const double *arrivals, double *t_done,
+                    double *info)
+{
+    if (!s || n < 0 || (n > 0 && (!reqs || !t_done))) return ZFPX_EINVAL;
+    using clk = std::chrono::steady_clock;
+    const clk::time_point t0 = clk::now();
+    auto elapsed = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    std::unordered_map<int64_t, int> index;
+    index.reserve((size_t)n * 2 + 1);
+    const int64_t batches0 = s->batches;
+    int i = 0, done = 0, refused = 0, busy_max = 0;
+    std::vector<int64_t> fin(256);
+    double first = arrivals && n ? arrivals[0] : 0.0, last = 0.0;
+    for (int k = 0; k < n; k++) {
+        t_done[k] = -1.0;
+        if (arrivals && arrivals[k] < first) first = arrivals[k];
+    }
+    while (done < n) {
+        const double now = elapsed();
+        while (i < n && (!arrivals || arrivals[i] <= now)) {
+            int64_t id = 0;
+            const int rc = zfpx_server_submit(s, &reqs[i], &id);
+            if (rc == ZFPX_ENOMEM_BUDGET) {
+                refused++;
+                done++;
+            } else if (rc) {
+                return rc;
+            } else {
+                index[id] = i;
+            }
+            i++;
+        }
+        for (;;) {                                     // a batch on every free stream
+            int launched = 0;
+            const int rc = zfpx_server_pump(s, &launched);
+            if (rc) return rc;
+            if (!launched) break;
+        }
+        int busy = 0;
+        for (auto &sl : s->slots) busy += sl.busy ? 1 : 0;
+        busy_max = std::max(busy_max, busy);
+        int nd = 0;
+        const int rc = zfpx_server_poll(s, fin.data(), (int)fin.size(), &nd);
+        if (rc) return rc;
+        for (int k = 0; k < nd; k++) {
+            auto it = index.find(fin[k]);
+            if (it != index.end()) {
+                t_done[it->second] = elapsed();
+                last = t_done[it->second];
+                index.erase(it);
+                done++;
+            }
+            zfpx_server_release(s, fin[k]);
+        }
+    }
+    if (info) {
+        info[0] = n ? last - first : 0.0;
+        info[1] = (double)(s->batches - batches0);
+        info[2] = busy_max;
+        info[3] = refused;
+    }
     return ZFPX_OK;
 }
 

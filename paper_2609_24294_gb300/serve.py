@@ -85,6 +85,33 @@ class Server:
             pass
 
 
+def run_requests_native(server, requests, arrivals=None):
+    """The same loop as run_requests, run inside the library (zfpx_server_run):
+    no Python between arrivals, results released as they finish.  Returns
+    per-request latency (s; NaN for refused requests), the wall time from the
+    first arrival to the last completion, the most streams busy at once and
+    the number of batches."""
+    n = len(requests)
+    arr = (z.Field * max(n, 1))()
+    for k, r in enumerate(requests):
+        f = arr[k]
+        f.d_src = r["src"]
+        f.d_dst = None
+        f.lev_stride = r["lev_stride"]
+        f.dst_lev_stride = 0
+        f.nlev, f.dims, f.rate, f.row0, f.row1, f.reserved = r["nlev"], r["dims"], r["rate"], r["row0"], r["row1"], 0
+    a = None if arrivals is None else np.ascontiguousarray(arrivals, dtype=np.float64)
+    t_done = np.empty(max(n, 1), dtype=np.float64)
+    info = np.zeros(4, dtype=np.float64)
+    dp = ctypes.POINTER(ctypes.c_double)
+    z._check(z.lib().zfpx_server_run(server._h, arr, n, None if a is None else a.ctypes.data_as(dp),
+                                     t_done.ctypes.data_as(dp), info.ctypes.data_as(dp)), "zfpx_server_run")
+    t_done = t_done[:n]
+    base = np.zeros(n) if a is None else a
+    lat = np.where(t_done >= 0, t_done - base, np.nan)
+    return lat, float(info[0]), int(info[2]), int(info[1])
+
+
 def run_requests(server, requests, arrivals=None, keep_results=False, max_inflight_results=None):
     """Submits request i at arrivals[i] seconds after the start (all at once
     if arrivals is None), pumping and polling until every request finished.

@@ -102,6 +102,8 @@ def lib():
         "zfpx_server_release": ([vp, ctypes.c_int64], ctypes.c_int),
         "zfpx_server_copy_result": ([vp, ctypes.c_int64, vp, sz, vp, sz], ctypes.c_int),
         "zfpx_server_stats": ([vp, i64p], ctypes.c_int),
+        "zfpx_server_run": ([vp, ctypes.POINTER(Field), ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "zfpx_capture_end": ([ctypes.POINTER(vp), vp], ctypes.c_int),
         "zfpx_batch_create": ([ctypes.POINTER(vp), i64p, ctypes.c_int, ctypes.POINTER(Field), ctypes.c_int],
                               ctypes.c_int),

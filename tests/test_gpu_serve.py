@@ -84,3 +84,37 @@ def test_admission_waits_for_memory_and_refuses_oversize(z):
     assert e.value.code == -5
     srv.close()
     small.close()
+
+
+def test_native_loop_matches_python_loop(z):
+    """zfpx_server_run (the request loop inside the library) finishes every
+    request, refuses what cannot fit, and leaves results identical to the
+    submit / pump / poll path (checked on a request kept afterwards)."""
+    from fieldgen import octahedral as og
+    from paper_2609_24294_gb300 import serve
+    lens = og.row_lengths(64)
+    f = og.octahedral_field(64, 9, 77, device="cuda")
+    offs = np.concatenate([[0], np.cumsum(lens)])
+    calls = []
+    for k in range(40):
+        r0 = 4 * (k % 28)
+        r1 = min(len(lens), r0 + 4 * (1 + k % 5))
+        calls.append(dict(src=f.data_ptr() + 4 * int(offs[r0]), lev_stride=f.stride(0), nlev=1 + k % 9,
+                          dims=3 if k % 3 else 1, rate=8 if k % 2 else 16, row0=r0, row1=r1))
+    srv = serve.Server(lens, arena_bytes=1 << 24, nstreams=3, max_batch=8)
+    arrivals = np.cumsum(np.full(len(calls), 2e-5))
+    lat, wall, busy, nb = serve.run_requests_native(srv, calls, arrivals=arrivals)
+    assert np.all(np.isfinite(lat)) and np.all(lat >= 0) and wall > 0 and 1 <= busy <= 3 and nb >= 1
+    lat2, _, _, _ = serve.run_requests_native(srv, calls)                  # all at once
+    assert np.all(np.isfinite(lat2))
+    _, _, _, kept = serve.run_requests(srv, calls[:3], keep_results=True)
+    _, _, _, again = serve.run_requests(srv, calls[:3], keep_results=True)
+    for a, b in zip(kept, again):
+        assert a[0].tobytes() == b[0].tobytes() and np.array_equal(a[1].view(np.uint32), b[1].view(np.uint32))
+    srv.close()
+    # a request larger than the arena is refused, the others still finish
+    small = serve.Server(lens, arena_bytes=4096, nstreams=1, max_batch=4)
+    big = dict(calls[0], nlev=9, row0=0, row1=len(lens))
+    lat3, _, _, _ = serve.run_requests_native(small, [big])
+    assert np.isnan(lat3).all()
+    small.close()
