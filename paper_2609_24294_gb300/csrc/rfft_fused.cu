@@ -40,7 +40,7 @@ struct FusedUnit {
     int32_t nyr, nzr;        // real latitudes and levels in the block row (<= 4)
 };
 
-constexpr int kWarps = 5;                      // 160 lanes: a 1280-longitude unit (320 blocks) in two rounds
+constexpr int kWarps = 4;
 constexpr int kRows = 16;                      // rows per unit
 
 template <int RATE>
