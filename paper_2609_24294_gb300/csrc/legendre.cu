@@ -68,8 +68,6 @@ namespace {
 
 constexpr int kBM = 128;        // rows per CTA tile (the MMA's M)
 constexpr int kBK = 32;         // K per stage: one 128-byte swizzle row of float32
-constexpr int kThreads = 128;
-constexpr int kTmemCols = 256;
 constexpr long long kSpinLimit = 1ll << 26;   // about a second of polling
 
 struct LegGeom {
@@ -175,29 +173,53 @@ __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nc
     }
 }
 
-// One 128 x nt tile of one (m, p) block, warp-specialised: warp 0 (one lane)
-// keeps the TMA loads of the K slices `stages` ahead, refilling a stage as
-// soon as the MMAs that read it have completed; warps 1-3 wait for a slice,
-// derive its lo tiles and meet at a named barrier, after which one of their
-// threads issues the slice's MMAs and commits them to the stage's mbarrier
-// (nobody waits for the MMAs until the accumulator is read).  Dynamic shared
-// memory: `stages` x {A raw, A lo, B raw, B lo}, each tile 1024-byte aligned.
+// Persistent and warp-specialised: one CTA per SM walks the tiles t =
+// blockIdx.x, blockIdx.x + gridDim.x, ... (a tile: 128 rows x nt columns of one
+// (m, p) block).  Roles:
+//   warp 0 (one lane)  TMA producer: the K slices of every tile in turn, up to
+//                      `stages` ahead, a stage refilled once the MMAs that read
+//                      it have completed (mma_bar);
+//   warps 1-3          wait for a slice (full_bar), derive its lo tiles, meet at
+//                      a named barrier; one of their threads issues the slice's
+//                      MMAs into the tile's accumulator and commits them to the
+//                      stage, and after a tile's last slice to acc_full;
+//   warps 4-7          epilogue: once a tile's accumulator is complete, each
+//                      reads the 32 rows of its TMEM lane quadrant, scatters
+//                      them into the triangular output and frees the
+//                      accumulator (acc_empty).
+// Two accumulators of 256 columns (all of the SM's tensor memory) alternate
+// between tiles, so a tile's epilogue overlaps the next tile's MMAs.
+// Dynamic shared memory: `stages` x {A raw, A lo, B raw, B lo}, 1024-aligned.
 constexpr int kMaxStages = 4;
-constexpr int kConsumers = kThreads - 32;
+constexpr int kConsumers = 96;                  // warps 1-3
+constexpr int kMmaThreads = 256;                // 8 warps
+constexpr int kAccCols = 256;
 
-__global__ void __launch_bounds__(kThreads, 1)
+// A bounded wait that also gives up once another role has failed.
+__device__ __forceinline__ bool role_wait(uint32_t mbar, uint32_t parity, volatile int *fail)
+{
+    for (long long i = 0; i < kSpinLimit; i++) {
+        uint32_t ok;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+        if (ok) return true;
+        if ((i & 1023) == 1023 && *fail) return false;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kMmaThreads, 1)
 legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
-                    const LegItem *__restrict__ items, LegGeom g, int stages, float *__restrict__ are,
-                    float *__restrict__ aim, int *__restrict__ status)
+                    const LegItem *__restrict__ items, LegGeom g, int stages, int ntiles_total,
+                    float *__restrict__ are, float *__restrict__ aim, int *__restrict__ status)
 {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[kMaxStages], mma_bar[kMaxStages];
+    __shared__ __align__(8) uint64_t full_bar[kMaxStages], mma_bar[kMaxStages], acc_full[2], acc_empty[2];
     __shared__ uint32_t tmem_base;
     __shared__ int fail;
+    volatile int *vfail = &fail;
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const LegItem it = items[blockIdx.x / g.ntiles];
-    const int ct = blockIdx.x % g.ntiles;                // column tile
     const int nt = g.nt;
     const uint32_t a_bytes = kBM * 128, b_bytes = (uint32_t)nt * 128;
     const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
@@ -208,7 +230,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     :: "r"(smem_u32(&tmem_base)), "n"(kTmemCols));
+                     :: "r"(smem_u32(&tmem_base)), "n"(2 * kAccCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -216,6 +238,10 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
         for (int s = 0; s < stages; s++) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&full_bar[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mma_bar[s])));
+        }
+        for (int a = 0; a < 2; a++) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&acc_full[a])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" :: "r"(smem_u32(&acc_empty[a])));
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_a) : "memory");
@@ -226,94 +252,120 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = tmem_base;
     const int nk = (g.nh + kBK - 1) / kBK;
-    bool ok = true;
+
     if (warp == 0) {
         // ---- producer
         if (tid == 0) {
-            const int arow = (int)(it.arow + it.r0);
-            const int brow = (int)(((int64_t)it.m * 2 + it.p) * g.ncp + (int64_t)ct * nt);
-            for (int i = 0; i < nk; i++) {
-                const int s = i % stages;
-                if (i >= stages && !mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)(i / stages - 1) & 1u)) {
-                    ok = false;
-                    break;
+            int i = 0;                                   // slice count over all tiles of this CTA
+            for (int t = blockIdx.x; t < ntiles_total && !*vfail; t += gridDim.x) {
+                const LegItem it = items[t / g.ntiles];
+                const int ct = t % g.ntiles;
+                const int arow = (int)(it.arow + it.r0);
+                const int brow = (int)(((int64_t)it.m * 2 + it.p) * g.ncp + (int64_t)ct * nt);
+                for (int k = 0; k < nk; k++, i++) {
+                    const int s = i % stages;
+                    if (i >= stages && !role_wait(smem_u32(&mma_bar[s]), (uint32_t)(i / stages - 1) & 1u, vfail)) {
+                        *vfail = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_u32(&full_bar[s]);
+                    mbar_expect(fb, a_bytes + b_bytes);
+                    tma_load_2d(smem_u32(a_raw(s)), &tmap_a, k * kBK, arow, fb);
+                    tma_load_2d(smem_u32(b_raw(s)), &tmap_b, k * kBK, brow, fb);
                 }
-                const uint32_t fb = smem_u32(&full_bar[s]);
-                mbar_expect(fb, a_bytes + b_bytes);
-                tma_load_2d(smem_u32(a_raw(s)), &tmap_a, i * kBK, arow, fb);
-                tma_load_2d(smem_u32(b_raw(s)), &tmap_b, i * kBK, brow, fb);
+            }
+        }
+    } else if (warp <= 3) {
+        // ---- lo tiles and MMAs
+        const int c = tid - 32;
+        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
+                               ((uint32_t)(kBM >> 4) << 24);
+        int i = 0, j = 0;                                // slices, tiles of this CTA
+        bool stop = false;
+        for (int t = blockIdx.x; t < ntiles_total && !stop; t += gridDim.x, j++) {
+            const int acc = j & 1;
+            const uint32_t d = tmem + (uint32_t)(acc * kAccCols);
+            // the accumulator's previous tile must have been read out
+            if (tid == 32 && j >= 2 && !role_wait(smem_u32(&acc_empty[acc]), (uint32_t)(j / 2 - 1) & 1u, vfail))
+                *vfail = 1;
+            for (int k = 0; k < nk; k++, i++) {
+                const int s = i % stages;
+                if (!role_wait(smem_u32(&full_bar[s]), (uint32_t)(i / stages) & 1u, vfail)) *vfail = 1;
+                split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), c, kConsumers);
+                split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), c, kConsumers);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // the named barrier, reducing every consumer's view of the failure
+                // flag so that all of them take the same branch
+                uint32_t any_fail;
+                asm volatile("{\n\t.reg .pred q, r;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+                             "bar.red.or.pred r, 1, %2, q;\n\tselp.u32 %0, 1, 0, r;\n\t}"
+                             : "=r"(any_fail) : "r"((uint32_t)*vfail), "n"(kConsumers) : "memory");
+                if (any_fail) { stop = true; break; }
+                if (tid == 32) {
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t ah = smem_u32(a_raw(s)), al = smem_u32(a_lo(s));
+                    const uint32_t bh = smem_u32(b_raw(s)), bl = smem_u32(b_lo(s));
+#pragma unroll
+                    for (int q = 0; q < kBK / 8; q++) {     // 8-deep K steps, 32 bytes apart in the swizzle row
+                        const uint64_t dah = sw128_desc(ah + 32 * q), dal = sw128_desc(al + 32 * q);
+                        const uint64_t dbh = sw128_desc(bh + 32 * q), dbl = sw128_desc(bl + 32 * q);
+#pragma unroll
+                        for (int e = 0; e < 3; e++) {
+                            const uint64_t da = e == 2 ? dal : dah, db = e == 1 ? dbl : dbh;
+                            const uint32_t accum = (k > 0 || q > 0 || e > 0) ? 1u : 0u;
+                            asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                                         :: "r"(d), "l"(da), "l"(db), "r"(idesc), "r"(accum));
+                        }
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(smem_u32(&mma_bar[s])) : "memory");
+                    if (k == nk - 1)
+                        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                     :: "r"(smem_u32(&acc_full[acc])) : "memory");
+                }
             }
         }
     } else {
-        // ---- consumers: lo tiles, then the MMAs (thread 32)
-        const int ct_ = tid - 32;
-        const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
-                               ((uint32_t)(kBM >> 4) << 24);
-        for (int i = 0; i < nk; i++) {
-            const int s = i % stages;
-            if (!mbar_wait(smem_u32(&full_bar[s]), (uint32_t)(i / stages) & 1u)) ok = false;
-            split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), ct_, kConsumers);
-            split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), ct_, kConsumers);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            if (!ok) atomicExch(&fail, 1);
-            asm volatile("bar.sync 1, %0;" :: "n"(kConsumers) : "memory");
-            if (*(volatile int *)&fail) { ok = false; break; }
-            if (tid == 32) {
-                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                const uint32_t ah = smem_u32(a_raw(s)), al = smem_u32(a_lo(s));
-                const uint32_t bh = smem_u32(b_raw(s)), bl = smem_u32(b_lo(s));
+        // ---- epilogue: warp 4 + q reads TMEM lanes 32 q .. 32 q + 31
+        const int q = warp - 4, lane = tid & 31;
+        int j = 0;
+        for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x, j++) {
+            const int acc = j & 1;
+            const bool got = role_wait(smem_u32(&acc_full[acc]), (uint32_t)(j / 2) & 1u, vfail);
+            if (!__all_sync(0xffffffffu, got)) { *vfail = 1; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const LegItem it = items[t / g.ntiles];
+            const int ct = t % g.ntiles;
+            const int row = 32 * q + lane;
+            const bool live = row < it.nr;
+            const int64_t o = tri_offset(it.m, g.T) + it.p + 2 * (int64_t)(it.r0 + row);
+            for (int c0 = 0; c0 < nt; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * kAccCols + c0);
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                             : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (live) {
 #pragma unroll
-                for (int k = 0; k < kBK / 8; k++) {        // 8-deep K steps, 32 bytes apart in the swizzle row
-                    const uint64_t dah = sw128_desc(ah + 32 * k), dal = sw128_desc(al + 32 * k);
-                    const uint64_t dbh = sw128_desc(bh + 32 * k), dbl = sw128_desc(bl + 32 * k);
-#pragma unroll
-                    for (int t = 0; t < 3; t++) {
-                        const uint64_t da = t == 2 ? dal : dah, db = t == 1 ? dbl : dbh;
-                        const uint32_t acc = (i > 0 || k > 0 || t > 0) ? 1u : 0u;
-                        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-                                     :: "r"(tmem), "l"(da), "l"(db), "r"(idesc), "r"(acc));
+                    for (int e = 0; e < 16; e++) {
+                        const int col = ct * nt + c0 + e;
+                        if (col < g.N) {
+                            const int part = col >= g.nlev, lev = part ? col - g.nlev : col;
+                            (part ? aim : are)[(int64_t)lev * g.os + o] = __uint_as_float(v[e]);
+                        }
                     }
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                             :: "r"(smem_u32(&mma_bar[s])) : "memory");
             }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(smem_u32(&acc_empty[acc])) : "memory");
         }
     }
-    if (!ok) atomicExch(&fail, 1);
     __syncthreads();
-    ok = !fail;
-    // every MMA has completed once the last slice's commit has arrived
-    if (ok && nk > 0) {
-        const int s = (nk - 1) % stages;
-        if (!mbar_wait(smem_u32(&mma_bar[s]), (uint32_t)((nk - 1) / stages) & 1u)) ok = false;
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (__syncthreads_and(ok)) {
-        // warp w holds rows 32 w .. 32 w + 31 of the tile in its TMEM lanes
-        const int row = 32 * warp + (tid & 31);
-        const bool live = row < it.nr;
-        const int64_t o = tri_offset(it.m, g.T) + it.p + 2 * (int64_t)(it.r0 + row);
-        for (int c0 = 0; c0 < nt; c0 += 16) {
-            uint32_t v[16];
-            const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0;
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                         : "r"(taddr));
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (live) {
-#pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const int c = ct * nt + c0 + q;
-                    if (c < g.N) {
-                        const int part = c >= g.nlev, lev = part ? c - g.nlev : c;
-                        (part ? aim : are)[(int64_t)lev * g.os + o] = __uint_as_float(v[q]);
-                    }
-                }
-            }
-        }
-    } else if (tid == 0) {
+    if (*vfail && tid == 0) {
         atomicExch(status, 1);
         // let copies and MMAs still in flight land before the CTA leaves
         for (int s = 0; s < stages; s++) {
@@ -324,7 +376,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(kTmemCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "n"(2 * kAccCols));
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
@@ -563,8 +615,9 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
     const size_t smem = mma_smem_bytes(g.nt);
     if (cudaFuncSetAttribute(legendre_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return ZFPX_ECUDA;
-    legendre_mma_kernel<<<(unsigned)nblk, kThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, mma_stages(g.nt),
-                                                                d_are, d_aim, p->d_status);
+    const int grid = (int)std::min<int64_t>(nblk, num_sms());      // persistent: one CTA per SM
+    legendre_mma_kernel<<<grid, kMmaThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, mma_stages(g.nt), (int)nblk,
+                                                          d_are, d_aim, p->d_status);
     count_launch();
     return check_launch();
 }
