@@ -141,7 +141,7 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
             int64_t x0, y0, z0;
             block_origin(g, b0 + lane, x0, y0, z0);
             uint64_t amax = 0;
-#pragma unroll 1
+#pragma unroll 8
             for (int r = 0; r < 64; r++) {
                 const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
                 const double x = __ldg(src + min(z0 + k, g.n[2] - 1) * g.s[2] + min(y0 + j, g.n[1] - 1) * g.s[1] +
@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
                 const int s1 = sh > 600 ? 600 : sh;
                 const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
                 const double f2 = __longlong_as_double((long long)(sh - s1 + 1023) << 52);
-#pragma unroll 1
+#pragma unroll 8
                 for (int r = 0; r < 64; r++)
                     v[r * 32] = __double2ll_rz((__longlong_as_double(v[r * 32]) * f1) * f2);
 #pragma unroll 1
@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
         if (lane >= nact) continue;
         const int64_t b = b0 + lane;
         const uint64_t *s64 = reinterpret_cast<const uint64_t *>(in) + b * g.rate;
-#pragma unroll 1
+#pragma unroll 4
         for (int i = 0; i < g.rate; i++) v[i * 32] = (int64_t)__ldg(s64 + i);
         v[g.rate * 32] = 0;
         int64_t x0, y0, z0;
@@ -307,10 +307,10 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
 #pragma unroll 1
             for (int k = 0; k < 4; k++)
                 for (int j = 0; j < 4; j++) lift_inv64(v + (16 * k + 4 * j) * 32, 1);
-#pragma unroll 1
+#pragma unroll 8
             for (int r = 0; r < 64; r++) v[r * 32] = __double_as_longlong(dequantize64(v[r * 32], e));
         }
-#pragma unroll 1
+#pragma unroll 8
         for (int r = 0; r < 64; r++) {
             const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
             if (x0 + i < g.n[0] && y0 + j < g.n[1] && z0 + k < g.n[2])
