@@ -393,6 +393,14 @@ ZFPX_API size_t zfpx_batch_field_bytes(zfpx_batch batch, int f);
 /* Launch shape used by later calls: warps per CTA (4 or 8) and CTAs per SM
  * (0 = as many as fit).  Picked by the autotuner; results never depend on it. */
 ZFPX_API int zfpx_batch_set_launch(zfpx_batch batch, int warps_per_cta, int ctas_per_sm);
+/* Work-unit size of 1-D items: a warp claims 32 x blocks_per_lane_1d
+ * consecutive 1-D blocks at a time, each lane coding blocks_per_lane_1d of
+ * them (1..64, default 8; 3-D units stay 32 blocks, one per lane).  Larger
+ * units spend fewer work claims and table searches per block, smaller ones
+ * balance short batches better.  Rebuilds the batch's work tables after
+ * waiting for the device to go idle.  Picked by the autotuner; results never
+ * depend on it.  Errors: ZFPX_EINVAL, ZFPX_ECUDA, ZFPX_ENOMEM. */
+ZFPX_API int zfpx_batch_set_unit_blocks(zfpx_batch batch, int blocks_per_lane_1d);
 ZFPX_API int zfpx_batch_encode(zfpx_batch batch, uint8_t *d_out, size_t cap, void *stream);
 ZFPX_API int zfpx_batch_decode(zfpx_batch batch, const uint8_t *d_in, size_t len, void *stream);
 
@@ -419,6 +427,9 @@ ZFPX_API int zfpx_server_create(zfpx_server *out, const int64_t *row_len, int nr
                                 int max_batch);
 ZFPX_API void zfpx_server_destroy(zfpx_server server);
 ZFPX_API int zfpx_server_set_launch(zfpx_server server, int warps_per_cta, int ctas_per_sm);
+/* The 1-D work-unit size of zfpx_batch_set_unit_blocks, for batches launched
+ * from then on.  Errors: ZFPX_EINVAL. */
+ZFPX_API int zfpx_server_set_unit_blocks(zfpx_server server, int blocks_per_lane_1d);
 ZFPX_API int zfpx_server_submit(zfpx_server server, const zfpx_field *request, int64_t *id);
 ZFPX_API int zfpx_server_pump(zfpx_server server, int *launched);
 ZFPX_API int zfpx_server_poll(zfpx_server server, int64_t *done, int max, int *ndone);

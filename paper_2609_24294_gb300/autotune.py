@@ -10,7 +10,9 @@ tuned once per machine type.
 Candidates:
 * batched ragged kernels: warps per CTA (4 or 8: the per-warp shared-memory
   tiles and the scheduling granularity) x CTAs per SM (1..as many as fit: fewer
-  CTAs leave more L1 per block, more CTAs hide latency);
+  CTAs leave more L1 per block, more CTAs hide latency); then, for batches
+  with 1-D fields, the 1-D blocks each lane codes per work unit (fewer claims
+  and searches per block against balance on short batches);
 * plan codec kernels (3-D blocks): consecutive 32-block units per warp (the
   blocks-per-warp knob; each CTA of the grid codes units-per-warp x warps
   units, so it also sets the grid size), per direction and rate.
@@ -25,6 +27,7 @@ import torch
 CACHE = os.environ.get("ZFPX_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "zfpx", "tune.json"))
 
 BATCH_CANDIDATES = [(4, 0), (4, 3), (4, 2), (8, 0), (8, 1)]
+LB1_CANDIDATES = (1, 4, 8, 16, 32)
 UPW_CANDIDATES = (1, 2, 3, 4, 8)
 
 
@@ -74,27 +77,42 @@ def time_call(fn, reps=3, warmup=1, stream=None):
     return statistics.median(ts)
 
 
-def tune_batch(batch, specs, out, candidates=None, reps=3, use_cache=True):
-    """Picks (warps per CTA, CTAs per SM) for batch encode + decode; returns
-    (choice, {choice: ms})."""
+def tune_batch(batch, specs, out, candidates=None, lb1_candidates=None, reps=3, use_cache=True):
+    """Picks (warps per CTA, CTAs per SM) for batch encode + decode, then the
+    1-D blocks per lane if any spec (nlev, dims, rate) has dims 1; returns
+    ((warps, ctas, blocks_per_lane_1d), {candidate: ms})."""
     key = batch_signature(batch, specs) + "@" + _device_key()
     cache = _load() if use_cache else {}
-    if use_cache and key in cache:
-        w, c = cache[key]["choice"]
+    if use_cache and key in cache and len(cache[key]["choice"]) == 3:
+        w, c, l1 = cache[key]["choice"]
         batch.set_launch(w, c)
-        return (w, c), cache[key].get("timings", {})
+        batch.set_unit_blocks(l1)
+        return (w, c, l1), cache[key].get("timings", {})
     timings = {}
+    both = lambda: (batch.encode(out), batch.decode(out))
+    batch.set_unit_blocks(8)
     for (w, c) in (candidates or BATCH_CANDIDATES):
         batch.set_launch(w, c)
-        ms = time_call(lambda: (batch.encode(out), batch.decode(out)), reps=reps)
-        timings["%d,%d" % (w, c)] = ms
+        timings["%d,%d" % (w, c)] = time_call(both, reps=reps)
     best = min(timings, key=timings.get)
     w, c = (int(v) for v in best.split(","))
     batch.set_launch(w, c)
+    l1, best_ms = 8, timings[best]
+    batch.set_unit_blocks(l1)
+    if any(s[1] == 1 for s in specs):
+        for cand in (lb1_candidates or LB1_CANDIDATES):
+            if cand == 8:
+                continue
+            batch.set_unit_blocks(cand)
+            ms = time_call(both, reps=reps)
+            timings["%d,%d,lb%d" % (w, c, cand)] = ms
+            if ms < best_ms:
+                l1, best_ms = cand, ms
+        batch.set_unit_blocks(l1)
     if use_cache:
-        cache[key] = {"choice": [w, c], "timings": timings}
+        cache[key] = {"choice": [w, c, l1], "timings": timings}
         _store(cache)
-    return (w, c), timings
+    return (w, c, l1), timings
 
 
 def plan_signature(plan, rate):

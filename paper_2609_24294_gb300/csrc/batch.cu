@@ -82,6 +82,7 @@ struct BatchGeom {
     int64_t nunits;
     GroupDev groups[kMaxGroups];
     int ngroups;
+    int lb1;              // 1-D units: 32 lb1 blocks, lb1 per lane
     uint32_t *ctr;        // ngroups work counters, zero at launch
 };
 
@@ -93,6 +94,16 @@ __device__ __forceinline__ int item_of_unit(const ItemDevB *items, int n, int64_
         if (__ldg(&items[mid].unit0) <= u) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// The 1-D plane tables, built by the CTA when the batch holds 1-D items.
+__device__ __forceinline__ void fill_plane4(const BatchGeom &bg, Plane4Tab &tab)
+{
+    bool any1 = false;
+    for (int i = 0; i < bg.ngroups; i++) any1 |= bg.groups[i].dims == 1;
+    if (!any1) return;
+    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    __syncthreads();
 }
 
 // Work distribution of the batch kernels.  A batch with no more units than
@@ -147,6 +158,16 @@ __device__ __forceinline__ int upper_index(const int64_t *pre, int n, int64_t b)
         if (__ldg(pre + mid) <= b) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// The same index for a block at most 31 past one whose index is `start` (a
+// unit's first block, searched once by the whole warp): a forward walk,
+// which on grids of rows several blocks long takes a step or two at most.
+__device__ __forceinline__ int upper_index_from(const int64_t *pre, int n, int start, int64_t b)
+{
+    int i = start;
+    while (i + 1 < n && __ldg(pre + i + 1) <= b) i++;
+    return i;
 }
 
 // 64 values of a 3-D block of row-quad q, x block bxi, levels z0.. (rows past
@@ -219,7 +240,7 @@ __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g,
     {
         // lanes past the unit's last block load that block and code nothing
         const int64_t bg = b0 + (valid ? lane : nact - 1) + f.b0;
-        const int q = upper_index(g.qpre, g.nq + 1, bg);
+        const int q = upper_index_from(g.qpre, g.nq + 1, upper_index(g.qpre, g.nq + 1, b0 + f.b0), bg);
         const int bxi = (int)(bg - __ldg(g.qpre + q));
         gather_quad(f, g, q, bxi, it.z0, it.nz, x);
     }
@@ -229,28 +250,49 @@ __device__ __forceinline__ void enc3_chunk(const FieldDevB &f, const GridDev &g,
     __syncwarp();
 }
 
+// A 1-D unit: 32 lb1 consecutive blocks, lane l coding blocks b0 + l + 32 j
+// (each step of j one coalesced load and store across the warp).  The
+// blocks go in groups of kLoads1 per lane, all of a group's loads issued
+// before any is coded, so a warp keeps that many 16-byte loads in flight.
+constexpr int kLoads1 = 4;
+
 template <int RATE>
-__device__ __forceinline__ void enc1_chunk(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                           int nact, int lane, uint8_t *out)
+__device__ __forceinline__ void enc1_unit(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
+                                          int lb1, int lane, const Plane4Tab &tab, uint8_t *out)
 {
-    if (lane >= nact) return;
-    const int64_t b = b0 + lane;
-    const int64_t bg = b + f.b0;
-    const int r = upper_index(g.rpre, g.nrows + 1, bg);
-    const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
-    const int len = __ldg(g.row_len + r);
-    const float *row = f.src + (int64_t)it.z0 * f.src_ls + (__ldg(g.row_off + r) - f.roff0);
-    float x[4];
-    if (f.vec && x0 + 4 <= len) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x0));
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-    } else {
+    int r = upper_index(g.rpre, g.nrows + 1, b0 + f.b0);
+    const float *src = f.src + (int64_t)it.z0 * f.src_ls - f.roff0;
+#pragma unroll 1
+    for (int j0 = 0; j0 < lb1; j0 += kLoads1) {
+        float x[kLoads1][4];
 #pragma unroll
-        for (int i = 0; i < 4; i++) x[i] = __ldg(row + min(x0 + i, len - 1));
+        for (int k = 0; k < kLoads1; k++) {
+            const int64_t b = b0 + 32 * (j0 + k) + lane;
+            x[k][0] = x[k][1] = x[k][2] = x[k][3] = 0.0f;
+            if (j0 + k >= lb1 || b >= it.nblocks) continue;
+            const int64_t bg = b + f.b0;
+            r = upper_index_from(g.rpre, g.nrows + 1, r, bg);
+            const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
+            const int len = __ldg(g.row_len + r);
+            const float *row = src + __ldg(g.row_off + r);
+            if (f.vec && x0 + 4 <= len) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(row + x0));
+                x[k][0] = v.x; x[k][1] = v.y; x[k][2] = v.z; x[k][3] = v.w;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++) x[k][i] = __ldg(row + min(x0 + i, len - 1));
+            }
+        }
+        uint64_t w[kLoads1];
+        encode_blocks1<RATE, kLoads1>(x, tab, w);
+#pragma unroll
+        for (int k = 0; k < kLoads1; k++) {
+            const int64_t b = b0 + 32 * (j0 + k) + lane;
+            if (j0 + k >= lb1 || b >= it.nblocks) continue;
+            if (RATE == 16) reinterpret_cast<uint64_t *>(out + it.out_off)[b] = w[k];
+            else reinterpret_cast<uint32_t *>(out + it.out_off)[b] = (uint32_t)w[k];
+        }
     }
-    const uint64_t w = encode_block1<RATE>(x);
-    if (RATE == 16) reinterpret_cast<uint64_t *>(out + it.out_off)[b] = w;
-    else reinterpret_cast<uint32_t *>(out + it.out_off)[b] = (uint32_t)w;
 }
 
 template <int WARPS>
@@ -258,6 +300,8 @@ __global__ void __launch_bounds__(32 * WARPS)
 batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
 {
     __shared__ enc3::Shared<16> sh[WARPS];             // rate-16 sized, shared by both rates
+    __shared__ Plane4Tab tab;
+    fill_plane4(bg, tab);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const enc3::View v = sh[wid].view();
     enc3::clear(v, lane, enc3::kWords<16>);
@@ -265,21 +309,22 @@ batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
     for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
         const ItemDevB it = bg.items[ii];
         const FieldDevB f = bg.fields[it.field];
-        const int64_t b0 = (c - it.unit0) * 32;
-        const int nact = (int)min((int64_t)32, it.nblocks - b0);
         if (G.dims == 3) {
+            const int64_t b0 = (c - it.unit0) * 32;
+            const int nact = (int)min((int64_t)32, it.nblocks - b0);
             if (G.rate == 8) enc3_chunk<8>(f, bg.grid, it, b0, nact, lane, v, out);
             else enc3_chunk<16>(f, bg.grid, it, b0, nact, lane, v, out);
         } else {
-            if (G.rate == 8) enc1_chunk<8>(f, bg.grid, it, b0, nact, lane, out);
-            else enc1_chunk<16>(f, bg.grid, it, b0, nact, lane, out);
+            const int64_t b0 = (c - it.unit0) * 32 * bg.lb1;
+            if (G.rate == 8) enc1_unit<8>(f, bg.grid, it, b0, bg.lb1, lane, tab, out);
+            else enc1_unit<16>(f, bg.grid, it, b0, bg.lb1, lane, tab, out);
         }
     });
 }
 
 template <int RATE>
 __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b,
-                                          int lane, const uint8_t *in, uint32_t *t32, uint64_t *wpl)
+                                          int start, int lane, const uint8_t *in, uint32_t *t32, uint64_t *wpl)
 {
     const uint4 *src4 = reinterpret_cast<const uint4 *>(in + it.out_off) + b * (RATE / 2);
 #pragma unroll
@@ -293,7 +338,7 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
 #pragma unroll
     for (int r = 0; r < kTileZeroRows<RATE>; r++) t32[(2 * RATE + r) * 32 + lane] = 0u;
     const int64_t bg = b + f.b0;
-    const int q = upper_index(g.qpre, g.nq + 1, bg);
+    const int q = upper_index_from(g.qpre, g.nq + 1, start, bg);
     const int bxi = (int)(bg - __ldg(g.qpre + q));
     float x[64];
     const StreamTile tile{t32, lane};
@@ -303,25 +348,42 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
 }
 
 template <int RATE>
-__device__ __forceinline__ void dec1_lane(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b,
-                                          const uint8_t *in)
+__device__ __forceinline__ void dec1_unit(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
+                                          int lb1, int lane, const Plane4Tab &tab, const uint8_t *in)
 {
-    uint64_t w;
-    if (RATE == 16) w = __ldg(reinterpret_cast<const uint64_t *>(in + it.out_off) + b);
-    else w = __ldg(reinterpret_cast<const uint32_t *>(in + it.out_off) + b);
-    float x[4];
-    decode_block1<RATE>(w, x);
-    const int64_t bg = b + f.b0;
-    const int r = upper_index(g.rpre, g.nrows + 1, bg);
-    const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
-    const int len = __ldg(g.row_len + r);
-    float *row = f.dst + (int64_t)it.z0 * f.dst_ls + (__ldg(g.row_off + r) - f.roff0);
-    if (f.vec && x0 + 4 <= len) {
-        *reinterpret_cast<float4 *>(row + x0) = make_float4(x[0], x[1], x[2], x[3]);
-    } else {
+    int r = upper_index(g.rpre, g.nrows + 1, b0 + f.b0);
+    float *dst = f.dst + (int64_t)it.z0 * f.dst_ls - f.roff0;
+#pragma unroll 1
+    for (int j0 = 0; j0 < lb1; j0 += kLoads1) {
+        uint64_t w[kLoads1];
 #pragma unroll
-        for (int i = 0; i < 4; i++)
-            if (x0 + i < len) row[x0 + i] = x[i];
+        for (int k = 0; k < kLoads1; k++) {
+            const int64_t b = b0 + 32 * (j0 + k) + lane;
+            w[k] = 0;
+            if (j0 + k >= lb1 || b >= it.nblocks) continue;
+            if (RATE == 16) w[k] = __ldg(reinterpret_cast<const uint64_t *>(in + it.out_off) + b);
+            else w[k] = __ldg(reinterpret_cast<const uint32_t *>(in + it.out_off) + b);
+        }
+        float xs[kLoads1][4];
+        decode_blocks1<RATE, kLoads1>(w, tab, xs);
+#pragma unroll
+        for (int k = 0; k < kLoads1; k++) {
+            const int64_t b = b0 + 32 * (j0 + k) + lane;
+            if (j0 + k >= lb1 || b >= it.nblocks) continue;
+            const float (&x)[4] = xs[k];
+            const int64_t bg = b + f.b0;
+            r = upper_index_from(g.rpre, g.nrows + 1, r, bg);
+            const int x0 = 4 * (int)(bg - __ldg(g.rpre + r));
+            const int len = __ldg(g.row_len + r);
+            float *row = dst + __ldg(g.row_off + r);
+            if (f.vec && x0 + 4 <= len) {
+                *reinterpret_cast<float4 *>(row + x0) = make_float4(x[0], x[1], x[2], x[3]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; i++)
+                    if (x0 + i < len) row[x0 + i] = x[i];
+            }
+        }
     }
 }
 
@@ -331,21 +393,24 @@ batch_decode_kernel(BatchGeom bg, const uint8_t *__restrict__ in)
 {
     __shared__ uint32_t stile[WARPS][(2 * 16 + 2) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
+    __shared__ Plane4Tab tab;
+    fill_plane4(bg, tab);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
         const ItemDevB it = bg.items[ii];
         const FieldDevB f = bg.fields[it.field];
-        const int64_t b0 = (c - it.unit0) * 32;
-        const int nact = (int)min((int64_t)32, it.nblocks - b0);
-        if (lane < nact) {
-            const int64_t b = b0 + lane;
-            if (G.dims == 3) {
-                if (G.rate == 8) dec3_lane<8>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
-                else dec3_lane<16>(f, bg.grid, it, b, lane, in, stile[wid], splanes[wid]);
-            } else {
-                if (G.rate == 8) dec1_lane<8>(f, bg.grid, it, b, in);
-                else dec1_lane<16>(f, bg.grid, it, b, in);
+        if (G.dims == 3) {
+            const int64_t b0 = (c - it.unit0) * 32;
+            const int nact = (int)min((int64_t)32, it.nblocks - b0);
+            if (lane < nact) {
+                const int start = upper_index(bg.grid.qpre, bg.grid.nq + 1, b0 + f.b0);
+                if (G.rate == 8) dec3_lane<8>(f, bg.grid, it, b0 + lane, start, lane, in, stile[wid], splanes[wid]);
+                else dec3_lane<16>(f, bg.grid, it, b0 + lane, start, lane, in, stile[wid], splanes[wid]);
             }
+        } else {
+            const int64_t b0 = (c - it.unit0) * 32 * bg.lb1;
+            if (G.rate == 8) dec1_unit<8>(f, bg.grid, it, b0, bg.lb1, lane, tab, in);
+            else dec1_unit<16>(f, bg.grid, it, b0, bg.lb1, lane, tab, in);
         }
         __syncwarp();
     });
@@ -443,9 +508,14 @@ int64_t field_stream_bytes(const GridHost &g, const zfpx_field &F, int r0, int r
     return items * field_item_blocks(g, F, r0, r1) * per_block;
 }
 
+// Blocks of one work unit: 32 for 3-D items (one per lane), 32 lb1 for 1-D.
+constexpr int kDefaultLb1 = 8;
+constexpr int kMaxLb1 = 64;
+inline int64_t unit_blocks(int dims, int lb1) { return dims == 3 ? 32 : 32 * (int64_t)lb1; }
+
 // Field and item descriptors of a set of fields whose streams start at the
 // given byte offsets; items grouped by (dims, rate) class.
-void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stream_off, int nfields,
+void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stream_off, int nfields, int lb1,
                 std::vector<FieldDevB> &fd, std::vector<ItemDevB> &items, int64_t &units,
                 std::vector<GroupDev> &groups)
 {
@@ -492,7 +562,7 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
             it.nz = std::min(step, F.nlev - z);
             it.pad = 0;
             items.push_back(it);
-            units += (blocks + 31) / 32;
+            units += (blocks + unit_blocks(F.dims, lb1) - 1) / unit_blocks(F.dims, lb1);
             ioff += blocks * per_block;
         }
     }
@@ -502,7 +572,8 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
     std::vector<double> work;
     for (const ItemDevB &it : items) {
         const FieldDevB &F = fd[it.field];
-        const int64_t n = (it.nblocks + 31) / 32;
+        const int64_t ub = unit_blocks(F.dims, lb1);
+        const int64_t n = (it.nblocks + ub - 1) / ub;
         if (groups.empty() || groups.back().dims != F.dims || groups.back().rate != F.rate) {
             GroupDev G;
             G.u0 = it.unit0; G.n = 0; G.dims = F.dims; G.rate = F.rate; G.cum1 = 1.0f; G.pad = 0;
@@ -510,7 +581,7 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
             work.push_back(0.0);
         }
         groups.back().n += n;
-        work.back() += (double)n * (F.dims == 3 ? 2048.0 : 128.0) * (F.rate == 16 ? 1.15 : 1.0);
+        work.back() += (double)n * (double)ub * (F.dims == 3 ? 64.0 : 4.0) * (F.rate == 16 ? 1.15 : 1.0);
     }
     double total = 0.0, acc = 0.0;
     for (double w : work) total += w;
@@ -521,9 +592,10 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
 }
 
 BatchGeom make_geom(const FieldDevB *d_fields, const ItemDevB *d_items, const GridDev &grid, int nitems,
-                    int64_t nunits, const std::vector<GroupDev> &groups, uint32_t *d_ctr)
+                    int64_t nunits, const std::vector<GroupDev> &groups, int lb1, uint32_t *d_ctr)
 {
     BatchGeom g;
+    g.lb1 = lb1;
     g.items = d_items;
     g.fields = d_fields;
     g.grid = grid;
@@ -568,6 +640,7 @@ struct zfpx_batch_s {
     int nitems = 0;
     int64_t nunits = 0;
     int warps = 4, ctas_per_sm = 0;     // 0 = as many as fit
+    int lb1 = zfpx::kDefaultLb1;        // 1-D blocks per lane of a unit
     zfpx::FieldDevB *d_fields = nullptr;
     zfpx::ItemDevB *d_items = nullptr;
     std::vector<zfpx::GroupDev> groups;
@@ -586,6 +659,23 @@ void zfpx_batch_destroy(zfpx_batch b)
     cudaFree(b->d_items);
     cudaFree(b->d_ctr);
     delete b;
+}
+
+// (Re)builds the batch's field and item tables for its current unit size.
+static int batch_work(zfpx_batch b)
+{
+    std::vector<FieldDevB> fd;
+    std::vector<ItemDevB> items;
+    build_work(b->grid, b->fields.data(), b->field_off.data(), (int)b->fields.size(), b->lb1, fd, items, b->nunits,
+               b->groups);
+    b->nitems = (int)items.size();
+    cudaFree(b->d_fields);
+    cudaFree(b->d_items);
+    b->d_fields = nullptr;
+    b->d_items = nullptr;
+    int rc = upload(&b->d_fields, fd);
+    if (!rc) rc = upload(&b->d_items, items);
+    return rc;
 }
 
 int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const zfpx_field *fields, int nfields)
@@ -610,13 +700,8 @@ int zfpx_batch_create(zfpx_batch *out, const int64_t *row_len, int nrows, const 
         off = (off + b->field_bytes[f] + 255) / 256 * 256;
     }
     b->total = off;
-    std::vector<FieldDevB> fd;
-    std::vector<ItemDevB> items;
-    build_work(b->grid, fields, b->field_off.data(), nfields, fd, items, b->nunits, b->groups);
-    b->nitems = (int)items.size();
     rc = upload_grid(b->grid);
-    if (!rc) rc = upload(&b->d_fields, fd);
-    if (!rc) rc = upload(&b->d_items, items);
+    if (!rc) rc = batch_work(b);
     if (!rc && cudaMalloc((void **)&b->d_ctr, 2 * kMaxGroups * sizeof(uint32_t)) != cudaSuccess) rc = ZFPX_ENOMEM;
     if (rc) { zfpx_batch_destroy(b); return rc; }
     *out = b;
@@ -645,12 +730,22 @@ int zfpx_batch_set_launch(zfpx_batch b, int warps_per_cta, int ctas_per_sm)
     return ZFPX_OK;
 }
 
+int zfpx_batch_set_unit_blocks(zfpx_batch b, int blocks_per_lane_1d)
+{
+    if (!b || blocks_per_lane_1d < 1 || blocks_per_lane_1d > kMaxLb1) return ZFPX_EINVAL;
+    if (blocks_per_lane_1d == b->lb1) return ZFPX_OK;
+    // the tables in use by launches still in flight stay valid until they finish
+    if (cudaDeviceSynchronize() != cudaSuccess) return ZFPX_ECUDA;
+    b->lb1 = blocks_per_lane_1d;
+    return batch_work(b);
+}
+
 // Geometry for one launch; its work counters are zeroed on the stream first.
 static int batch_geom(zfpx_batch b, bool encode, cudaStream_t st, BatchGeom &g)
 {
     uint32_t *ctr = b->d_ctr + (encode ? 0 : kMaxGroups);
     if (cudaMemsetAsync(ctr, 0, kMaxGroups * sizeof(uint32_t), st) != cudaSuccess) return ZFPX_ECUDA;
-    g = make_geom(b->d_fields, b->d_items, b->grid.dev(), b->nitems, b->nunits, b->groups, ctr);
+    g = make_geom(b->d_fields, b->d_items, b->grid.dev(), b->nitems, b->nunits, b->groups, b->lb1, ctr);
     return ZFPX_OK;
 }
 
@@ -764,6 +859,7 @@ struct zfpx_server_s {
     int64_t next_id = 1;
     int max_batch = 64;
     int warps = 4, ctas_per_sm = 0;
+    int lb1 = zfpx::kDefaultLb1;
     std::deque<int64_t> completed;
     int64_t batches = 0;
 };
@@ -821,6 +917,13 @@ int zfpx_server_set_launch(zfpx_server s, int warps_per_cta, int ctas_per_sm)
     if (!s || (warps_per_cta != 4 && warps_per_cta != 8) || ctas_per_sm < 0) return ZFPX_EINVAL;
     s->warps = warps_per_cta;
     s->ctas_per_sm = ctas_per_sm;
+    return ZFPX_OK;
+}
+
+int zfpx_server_set_unit_blocks(zfpx_server s, int blocks_per_lane_1d)
+{
+    if (!s || blocks_per_lane_1d < 1 || blocks_per_lane_1d > kMaxLb1) return ZFPX_EINVAL;
+    s->lb1 = blocks_per_lane_1d;              // applies to batches launched from now on
     return ZFPX_OK;
 }
 
@@ -899,7 +1002,7 @@ int zfpx_server_pump(zfpx_server s, int *launched)
     std::vector<ItemDevB> items;
     std::vector<GroupDev> groups;
     int64_t units = 0;
-    build_work(s->grid, fields.data(), soff.data(), (int)fields.size(), fd, items, units, groups);
+    build_work(s->grid, fields.data(), soff.data(), (int)fields.size(), s->lb1, fd, items, units, groups);
     // descriptors: fields, items, then zeroed work counters (encode, decode)
     const size_t fbytes = fd.size() * sizeof(FieldDevB);
     const size_t ioff = (fbytes + 255) / 256 * 256;
@@ -914,8 +1017,9 @@ int zfpx_server_pump(zfpx_server s, int *launched)
     uint32_t *ctr = reinterpret_cast<uint32_t *>(sl.d_desc + coff);
     const FieldDevB *dfd = reinterpret_cast<const FieldDevB *>(sl.d_desc);
     const ItemDevB *dit = reinterpret_cast<const ItemDevB *>(sl.d_desc + ioff);
-    const BatchGeom ge = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, ctr);
-    const BatchGeom gd = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, ctr + kMaxGroups);
+    const BatchGeom ge = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1, ctr);
+    const BatchGeom gd = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1,
+                                   ctr + kMaxGroups);
     int rc = launch_batch(ge, s->warps, s->ctas_per_sm, true, nullptr, s->d_arena, sl.stream);
     if (!rc) rc = launch_batch(gd, s->warps, s->ctas_per_sm, false, s->d_arena, nullptr, sl.stream);
     if (!rc && cudaEventRecord(sl.done, sl.stream) != cudaSuccess) rc = ZFPX_ECUDA;

@@ -266,6 +266,9 @@ template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 encode1_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
 {
+    __shared__ Plane4Tab tab;
+    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
@@ -295,7 +298,7 @@ encode1_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
 #pragma unroll
             for (int i = 0; i < 4; i++) r[i] = __ldg(row + (int64_t)min(x0 + i, nx - 1) * g.ss[0]);
         }
-        const uint64_t w = encode_block1<RATE>(r);
+        const uint64_t w = encode_block1<RATE>(r, tab);
         if (RATE == 16) reinterpret_cast<uint64_t *>(out + boff)[b] = w;
         else reinterpret_cast<uint32_t *>(out + boff)[b] = (uint32_t)w;
     }
@@ -305,6 +308,9 @@ template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
+    __shared__ Plane4Tab tab;
+    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * kWarps;
     const int64_t gw = (int64_t)blockIdx.x * kWarps + wid;
@@ -326,7 +332,7 @@ decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         if (RATE == 16) w = __ldg(reinterpret_cast<const uint64_t *>(in + boff) + b);
         else w = __ldg(reinterpret_cast<const uint32_t *>(in + boff) + b);
         float v[4];
-        decode_block1<RATE>(w, v);
+        decode_block1<RATE>(w, v, tab);
         const int bxi = b % bxn, t = b / bxn;
         const int y = t % byn, z = t / byn;
         const int x0 = 4 * bxi;

@@ -931,64 +931,174 @@ struct WordReader {
     ZFPX_HD void skip(int k) { off += k; }
 };
 
-template <int RATE>
-ZFPX_HD uint64_t encode_block1(const float (&x)[4])
+// With four coefficients a plane's code depends only on n (significant
+// coefficients, 0..4) and its four bits X (encoding) or the next seven stream
+// bits (decoding; no plane of four takes more).  The coders look planes up in
+// a table built from code_plane / decode_plane at launch: encoder entry
+// (n, X) = code bits 0..6, length bits 7..9, new n bits 10..12; decoder entry
+// (n, w7) = X bits 0..3, length bits 4..6, new n bits 7..9.
+// The encoder's output is the first 4 RATE bits of the unbounded code
+// (code_plane only ever cuts a plane short), so its loop just stops at the
+// budget.  For a plane the budget cuts after r bits the decoder looks up the
+// window with the bits from r on cleared: zeros past the budget add no one
+// except, when n < 4, the implied one of coefficient 3, which needs the whole
+// plane and so is dropped; what is left is what reading stops at the budget
+// gives.  Both run K blocks of a lane in lockstep so that their table
+// lookups, which each plane's successor waits for, overlap.
+struct Plane4Tab {
+    uint16_t enc[5 * 16];
+    uint16_t dec[5 * 128];
+};
+constexpr int kPlane4Entries = 5 * 16 + 5 * 128;
+
+ZFPX_HD uint16_t plane4_enc_entry(int n, uint32_t X)
 {
-    uint32_t amax = 0;
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const uint32_t a = f2u(x[i]) & 0x7fffffffu;
-        amax = a > amax ? a : amax;
-    }
-    const int E = (int)(amax >> 23);
     RegWriter wr{0ull, 0};
-    if (amax < 0x00400000u || E == 255) return 0ull;
-    const QuantScale qs(E);
-    int32_t q0 = qs(x[0]), q1 = qs(x[1]), q2 = qs(x[2]), q3 = qs(x[3]);
-    lift_fwd(q0, q1, q2, q3);
-    const uint32_t u0 = to_negabinary(q0), u1 = to_negabinary(q1);
-    const uint32_t u2 = to_negabinary(q2), u3 = to_negabinary(q3);
-    wr.put(1ull | ((uint64_t)(E + 1) << 1), 9);
-    int n = 0, R = 4 * RATE - 9;
+    int nn = n, R = 64;
+    code_plane<4>(wr, X, nn, R);
+    return (uint16_t)((uint32_t)wr.acc | ((uint32_t)wr.nb << 7) | ((uint32_t)nn << 10));
+}
+
+ZFPX_HD uint16_t plane4_dec_entry(int n, uint32_t w7)
+{
+    WordReader rd{w7, 0};
+    int nn = n, R = 64;
+    const uint32_t X = (uint32_t)decode_plane<4>(rd, nn, R);
+    return (uint16_t)(X | ((uint32_t)rd.off << 4) | ((uint32_t)nn << 7));
+}
+
+// Entry i of the concatenated tables (0 <= i < kPlane4Entries), for a fill
+// spread over a CTA's threads.
+ZFPX_HD void plane4_fill(Plane4Tab &t, int i)
+{
+    if (i < 80) t.enc[i] = plane4_enc_entry(i >> 4, (uint32_t)i & 15u);
+    else if (i < kPlane4Entries) t.dec[i - 80] = plane4_dec_entry((i - 80) >> 7, (uint32_t)(i - 80) & 127u);
+}
+
+// Encodes K blocks x[b][0..3]; w[b] = the block's 4 RATE bits.
+template <int RATE, int K>
+ZFPX_HD void encode_blocks1(const float (&x)[K][4], const Plane4Tab &tab, uint64_t (&w)[K])
+{
+    constexpr int END = 4 * RATE;
+    uint32_t u[K][4];
+    int pos[K], n[K];
 #pragma unroll
+    for (int b = 0; b < K; b++) {
+        uint32_t amax = 0;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const uint32_t a = f2u(x[b][i]) & 0x7fffffffu;
+            amax = a > amax ? a : amax;
+        }
+        const int E = (int)(amax >> 23);
+        const bool zero = amax < 0x00400000u || E == 255;          // a single 0 bit
+        const QuantScale qs(zero ? 127 : E);
+        int32_t q0 = qs(x[b][0]), q1 = qs(x[b][1]), q2 = qs(x[b][2]), q3 = qs(x[b][3]);
+        lift_fwd(q0, q1, q2, q3);
+        u[b][0] = to_negabinary(q0); u[b][1] = to_negabinary(q1);
+        u[b][2] = to_negabinary(q2); u[b][3] = to_negabinary(q3);
+        w[b] = zero ? 0ull : 1ull | ((uint64_t)(E + 1) << 1);      // header, 9 bits
+        pos[b] = zero ? END : 9;
+        n[b] = 0;
+    }
+#pragma unroll 1
     for (int k = 31; k >= 0; k--) {
-        if (R > 0) {
-            const uint64_t X = ((u0 >> k) & 1u) | (((u1 >> k) & 1u) << 1) | (((u2 >> k) & 1u) << 2) |
-                               (((u3 >> k) & 1u) << 3);
-            code_plane<4>(wr, X, n, R);
+        bool more = false;
+#pragma unroll
+        for (int b = 0; b < K; b++) {
+            if (pos[b] >= END) continue;
+            const uint32_t X = ((u[b][0] >> k) & 1u) | (((u[b][1] >> k) & 1u) << 1) | (((u[b][2] >> k) & 1u) << 2) |
+                               (((u[b][3] >> k) & 1u) << 3);
+            const uint32_t e = tab.enc[n[b] * 16 + (int)X];
+            w[b] |= (uint64_t)(e & 127u) << pos[b];                // pos < END <= 64
+            pos[b] += (int)((e >> 7) & 7u);
+            n[b] = (int)(e >> 10);
+            more |= pos[b] < END;
+        }
+        if (!more) break;
+    }
+#pragma unroll
+    for (int b = 0; b < K; b++) w[b] &= low_mask(END);
+}
+
+// Decodes K blocks from their 4 RATE-bit words.
+template <int RATE, int K>
+ZFPX_HD void decode_blocks1(const uint64_t (&win)[K], const Plane4Tab &tab, float (&x)[K][4])
+{
+    constexpr int END = 4 * RATE;
+    uint64_t w[K];
+    uint32_t u[K][4];
+    int pos[K], n[K];
+#pragma unroll
+    for (int b = 0; b < K; b++) {
+        w[b] = win[b] & low_mask(END);
+        pos[b] = (w[b] & 1ull) ? 9 : END;
+        n[b] = 0;
+        u[b][0] = u[b][1] = u[b][2] = u[b][3] = 0u;
+    }
+#pragma unroll 1
+    for (int k = 31; k >= 0; k--) {
+        bool more = false;
+#pragma unroll
+        for (int b = 0; b < K; b++) {
+            if (pos[b] >= END) continue;
+            const int r = END - pos[b];
+            uint32_t w7 = (uint32_t)(w[b] >> pos[b]) & 127u;       // pos < END <= 64
+            if (r < 7) w7 &= (1u << r) - 1u;
+            const uint32_t d = tab.dec[n[b] * 128 + (int)w7];
+            uint32_t X = d & 15u;
+            const int len = (int)((d >> 4) & 7u);
+            if (len > r) {                                         // the budget cuts this plane
+                if (n[b] < 4) X &= 7u;
+                pos[b] = END;
+            } else {
+                pos[b] += len;
+                n[b] = (int)(d >> 7);
+            }
+            u[b][0] |= (X & 1u) << k;
+            u[b][1] |= ((X >> 1) & 1u) << k;
+            u[b][2] |= ((X >> 2) & 1u) << k;
+            u[b][3] |= ((X >> 3) & 1u) << k;
+            more |= pos[b] < END;
+        }
+        if (!more) break;
+    }
+#pragma unroll
+    for (int b = 0; b < K; b++) {
+        if (!(w[b] & 1ull)) {
+            x[b][0] = x[b][1] = x[b][2] = x[b][3] = 0.0f;
+            continue;
+        }
+        const int e = (int)((w[b] >> 1) & 0xffu);
+        int32_t q0 = from_negabinary(u[b][0]), q1 = from_negabinary(u[b][1]);
+        int32_t q2 = from_negabinary(u[b][2]), q3 = from_negabinary(u[b][3]);
+        lift_inv(q0, q1, q2, q3);
+        if (e >= 31) {
+            const float sc = dequant_scale(e);
+            x[b][0] = dequantize_fast(q0, sc); x[b][1] = dequantize_fast(q1, sc);
+            x[b][2] = dequantize_fast(q2, sc); x[b][3] = dequantize_fast(q3, sc);
+        } else {
+            x[b][0] = dequantize_small(q0, e); x[b][1] = dequantize_small(q1, e);
+            x[b][2] = dequantize_small(q2, e); x[b][3] = dequantize_small(q3, e);
         }
     }
-    return wr.acc;
 }
 
 template <int RATE>
-ZFPX_HD void decode_block1(uint64_t w, float (&x)[4])
+ZFPX_HD uint64_t encode_block1(const float (&x)[4], const Plane4Tab &tab)
 {
-    x[0] = x[1] = x[2] = x[3] = 0.0f;
-    if (!(w & 1ull)) return;
-    const int e = (int)((w >> 1) & 0xffu);
-    WordReader rd{w, 9};
-    uint32_t u[4] = {0u, 0u, 0u, 0u};
-    int n = 0, R = 4 * RATE - 9;
-#pragma unroll
-    for (int k = 31; k >= 0; k--) {
-        if (R > 0) {
-            const uint64_t X = decode_plane<4>(rd, n, R);
-#pragma unroll
-            for (int i = 0; i < 4; i++) u[i] |= (uint32_t)((X >> i) & 1ull) << k;
-        }
-    }
-    int32_t q0 = from_negabinary(u[0]), q1 = from_negabinary(u[1]);
-    int32_t q2 = from_negabinary(u[2]), q3 = from_negabinary(u[3]);
-    lift_inv(q0, q1, q2, q3);
-    if (e >= 31) {
-        const float sc = dequant_scale(e);
-        x[0] = dequantize_fast(q0, sc); x[1] = dequantize_fast(q1, sc);
-        x[2] = dequantize_fast(q2, sc); x[3] = dequantize_fast(q3, sc);
-    } else {
-        x[0] = dequantize_small(q0, e); x[1] = dequantize_small(q1, e);
-        x[2] = dequantize_small(q2, e); x[3] = dequantize_small(q3, e);
-    }
+    const float (&xx)[1][4] = reinterpret_cast<const float (&)[1][4]>(x);
+    uint64_t w[1];
+    encode_blocks1<RATE, 1>(xx, tab, w);
+    return w[0];
+}
+
+template <int RATE>
+ZFPX_HD void decode_block1(uint64_t w, float (&x)[4], const Plane4Tab &tab)
+{
+    const uint64_t win[1] = {w};
+    float (&xx)[1][4] = reinterpret_cast<float (&)[1][4]>(x);
+    decode_blocks1<RATE, 1>(win, tab, xx);
 }
 
 }  // namespace blk

@@ -28,6 +28,9 @@ class Server:
     def set_launch(self, warps_per_cta, ctas_per_sm=0):
         z._check(z.lib().zfpx_server_set_launch(self._h, warps_per_cta, ctas_per_sm), "zfpx_server_set_launch")
 
+    def set_unit_blocks(self, blocks_per_lane_1d):
+        z._check(z.lib().zfpx_server_set_unit_blocks(self._h, blocks_per_lane_1d), "zfpx_server_set_unit_blocks")
+
     def submit(self, src, lev_stride, nlev, dims, rate, row0, row1):
         """src: device pointer (int) of level 0, first point of row row0."""
         f = z.Field()

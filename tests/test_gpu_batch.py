@@ -22,8 +22,8 @@ SPECS = [(9, "temperature", 3, 8), (6, "power", 3, 16), (1, "humidity", 1, 8), (
          (2, "power", 1, 16), (3, "temperature", 3, 16)]
 
 
-@pytest.mark.parametrize("N,warps", [(6, 4), (13, 8)])
-def test_batch_matches_oracle(z, N, warps):
+@pytest.mark.parametrize("N,warps,lb1", [(6, 4, 8), (13, 8, 8), (13, 4, 1), (13, 4, 3), (6, 8, 64)])
+def test_batch_matches_oracle(z, N, warps, lb1):
     lens = og.row_lengths(N)
     if N == 13:
         lens = lens[:-2]                         # a partial last row-quad
@@ -38,6 +38,7 @@ def test_batch_matches_oracle(z, N, warps):
         specs.append((nlev, dims, rate))
     b = z.Batch(lens, [(s, d, dims, rate) for s, d, (_, dims, rate) in zip(srcs, dsts, specs)])
     b.set_launch(warps, 0)
+    b.set_unit_blocks(lb1)                      # 1-D blocks per lane of a work unit
     ref = ob.encode_batch(host, lens, specs)
     assert b.nbytes() == ref.size
     out = torch.zeros(b.nbytes(), dtype=torch.uint8, device="cuda")

@@ -55,6 +55,12 @@ def test_alone_equals_mix_and_oracle(z):
         assert sa.tobytes() == sm.tobytes(), i
         assert np.array_equal(va.view(np.uint32), vm.view(np.uint32)), i
     assert np.all(lat > 0) and st1["arena_used"] == 0 and st1["queued"] == 0
+    # another 1-D work-unit size changes nothing either
+    srv.set_unit_blocks(2)
+    _, _, _, mixed2 = serve.run_requests(srv, calls, arrivals=arrivals, keep_results=True)
+    for i, ((sa, va), (sm, vm)) in enumerate(zip(alone, mixed2)):
+        assert sa.tobytes() == sm.tobytes(), i
+        assert np.array_equal(va.view(np.uint32), vm.view(np.uint32)), i
     # oracle on a sample of requests
     offs = np.concatenate([[0], np.cumsum(lens)])
     for i in range(0, len(calls), 7):
