@@ -390,12 +390,13 @@ ZFPX_API void zfpx_batch_destroy(zfpx_batch batch);
 ZFPX_API size_t zfpx_batch_bytes(zfpx_batch batch);
 ZFPX_API int64_t zfpx_batch_field_offset(zfpx_batch batch, int f);
 ZFPX_API size_t zfpx_batch_field_bytes(zfpx_batch batch, int f);
-/* Launch shape used by later calls: warps per CTA (4 or 8) and CTAs per SM
- * (0 = as many as fit).  Picked by the autotuner; results never depend on it. */
+/* Launch shape used by later calls: warps per CTA (2, 3, 4 or 8; default 3)
+ * and CTAs per SM (0 = as many as fit, the default).  Picked by the autotuner;
+ * results never depend on it. */
 ZFPX_API int zfpx_batch_set_launch(zfpx_batch batch, int warps_per_cta, int ctas_per_sm);
 /* Work-unit size of 1-D items: a warp claims 32 x blocks_per_lane_1d
  * consecutive 1-D blocks at a time, each lane coding blocks_per_lane_1d of
- * them (1..64, default 8; 3-D units stay 32 blocks, one per lane).  Larger
+ * them (1..64, default 16; 3-D units stay 32 blocks, one per lane).  Larger
  * units spend fewer work claims and table searches per block, smaller ones
  * balance short batches better.  Rebuilds the batch's work tables after
  * waiting for the device to go idle.  Picked by the autotuner; results never

@@ -8,8 +8,8 @@ by the workload's signature, the GPU name and its SM count, so a workload is
 tuned once per machine type.
 
 Candidates:
-* batched ragged kernels: warps per CTA (4 or 8: the per-warp shared-memory
-  tiles and the scheduling granularity) x CTAs per SM (1..as many as fit: fewer
+* batched ragged kernels: warps per CTA (2, 3, 4 or 8: the per-warp
+  shared-memory tiles and the scheduling granularity) x CTAs per SM (1..as many as fit: fewer
   CTAs leave more L1 per block, more CTAs hide latency); then, for batches
   with 1-D fields, the 1-D blocks each lane codes per work unit (fewer claims
   and searches per block against balance on short batches);
@@ -26,8 +26,9 @@ import torch
 
 CACHE = os.environ.get("ZFPX_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "zfpx", "tune.json"))
 
-BATCH_CANDIDATES = [(4, 0), (4, 3), (4, 2), (8, 0), (8, 1)]
-LB1_CANDIDATES = (1, 4, 8, 16, 32)
+BATCH_CANDIDATES = [(3, 0), (2, 0), (4, 0), (3, 3), (8, 0)]
+LB1_DEFAULT = 16
+LB1_CANDIDATES = (2, 4, 8, 16, 32)
 UPW_CANDIDATES = (1, 2, 3, 4, 8)
 
 
@@ -90,18 +91,17 @@ def tune_batch(batch, specs, out, candidates=None, lb1_candidates=None, reps=3, 
         return (w, c, l1), cache[key].get("timings", {})
     timings = {}
     both = lambda: (batch.encode(out), batch.decode(out))
-    batch.set_unit_blocks(8)
+    batch.set_unit_blocks(LB1_DEFAULT)
     for (w, c) in (candidates or BATCH_CANDIDATES):
         batch.set_launch(w, c)
         timings["%d,%d" % (w, c)] = time_call(both, reps=reps)
     best = min(timings, key=timings.get)
     w, c = (int(v) for v in best.split(","))
     batch.set_launch(w, c)
-    l1, best_ms = 8, timings[best]
-    batch.set_unit_blocks(l1)
+    l1, best_ms = LB1_DEFAULT, timings[best]
     if any(s[1] == 1 for s in specs):
         for cand in (lb1_candidates or LB1_CANDIDATES):
-            if cand == 8:
+            if cand == LB1_DEFAULT:
                 continue
             batch.set_unit_blocks(cand)
             ms = time_call(both, reps=reps)

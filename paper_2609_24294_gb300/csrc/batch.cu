@@ -96,13 +96,14 @@ __device__ __forceinline__ int item_of_unit(const ItemDevB *items, int n, int64_
     return lo;
 }
 
-// The 1-D plane tables, built by the CTA when the batch holds 1-D items.
-__device__ __forceinline__ void fill_plane4(const BatchGeom &bg, Plane4Tab &tab)
+// A 1-D plane table, built by the CTA when the batch holds 1-D items.
+template <class Tab>
+__device__ __forceinline__ void fill_plane4(const BatchGeom &bg, Tab &tab)
 {
     bool any1 = false;
     for (int i = 0; i < bg.ngroups; i++) any1 |= bg.groups[i].dims == 1;
     if (!any1) return;
-    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    plane4_fill(tab, threadIdx.x, blockDim.x);
     __syncthreads();
 }
 
@@ -258,7 +259,7 @@ constexpr int kLoads1 = 4;
 
 template <int RATE>
 __device__ __forceinline__ void enc1_unit(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                          int lb1, int lane, const Plane4Tab &tab, uint8_t *out)
+                                          int lb1, int lane, const Plane4Enc &tab, uint8_t *out)
 {
     int r = upper_index(g.rpre, g.nrows + 1, b0 + f.b0);
     const float *src = f.src + (int64_t)it.z0 * f.src_ls - f.roff0;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(32 * WARPS)
 batch_encode_kernel(BatchGeom bg, uint8_t *__restrict__ out)
 {
     __shared__ enc3::Shared<16> sh[WARPS];             // rate-16 sized, shared by both rates
-    __shared__ Plane4Tab tab;
+    __shared__ Plane4Enc tab;
     fill_plane4(bg, tab);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const enc3::View v = sh[wid].view();
@@ -349,7 +350,7 @@ __device__ __forceinline__ void dec3_lane(const FieldDevB &f, const GridDev &g, 
 
 template <int RATE>
 __device__ __forceinline__ void dec1_unit(const FieldDevB &f, const GridDev &g, const ItemDevB &it, int64_t b0,
-                                          int lb1, int lane, const Plane4Tab &tab, const uint8_t *in)
+                                          int lb1, int lane, const Plane4Dec &tab, const uint8_t *in)
 {
     int r = upper_index(g.rpre, g.nrows + 1, b0 + f.b0);
     float *dst = f.dst + (int64_t)it.z0 * f.dst_ls - f.roff0;
@@ -393,7 +394,7 @@ batch_decode_kernel(BatchGeom bg, const uint8_t *__restrict__ in)
 {
     __shared__ uint32_t stile[WARPS][(2 * 16 + 2) * 32];
     __shared__ uint64_t splanes[WARPS][32 * 32];
-    __shared__ Plane4Tab tab;
+    __shared__ Plane4Dec tab;
     fill_plane4(bg, tab);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for_each_unit(bg, lane, [&](const GroupDev &G, int64_t c, int ii) {
@@ -509,7 +510,7 @@ int64_t field_stream_bytes(const GridHost &g, const zfpx_field &F, int r0, int r
 }
 
 // Blocks of one work unit: 32 for 3-D items (one per lane), 32 lb1 for 1-D.
-constexpr int kDefaultLb1 = 8;
+constexpr int kDefaultLb1 = 16;
 constexpr int kMaxLb1 = 64;
 inline int64_t unit_blocks(int dims, int lb1) { return dims == 3 ? 32 : 32 * (int64_t)lb1; }
 
@@ -607,24 +608,39 @@ BatchGeom make_geom(const FieldDevB *d_fields, const ItemDevB *d_items, const Gr
     return g;
 }
 
+// Warps per CTA the batch kernels are built for: fewer warps per CTA let
+// more CTAs share an SM's shared memory (the encoder's per-warp storage is
+// about 15 KB).
+bool batch_warps_ok(int warps) { return warps == 2 || warps == 3 || warps == 4 || warps == 8; }
+
+template <int W>
+const void *batch_kernel(bool encode)
+{
+    return encode ? (const void *)batch_encode_kernel<W> : (const void *)batch_decode_kernel<W>;
+}
+
+template <int W>
+void launch_w(bool encode, int grid, const BatchGeom &g, const uint8_t *in, uint8_t *out, cudaStream_t st)
+{
+    if (encode) batch_encode_kernel<W><<<grid, 32 * W, 0, st>>>(g, out);
+    else batch_decode_kernel<W><<<grid, 32 * W, 0, st>>>(g, in);
+}
+
 int launch_batch(const BatchGeom &g, int warps, int ctas_per_sm, bool encode, const uint8_t *in, uint8_t *out,
                  cudaStream_t st)
 {
     if (g.nunits == 0) return ZFPX_OK;
-    const void *fn = nullptr;
-    if (encode) fn = warps == 8 ? (const void *)batch_encode_kernel<8> : (const void *)batch_encode_kernel<4>;
-    else fn = warps == 8 ? (const void *)batch_decode_kernel<8> : (const void *)batch_decode_kernel<4>;
+    if (!batch_warps_ok(warps)) return ZFPX_EINVAL;
+    const void *fn = warps == 2 ? batch_kernel<2>(encode) : warps == 3 ? batch_kernel<3>(encode)
+                   : warps == 8 ? batch_kernel<8>(encode) : batch_kernel<4>(encode);
     const int fit = occupancy(fn, 32 * warps);
     const int per_sm = ctas_per_sm > 0 ? std::min(ctas_per_sm, fit) : fit;
     const int64_t want = (g.nunits + warps - 1) / warps;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * per_sm));
-    if (encode) {
-        if (warps == 8) batch_encode_kernel<8><<<grid, 256, 0, st>>>(g, out);
-        else batch_encode_kernel<4><<<grid, 128, 0, st>>>(g, out);
-    } else {
-        if (warps == 8) batch_decode_kernel<8><<<grid, 256, 0, st>>>(g, in);
-        else batch_decode_kernel<4><<<grid, 128, 0, st>>>(g, in);
-    }
+    if (warps == 2) launch_w<2>(encode, grid, g, in, out, st);
+    else if (warps == 3) launch_w<3>(encode, grid, g, in, out, st);
+    else if (warps == 8) launch_w<8>(encode, grid, g, in, out, st);
+    else launch_w<4>(encode, grid, g, in, out, st);
     count_launch();
     return check_launch();
 }
@@ -639,7 +655,7 @@ struct zfpx_batch_s {
     int64_t total = 0;
     int nitems = 0;
     int64_t nunits = 0;
-    int warps = 4, ctas_per_sm = 0;     // 0 = as many as fit
+    int warps = 3, ctas_per_sm = 0;     // 0 = as many as fit
     int lb1 = zfpx::kDefaultLb1;        // 1-D blocks per lane of a unit
     zfpx::FieldDevB *d_fields = nullptr;
     zfpx::ItemDevB *d_items = nullptr;
@@ -724,7 +740,7 @@ size_t zfpx_batch_field_bytes(zfpx_batch b, int f)
 
 int zfpx_batch_set_launch(zfpx_batch b, int warps_per_cta, int ctas_per_sm)
 {
-    if (!b || (warps_per_cta != 4 && warps_per_cta != 8) || ctas_per_sm < 0) return ZFPX_EINVAL;
+    if (!b || !batch_warps_ok(warps_per_cta) || ctas_per_sm < 0) return ZFPX_EINVAL;
     b->warps = warps_per_cta;
     b->ctas_per_sm = ctas_per_sm;
     return ZFPX_OK;
@@ -858,7 +874,7 @@ struct zfpx_server_s {
     int next_slot = 0;
     int64_t next_id = 1;
     int max_batch = 64;
-    int warps = 4, ctas_per_sm = 0;
+    int warps = 3, ctas_per_sm = 0;
     int lb1 = zfpx::kDefaultLb1;
     std::deque<int64_t> completed;
     int64_t batches = 0;
@@ -914,7 +930,7 @@ int zfpx_server_create(zfpx_server *out, const int64_t *row_len, int nrows, size
 
 int zfpx_server_set_launch(zfpx_server s, int warps_per_cta, int ctas_per_sm)
 {
-    if (!s || (warps_per_cta != 4 && warps_per_cta != 8) || ctas_per_sm < 0) return ZFPX_EINVAL;
+    if (!s || !batch_warps_ok(warps_per_cta) || ctas_per_sm < 0) return ZFPX_EINVAL;
     s->warps = warps_per_cta;
     s->ctas_per_sm = ctas_per_sm;
     return ZFPX_OK;

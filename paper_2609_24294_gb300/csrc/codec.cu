@@ -266,8 +266,8 @@ template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 encode1_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchGeom g, int layout, int vec)
 {
-    __shared__ Plane4Tab tab;
-    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    __shared__ Plane4Enc tab;
+    plane4_fill(tab, threadIdx.x, blockDim.x);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * kWarps;
@@ -308,8 +308,8 @@ template <int RATE>
 __global__ void __launch_bounds__(kThreads)
 decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchGeom g, int layout, int vec)
 {
-    __shared__ Plane4Tab tab;
-    for (int i = threadIdx.x; i < kPlane4Entries; i += blockDim.x) plane4_fill(tab, i);
+    __shared__ Plane4Dec tab;
+    plane4_fill(tab, threadIdx.x, blockDim.x);
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t W = (int64_t)gridDim.x * kWarps;

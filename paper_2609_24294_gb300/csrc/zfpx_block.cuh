@@ -945,11 +945,12 @@ struct WordReader {
 // plane and so is dropped; what is left is what reading stops at the budget
 // gives.  Both run K blocks of a lane in lockstep so that their table
 // lookups, which each plane's successor waits for, overlap.
-struct Plane4Tab {
-    uint16_t enc[5 * 16];
-    uint16_t dec[5 * 128];
+struct Plane4Enc {
+    uint16_t e[5 * 16];
 };
-constexpr int kPlane4Entries = 5 * 16 + 5 * 128;
+struct Plane4Dec {
+    uint16_t d[5 * 128];
+};
 
 ZFPX_HD uint16_t plane4_enc_entry(int n, uint32_t X)
 {
@@ -967,17 +968,20 @@ ZFPX_HD uint16_t plane4_dec_entry(int n, uint32_t w7)
     return (uint16_t)(X | ((uint32_t)rd.off << 4) | ((uint32_t)nn << 7));
 }
 
-// Entry i of the concatenated tables (0 <= i < kPlane4Entries), for a fill
-// spread over a CTA's threads.
-ZFPX_HD void plane4_fill(Plane4Tab &t, int i)
+// Fills a table with `nthreads` threads, thread `t` taking every nthreads-th
+// entry (the caller synchronises).
+ZFPX_HD void plane4_fill(Plane4Enc &tab, int t, int nthreads)
 {
-    if (i < 80) t.enc[i] = plane4_enc_entry(i >> 4, (uint32_t)i & 15u);
-    else if (i < kPlane4Entries) t.dec[i - 80] = plane4_dec_entry((i - 80) >> 7, (uint32_t)(i - 80) & 127u);
+    for (int i = t; i < 5 * 16; i += nthreads) tab.e[i] = plane4_enc_entry(i >> 4, (uint32_t)i & 15u);
+}
+ZFPX_HD void plane4_fill(Plane4Dec &tab, int t, int nthreads)
+{
+    for (int i = t; i < 5 * 128; i += nthreads) tab.d[i] = plane4_dec_entry(i >> 7, (uint32_t)i & 127u);
 }
 
 // Encodes K blocks x[b][0..3]; w[b] = the block's 4 RATE bits.
 template <int RATE, int K>
-ZFPX_HD void encode_blocks1(const float (&x)[K][4], const Plane4Tab &tab, uint64_t (&w)[K])
+ZFPX_HD void encode_blocks1(const float (&x)[K][4], const Plane4Enc &tab, uint64_t (&w)[K])
 {
     constexpr int END = 4 * RATE;
     uint32_t u[K][4];
@@ -1009,7 +1013,7 @@ ZFPX_HD void encode_blocks1(const float (&x)[K][4], const Plane4Tab &tab, uint64
             if (pos[b] >= END) continue;
             const uint32_t X = ((u[b][0] >> k) & 1u) | (((u[b][1] >> k) & 1u) << 1) | (((u[b][2] >> k) & 1u) << 2) |
                                (((u[b][3] >> k) & 1u) << 3);
-            const uint32_t e = tab.enc[n[b] * 16 + (int)X];
+            const uint32_t e = tab.e[n[b] * 16 + (int)X];
             w[b] |= (uint64_t)(e & 127u) << pos[b];                // pos < END <= 64
             pos[b] += (int)((e >> 7) & 7u);
             n[b] = (int)(e >> 10);
@@ -1023,7 +1027,7 @@ ZFPX_HD void encode_blocks1(const float (&x)[K][4], const Plane4Tab &tab, uint64
 
 // Decodes K blocks from their 4 RATE-bit words.
 template <int RATE, int K>
-ZFPX_HD void decode_blocks1(const uint64_t (&win)[K], const Plane4Tab &tab, float (&x)[K][4])
+ZFPX_HD void decode_blocks1(const uint64_t (&win)[K], const Plane4Dec &tab, float (&x)[K][4])
 {
     constexpr int END = 4 * RATE;
     uint64_t w[K];
@@ -1045,7 +1049,7 @@ ZFPX_HD void decode_blocks1(const uint64_t (&win)[K], const Plane4Tab &tab, floa
             const int r = END - pos[b];
             uint32_t w7 = (uint32_t)(w[b] >> pos[b]) & 127u;       // pos < END <= 64
             if (r < 7) w7 &= (1u << r) - 1u;
-            const uint32_t d = tab.dec[n[b] * 128 + (int)w7];
+            const uint32_t d = tab.d[n[b] * 128 + (int)w7];
             uint32_t X = d & 15u;
             const int len = (int)((d >> 4) & 7u);
             if (len > r) {                                         // the budget cuts this plane
@@ -1085,7 +1089,7 @@ ZFPX_HD void decode_blocks1(const uint64_t (&win)[K], const Plane4Tab &tab, floa
 }
 
 template <int RATE>
-ZFPX_HD uint64_t encode_block1(const float (&x)[4], const Plane4Tab &tab)
+ZFPX_HD uint64_t encode_block1(const float (&x)[4], const Plane4Enc &tab)
 {
     const float (&xx)[1][4] = reinterpret_cast<const float (&)[1][4]>(x);
     uint64_t w[1];
@@ -1094,7 +1098,7 @@ ZFPX_HD uint64_t encode_block1(const float (&x)[4], const Plane4Tab &tab)
 }
 
 template <int RATE>
-ZFPX_HD void decode_block1(uint64_t w, float (&x)[4], const Plane4Tab &tab)
+ZFPX_HD void decode_block1(uint64_t w, float (&x)[4], const Plane4Dec &tab)
 {
     const uint64_t win[1] = {w};
     float (&xx)[1][4] = reinterpret_cast<float (&)[1][4]>(x);
