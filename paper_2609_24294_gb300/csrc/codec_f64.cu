@@ -7,11 +7,13 @@
 // planes 63 .. 0 cut at exactly 64 r bits; decode x = q 2^(e_max - 62)
 // rounded once to nearest even.
 //
-// A block's 64 int64 values do not fit a lane's registers, so this path keeps
-// them in shared memory: one lane per block, 32 consecutive blocks per warp,
-// one warp per CTA ([value][lane] tiles, each lane in its own column).  The
-// 64 bit planes come from four 32x32 register transposes (low / high 32
-// coefficients x low / high 32 bits).  Rates 1 .. 32 bits per value.
+// One lane per block, 32 consecutive blocks per warp, one warp per CTA.  A
+// block's 64 int64 values live in the lane's registers (128 of them) through
+// the gather, quantisation, transform and negabinary map; the 64 bit planes
+// come from four 32x32 register transposes (low / high 32 coefficients x low
+// / high 32 bits) and wait in shared memory ([plane][lane]) for the coder,
+// which writes the lane's column of a [word][lane] stream tile.  Rates 1 .. 32
+// bits per value.
 #include <algorithm>
 #include <climits>
 #include <cuda_runtime.h>
@@ -26,35 +28,11 @@ namespace {
 using namespace blk;
 
 constexpr int kMaxRate = 32;
+constexpr int kF64MinCtas = 10;         // one-warp CTAs per SM the registers are budgeted for
 constexpr uint64_t kNega64 = 0xAAAAAAAAAAAAAAAAull;
-// the 3-D coefficient order (the warp reads one entry at a time: a broadcast)
-__constant__ int kSeq64[64] = ZFPX_SEQ3;
 
 __device__ __forceinline__ int64_t add64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a + (uint64_t)b); }
 __device__ __forceinline__ int64_t sub64(int64_t a, int64_t b) { return (int64_t)((uint64_t)a - (uint64_t)b); }
-
-// The five lifting steps on one line of the [value][lane] tile (stride s
-// values), floor halving; and their inverse.
-__device__ __forceinline__ void lift_fwd64(int64_t *t, int s)
-{
-    int64_t a = t[0], b = t[s * 32], c = t[2 * s * 32], d = t[3 * s * 32];
-    a = add64(a, d) >> 1; d = sub64(d, a);
-    c = add64(c, b) >> 1; b = sub64(b, c);
-    a = add64(a, c) >> 1; c = sub64(c, a);
-    d = add64(d, b) >> 1; b = sub64(b, d);
-    d = add64(d, b >> 1); b = sub64(b, d >> 1);
-    t[0] = a; t[s * 32] = b; t[2 * s * 32] = c; t[3 * s * 32] = d;
-}
-__device__ __forceinline__ void lift_inv64(int64_t *t, int s)
-{
-    int64_t a = t[0], b = t[s * 32], c = t[2 * s * 32], d = t[3 * s * 32];
-    b = add64(b, d >> 1); d = sub64(d, b >> 1);
-    b = add64(b, d); d = sub64(add64(d, d), b);
-    c = add64(c, a); a = sub64(add64(a, a), c);
-    b = add64(b, c); c = sub64(add64(c, c), b);
-    d = add64(d, a); a = sub64(add64(a, a), d);
-    t[0] = a; t[s * 32] = b; t[2 * s * 32] = c; t[3 * s * 32] = d;
-}
 
 // Writer into this lane's column of a [word][lane] tile of nwords + 2 words.
 struct VarWriter {
@@ -123,25 +101,81 @@ __device__ __forceinline__ int block_exponent(uint64_t amax)
     return E == 0 ? 1 : E + 1;                                   // frexp exponent + 1023
 }
 
-__global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict__ src, uint8_t *__restrict__ out,
-                                                        Geom64 g)
+// The 3-D transform on a block held in registers (int64 v[i + 4j + 16k]).
+__device__ __forceinline__ void lift_fwd64r(int64_t &a, int64_t &b, int64_t &c, int64_t &d)
 {
-    __shared__ int64_t vals[64 * 32];
-    __shared__ uint64_t planes[64 * 32];
-    // the stream tile reuses the values tile: lane l writes its stream words
-    // into its own column only after its last read of its values
-    uint64_t *stile = reinterpret_cast<uint64_t *>(vals);
+    a = add64(a, d) >> 1; d = sub64(d, a);
+    c = add64(c, b) >> 1; b = sub64(b, c);
+    a = add64(a, c) >> 1; c = sub64(c, a);
+    d = add64(d, b) >> 1; b = sub64(b, d);
+    d = add64(d, b >> 1); b = sub64(b, d >> 1);
+}
+__device__ __forceinline__ void lift_inv64r(int64_t &a, int64_t &b, int64_t &c, int64_t &d)
+{
+    b = add64(b, d >> 1); d = sub64(d, b >> 1);
+    b = add64(b, d); d = sub64(add64(d, d), b);
+    c = add64(c, a); a = sub64(add64(a, a), c);
+    b = add64(b, c); c = sub64(add64(c, c), b);
+    d = add64(d, a); a = sub64(add64(a, a), d);
+}
+__device__ __forceinline__ void xform3_fwd64(int64_t (&v)[64])
+{
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            lift_fwd64r(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            lift_fwd64r(v[16 * k + i], v[16 * k + i + 4], v[16 * k + i + 8], v[16 * k + i + 12]);
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            lift_fwd64r(v[4 * j + i], v[4 * j + i + 16], v[4 * j + i + 32], v[4 * j + i + 48]);
+}
+__device__ __forceinline__ void xform3_inv64(int64_t (&v)[64])
+{
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            lift_inv64r(v[4 * j + i], v[4 * j + i + 16], v[4 * j + i + 32], v[4 * j + i + 48]);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            lift_inv64r(v[16 * k + i], v[16 * k + i + 4], v[16 * k + i + 8], v[16 * k + i + 12]);
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            lift_inv64r(v[16 * k + 4 * j], v[16 * k + 4 * j + 1], v[16 * k + 4 * j + 2], v[16 * k + 4 * j + 3]);
+}
+
+// Shared memory of one warp: the 64 bit planes ([plane][lane]) and the stream
+// tile ([64-bit word][lane], rate words and two zero words).
+__host__ __device__ constexpr size_t f64_smem_bytes(int rate) { return (size_t)(64 + rate + 2) * 32 * 8; }
+
+__global__ void __launch_bounds__(32, kF64MinCtas) encode_f64_kernel(const double *__restrict__ src,
+                                                                     uint8_t *__restrict__ out, Geom64 g)
+{
+    extern __shared__ uint64_t sm64[];
+    uint64_t *stile = sm64 + 64 * 32;
     const int lane = threadIdx.x;
-    int64_t *v = vals + lane;
-    SmemPlanes pl{planes, lane};
+    SmemPlanes pl{sm64, lane};
+    constexpr int kSeq[64] = ZFPX_SEQ3;
     for (int64_t u = blockIdx.x; u < g.nunits; u += gridDim.x) {
         const int64_t b0 = u * 32;
         const int nact = (int)min((int64_t)32, g.nblocks - b0);
         if (lane < nact) {
             int64_t x0, y0, z0;
             block_origin(g, b0 + lane, x0, y0, z0);
+            int64_t v[64];
             uint64_t amax = 0;
-#pragma unroll 8
+#pragma unroll
             for (int r = 0; r < 64; r++) {
                 const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
                 const double x = __ldg(src + min(z0 + k, g.n[2] - 1) * g.s[2] + min(y0 + j, g.n[1] - 1) * g.s[1] +
@@ -149,7 +183,7 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
                 const uint64_t bits = (uint64_t)__double_as_longlong(x);
                 const uint64_t a = bits & 0x7fffffffffffffffull;
                 amax = a > amax ? a : amax;
-                v[r * 32] = (int64_t)bits;
+                v[r] = (int64_t)bits;
             }
             const int e = block_exponent(amax);
             VarWriter wr{stile, 0ull, 0, 0, lane, g.rate};
@@ -162,29 +196,20 @@ __global__ void __launch_bounds__(32) encode_f64_kernel(const double *__restrict
                 const int s1 = sh > 600 ? 600 : sh;
                 const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
                 const double f2 = __longlong_as_double((long long)(sh - s1 + 1023) << 52);
-#pragma unroll 8
-                for (int r = 0; r < 64; r++)
-                    v[r * 32] = __double2ll_rz((__longlong_as_double(v[r * 32]) * f1) * f2);
-#pragma unroll 1
-                for (int k = 0; k < 4; k++)
-                    for (int j = 0; j < 4; j++) lift_fwd64(v + (16 * k + 4 * j) * 32, 1);
-#pragma unroll 1
-                for (int k = 0; k < 4; k++)
-                    for (int i = 0; i < 4; i++) lift_fwd64(v + (16 * k + i) * 32, 4);
-#pragma unroll 1
-                for (int j = 0; j < 4; j++)
-                    for (int i = 0; i < 4; i++) lift_fwd64(v + (4 * j + i) * 32, 16);
-                // negabinary in coding order, then the 64 planes by quadrant
-#pragma unroll 1
+#pragma unroll
+                for (int r = 0; r < 64; r++) v[r] = __double2ll_rz((__longlong_as_double(v[r]) * f1) * f2);
+                xform3_fwd64(v);
+#pragma unroll
+                for (int r = 0; r < 64; r++) v[r] = (int64_t)(((uint64_t)v[r] + kNega64) ^ kNega64);
+                // the 64 planes by quadrant: bits 32 hb .. 32 hb + 31 of the
+                // coefficients 32 ch .. 32 ch + 31 in coding order
+#pragma unroll
                 for (int hb = 0; hb < 2; hb++)
-#pragma unroll 1
+#pragma unroll
                     for (int ch = 0; ch < 2; ch++) {
                         uint32_t w[32];
 #pragma unroll
-                        for (int t = 0; t < 32; t++) {
-                            const uint64_t un = ((uint64_t)v[kSeq64[32 * ch + t] * 32] + kNega64) ^ kNega64;
-                            w[t] = (uint32_t)(un >> (32 * hb));
-                        }
+                        for (int t = 0; t < 32; t++) w[t] = (uint32_t)((uint64_t)v[kSeq[32 * ch + t]] >> (32 * hb));
                         transpose32(w);
 #pragma unroll
                         for (int k = 0; k < 32; k++) pl.store_half(32 * hb + k, ch, w[k]);
@@ -242,18 +267,15 @@ __device__ __forceinline__ double dequantize64(int64_t q, int e)
     return __longlong_as_double((long long)(m | sign));
 }
 
-__global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restrict__ in, double *__restrict__ dst,
-                                                        Geom64 g)
+__global__ void __launch_bounds__(32, kF64MinCtas) decode_f64_kernel(const uint8_t *__restrict__ in,
+                                                                     double *__restrict__ dst, Geom64 g)
 {
-    __shared__ int64_t vals[64 * 32];
-    __shared__ uint64_t planes[64 * 32];
-    // the stream tile ([64-bit word][lane], rate words and a zero word) sits in
-    // this lane's own column of the values tile, written over only after the
-    // planes are read out of the stream
-    const Tile64 st{reinterpret_cast<const uint64_t *>(vals), (int)threadIdx.x};
+    extern __shared__ uint64_t sm64[];
+    uint64_t *tile = sm64 + 64 * 32;
     const int lane = threadIdx.x;
-    int64_t *v = vals + lane;
-    SmemPlanes pl{planes, lane};
+    const Tile64 st{tile, lane};
+    SmemPlanes pl{sm64, lane};
+    constexpr int kSeq[64] = ZFPX_SEQ3;
     for (int64_t u = blockIdx.x; u < g.nunits; u += gridDim.x) {
         const int64_t b0 = u * 32;
         const int nact = (int)min((int64_t)32, g.nblocks - b0);
@@ -261,14 +283,16 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
         const int64_t b = b0 + lane;
         const uint64_t *s64 = reinterpret_cast<const uint64_t *>(in) + b * g.rate;
 #pragma unroll 4
-        for (int i = 0; i < g.rate; i++) v[i * 32] = (int64_t)__ldg(s64 + i);
-        v[g.rate * 32] = 0;
+        for (int i = 0; i < g.rate; i++) tile[i * 32 + lane] = __ldg(s64 + i);
+        tile[g.rate * 32 + lane] = 0ull;
+        tile[(g.rate + 1) * 32 + lane] = 0ull;
         int64_t x0, y0, z0;
         block_origin(g, b, x0, y0, z0);
         const uint64_t head = st.peek(0);
+        double x[64];
         if (!(head & 1ull)) {
-#pragma unroll 1
-            for (int r = 0; r < 64; r++) v[r * 32] = 0;
+#pragma unroll
+            for (int r = 0; r < 64; r++) x[r] = 0.0;
         } else {
             const int e = (int)((head >> 1) & 0x7ffu);
             TileReader64 rd{st, 12};
@@ -280,9 +304,10 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
             }
 #pragma unroll 1
             for (int k = 0; k < kmin; k++) pl.store(k, 0ull);
-#pragma unroll 1
+            int64_t v[64];
+#pragma unroll
             for (int hb = 0; hb < 2; hb++)
-#pragma unroll 1
+#pragma unroll
                 for (int ch = 0; ch < 2; ch++) {
                     uint32_t w[32];
 #pragma unroll
@@ -291,30 +316,37 @@ __global__ void __launch_bounds__(32) decode_f64_kernel(const uint8_t *__restric
                     // w[t] = bits 32 hb .. 32 hb + 31 of coefficient 32 ch + t
 #pragma unroll
                     for (int t = 0; t < 32; t++) {
-                        int64_t *c = v + kSeq64[32 * ch + t] * 32;
-                        const uint64_t part = (uint64_t)w[t] << (32 * hb);
-                        *c = hb ? (int64_t)(((uint64_t)*c & 0xffffffffull) | part) : (int64_t)part;
+                        int64_t &c = v[kSeq[32 * ch + t]];
+                        c = hb ? (int64_t)(((uint64_t)c & 0xffffffffull) | ((uint64_t)w[t] << 32)) : (int64_t)w[t];
                     }
                 }
+#pragma unroll
+            for (int r = 0; r < 64; r++) v[r] = sub64((int64_t)((uint64_t)v[r] ^ kNega64), (int64_t)kNega64);
+            xform3_inv64(v);
+            if (e >= 63) {
+                // every non-zero result is normal: (double)q rounds once and
+                // the two power-of-two scalings are exact
+                const int s = e - 1023 - 62, s1 = s < -600 ? -600 : s;
+                const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
+                const double f2 = __longlong_as_double((long long)(s - s1 + 1023) << 52);
+#pragma unroll
+                for (int r = 0; r < 64; r++) x[r] = (__ll2double_rn(v[r]) * f1) * f2;
+            } else {
+                // tiny exponents (rare): a rolled loop over a local copy
+                int64_t t[64];
+#pragma unroll
+                for (int r = 0; r < 64; r++) t[r] = v[r];
 #pragma unroll 1
-            for (int r = 0; r < 64; r++) v[r * 32] = sub64((int64_t)((uint64_t)v[r * 32] ^ kNega64), (int64_t)kNega64);
-#pragma unroll 1
-            for (int j = 0; j < 4; j++)
-                for (int i = 0; i < 4; i++) lift_inv64(v + (4 * j + i) * 32, 16);
-#pragma unroll 1
-            for (int k = 0; k < 4; k++)
-                for (int i = 0; i < 4; i++) lift_inv64(v + (16 * k + i) * 32, 4);
-#pragma unroll 1
-            for (int k = 0; k < 4; k++)
-                for (int j = 0; j < 4; j++) lift_inv64(v + (16 * k + 4 * j) * 32, 1);
-#pragma unroll 8
-            for (int r = 0; r < 64; r++) v[r * 32] = __double_as_longlong(dequantize64(v[r * 32], e));
+                for (int r = 0; r < 64; r++) t[r] = __double_as_longlong(dequantize64(t[r], e));
+#pragma unroll
+                for (int r = 0; r < 64; r++) x[r] = __longlong_as_double(t[r]);
+            }
         }
-#pragma unroll 8
+#pragma unroll
         for (int r = 0; r < 64; r++) {
             const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
             if (x0 + i < g.n[0] && y0 + j < g.n[1] && z0 + k < g.n[2])
-                dst[(z0 + k) * g.s[2] + (y0 + j) * g.s[1] + (x0 + i) * g.s[0]] = __longlong_as_double(v[r * 32]);
+                dst[(z0 + k) * g.s[2] + (y0 + j) * g.s[1] + (x0 + i) * g.s[0]] = x[r];
         }
     }
 }
@@ -330,10 +362,20 @@ Geom64 make_geom(const int64_t n[3], const int64_t s[3], int rate)
     return g;
 }
 
-unsigned grid_f64(const void *fn, int64_t nunits)
+unsigned grid_f64(const void *fn, int64_t nunits, size_t smem)
 {
-    const int64_t cap = (int64_t)num_sms() * occupancy(fn, 32);
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 32, smem) != cudaSuccess || per_sm < 1) per_sm = 1;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(nunits, cap));
+}
+
+// Dynamic shared memory above 48 KB is opted into per kernel.
+int f64_prepare(const void *fn, size_t smem)
+{
+    if (smem <= 48 * 1024) return ZFPX_OK;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess
+               ? ZFPX_OK : ZFPX_ECUDA;
 }
 
 bool valid_f64_args(int rate, const int64_t n[3], const int64_t stride[3])
@@ -364,7 +406,11 @@ int zfpx_encode_f64(int rate, const double *d_in, const int64_t n[3], const int6
     if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
     if (cap < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
     const Geom64 g = make_geom(n, stride, rate);
-    encode_f64_kernel<<<grid_f64((const void *)encode_f64_kernel, g.nunits), 32, 0, (cudaStream_t)stream>>>(d_in, d_out, g);
+    const size_t smem = f64_smem_bytes(rate);
+    const int rc = f64_prepare((const void *)encode_f64_kernel, smem);
+    if (rc) return rc;
+    encode_f64_kernel<<<grid_f64((const void *)encode_f64_kernel, g.nunits, smem), 32, smem, (cudaStream_t)stream>>>(
+        d_in, d_out, g);
     count_launch();
     return check_launch();
 }
@@ -376,7 +422,11 @@ int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3
     if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
     if (len < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
     const Geom64 g = make_geom(n, stride, rate);
-    decode_f64_kernel<<<grid_f64((const void *)decode_f64_kernel, g.nunits), 32, 0, (cudaStream_t)stream>>>(d_in, d_out, g);
+    const size_t smem = f64_smem_bytes(rate);
+    const int rc = f64_prepare((const void *)decode_f64_kernel, smem);
+    if (rc) return rc;
+    decode_f64_kernel<<<grid_f64((const void *)decode_f64_kernel, g.nunits, smem), 32, smem, (cudaStream_t)stream>>>(
+        d_in, d_out, g);
     count_launch();
     return check_launch();
 }
