@@ -128,7 +128,8 @@ ZFPX_API int zfpx_plan_prepare(zfpx_plan plan, int rate);
 ZFPX_API int zfpx_plan_num_messages(zfpx_plan plan);
 /* Geometry of message i (send order): ranks, peers, and the box x0,nx,y0,ny,z0,nz. */
 ZFPX_API int zfpx_plan_message(zfpx_plan plan, int i, int32_t ranks[4], int64_t box[6]);
-/* Bytes of message (src, dst) at `rate`; 0 if the pair exchanges nothing. */
+/* Bytes of message (src, dst) at `rate` -- what rank src sends to rank dst,
+ * the send-size query; 0 if the pair exchanges nothing. */
 ZFPX_API size_t zfpx_message_bytes(zfpx_plan plan, int rate, int src, int dst);
 /* Byte offset of message (src, dst) in the given layout; -1 if none. */
 ZFPX_API int64_t zfpx_message_offset(zfpx_plan plan, int rate, int layout, int src, int dst);
