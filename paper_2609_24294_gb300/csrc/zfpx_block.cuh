@@ -615,16 +615,24 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
             const int T = term ? lowest_set(term) : 64;          // offset of the closing 0
             const int lim = 62 - n;                              // offset - rank of coefficient 62
             const int B = END - pos;
+            // the t-th one, at offset p, is coefficient n + p - t: each one,
+            // lowest first, moves down by the number of ones below it
             int t = 0;
             uint64_t nw = 0;
-            bool over = false;                                   // a one past coefficient 62
             V &= low_mask(T);
-            while (V) {                                          // the t-th one, at offset p, is coefficient n + p - t
-                const int p = lowest_set(V);
-                if (p - t > lim) { over = true; break; }
-                nw |= 1ull << (p - t);
-                V &= V - 1;
+            while (V) {
+                const uint64_t b = V & (0ull - V);
+                nw |= b >> t;
+                V ^= b;
                 t++;
+            }
+            // ones past coefficient 62 lie beyond a part that ends at the
+            // implied one; the ones below stay, in the order they came
+            const uint64_t keep = low_mask(lim + 1);
+            const bool over = (nw & ~keep) != 0ull;             // a one past coefficient 62
+            if (over) {
+                nw &= keep;
+                t = popc64(nw);
             }
             X |= nw << n;
             const int E = 63 - n + t;                            // end of the part if it ends at the implied one
