@@ -612,14 +612,15 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
             // implied one needs the check that its zeros fit (B bits left).
             uint64_t term;
             uint64_t V = group_values(kTileZeroRows<RATE> >= 3 || pos < END ? tile_peek(tile, pos) : 0ull, term);
-            const int T = term ? lowest_set(term) : 64;          // offset of the closing 0
+            const uint64_t below = term ? (term & (0ull - term)) - 1ull : ~0ull;   // bits before the closing 0
+            const int T = popc64(below);                         // offset of the closing 0 (64: none)
             const int lim = 62 - n;                              // offset - rank of coefficient 62
             const int B = END - pos;
             // the t-th one, at offset p, is coefficient n + p - t: each one,
             // lowest first, moves down by the number of ones below it
             int t = 0;
             uint64_t nw = 0;
-            V &= low_mask(T);
+            V &= below;
             while (V) {
                 const uint64_t b = V & (0ull - V);
                 nw |= b >> t;
