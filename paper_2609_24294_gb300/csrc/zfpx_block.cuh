@@ -604,7 +604,7 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
         uint64_t X = w & lm;
         if (rem <= n) { pl.store(k, w & low_mask(rem)); break; }     // budget ends in the verbatim bits
         pos += n + 1;
-        if (!((w >> n) & 1ull)) { pl.store(k, X); continue; }       // group empty
+        if (!(w & (lm + 1ull))) { pl.store(k, X); continue; }       // group empty (lm + 1 = bit n)
         {
             // The whole part from one window.  The tile is zero past the
             // budget, so no one and no closing 0 can be read there: a part
@@ -616,20 +616,20 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
             const int T = popc64(below);                         // offset of the closing 0 (64: none)
             const int lim = 62 - n;                              // offset - rank of coefficient 62
             const int B = END - pos;
-            // the t-th one, at offset p, is coefficient n + p - t: each one,
-            // lowest first, moves down by the number of ones below it
+            // the t-th one, at offset p, is coefficient n + p - t: take the
+            // ones lowest first, shifting the rest down by one after each
             int t = 0;
             uint64_t nw = 0;
             V &= below;
             while (V) {
                 const uint64_t b = V & (0ull - V);
-                nw |= b >> t;
-                V ^= b;
+                nw |= b;
+                V = (V ^ b) >> 1;
                 t++;
             }
             // ones past coefficient 62 lie beyond a part that ends at the
             // implied one; the ones below stay, in the order they came
-            const uint64_t keep = low_mask(lim + 1);
+            const uint64_t keep = (~0ull >> n) >> 1;             // low_mask(lim + 1)
             const bool over = (nw & ~keep) != 0ull;             // a one past coefficient 62
             if (over) {
                 nw &= keep;
