@@ -126,8 +126,8 @@ encode3_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         {
             // lanes past the unit's last block load that block and code nothing
             const int b = (int)b0 + (valid ? lane : nact - 1);
-            const int bxi = b % bxn, t = b / bxn;
-            const int byi = t % byn, bzi = t / byn;
+            const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+            const int bzi = (int)divu((uint32_t)t, m.bym, m.byl), byi = t - bzi * byn;
             const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
             const float *base = src + src_off;
             if (VEC && x0 + 4 <= nx) {
@@ -213,8 +213,8 @@ decode3_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
                 t32[(4 * i + 2) * 32 + lane] = v.z;
                 t32[(4 * i + 3) * 32 + lane] = v.w;
             }
-            const int bxi = b % bxn, t = b / bxn;
-            const int byi = t % byn, bzi = t / byn;
+            const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+            const int bzi = (int)divu((uint32_t)t, m.bym, m.byl), byi = t - bzi * byn;
             const int x0 = 4 * bxi, y0 = 4 * byi, z0 = 4 * bzi;
             float v[64];
             decode_block3_tile<RATE>(tile, v, pl);
@@ -286,8 +286,8 @@ encode1_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         const int nx = m.nx, bxn = m.bx, byn = m.by;
         const int64_t boff = layout ? m.off[1] : m.off[0];
         const int b = (int)b0 + lane;
-        const int bxi = b % bxn, t = b / bxn;
-        const int y = t % byn, z = t / byn;
+        const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+        const int z = (int)divu((uint32_t)t, m.bym, m.byl), y = t - z * byn;
         const int x0 = 4 * bxi;
         const float *row = src + m.src_off + (int64_t)z * g.ss[2] + (int64_t)y * g.ss[1];
         float r[4];
@@ -333,8 +333,8 @@ decode1_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         else w = __ldg(reinterpret_cast<const uint32_t *>(in + boff) + b);
         float v[4];
         decode_block1<RATE>(w, v, tab);
-        const int bxi = b % bxn, t = b / bxn;
-        const int y = t % byn, z = t / byn;
+        const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+        const int z = (int)divu((uint32_t)t, m.bym, m.byl), y = t - z * byn;
         const int x0 = 4 * bxi;
         float *row = dstf + m.dst_off + (int64_t)z * g.ds[2] + (int64_t)y * g.ds[1];
         if (vec && x0 + 4 <= nx) {
@@ -378,8 +378,8 @@ encode2_kernel(const float *__restrict__ src, uint8_t *__restrict__ out, LaunchG
         if (lane < nact) {
             const int nx = m.nx, ny = m.ny, bxn = m.bx, byn = m.by;
             const int b = (int)b0 + lane;
-            const int bxi = b % bxn, t = b / bxn;
-            const int byi = t % byn, z = t / byn;
+            const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+            const int z = (int)divu((uint32_t)t, m.bym, m.byl), byi = t - z * byn;
             const int x0 = 4 * bxi, y0 = 4 * byi;
             const float *base = src + m.src_off + (int64_t)z * g.ss[2];
             float x[16];
@@ -453,8 +453,8 @@ decode2_kernel(const uint8_t *__restrict__ in, float *__restrict__ dstf, LaunchG
         }
         float v[16];
         decode_block2_tile<RATE>(tile, v, pl);
-        const int bxi = b % bxn, t = b / bxn;
-        const int byi = t % byn, z = t / byn;
+        const int t = (int)divu((uint32_t)b, m.bxm, m.bxl), bxi = b - t * bxn;
+        const int z = (int)divu((uint32_t)t, m.bym, m.byl), byi = t - z * byn;
         const int x0 = 4 * bxi, y0 = 4 * byi;
         float *base = dstf + m.dst_off + (int64_t)z * g.ds[2];
         if (vec && x0 + 4 <= nx) {
@@ -769,6 +769,7 @@ extern "C" int zfpx_transpose_noalloc(zfpx_plan p, int rate, const float *d_src,
         d.nx = (int32_t)m.nx; d.ny = (int32_t)m.ny; d.nz = (int32_t)m.nz;
         d.bx = (int32_t)bx; d.by = (int32_t)by; d.bz = (int32_t)bz;
         d.nblocks = bx * by * bz;
+        set_block_divisors(d);
         d.unit0 = units;
         units += (d.nblocks + 31) / 32;
     }

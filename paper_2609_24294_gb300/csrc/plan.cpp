@@ -136,6 +136,7 @@ int64_t host_table(const zfpx_plan_s *p, int rate, UnitKind kind, const std::vec
         d.nx = (int32_t)m.nx; d.ny = (int32_t)m.ny; d.nz = (int32_t)m.nz;
         d.bx = (int32_t)b[0]; d.by = (int32_t)b[1]; d.bz = (int32_t)b[2];
         d.nblocks = b[0] * b[1] * b[2];
+        set_block_divisors(d);
         d.unit0 = units;
         if (kind == UNIT_BLOCKS32) units += (d.nblocks + 31) / 32;
         else if (kind == UNIT_QUADS) units += ceil4(m.nx) * m.ny * m.nz;

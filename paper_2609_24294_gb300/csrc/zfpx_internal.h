@@ -23,7 +23,33 @@ struct MsgDev {
     int32_t nx, ny, nz; // box extents
     int32_t bx, by, bz; // block counts (dims 3: ceil(n/4) each; dims 1: ceil(nx/4), ny, nz)
     int64_t nblocks;    // bx * by * bz
+    uint32_t bxm, bym;  // divisors of bx and by for divu (set_block_divisors)
+    int32_t bxl, byl;
 };
+
+// Exact unsigned 32-bit division by an invariant d >= 1 as a high multiply,
+// an add and shifts (Granlund and Montgomery, "Division by invariant integers
+// using multiplication", 1994): l = ceil(log2 d), m = floor(2^32 (2^l - d) / d)
+// + 1, then n / d = (t + ((n - t) >> 1)) >> (l - 1) with t = mulhi(n, m), and
+// n itself when d = 1.
+inline void block_divisor(uint32_t d, uint32_t &m, int32_t &l)
+{
+    l = 0;
+    while (l < 32 && ((uint64_t)1 << l) < d) l++;
+    m = (uint32_t)(((((uint64_t)1 << l) - d) << 32) / d + 1);
+}
+inline void set_block_divisors(MsgDev &d)
+{
+    block_divisor((uint32_t)d.bx, d.bxm, d.bxl);
+    block_divisor((uint32_t)d.by, d.bym, d.byl);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ uint32_t divu(uint32_t n, uint32_t m, int32_t l)
+{
+    const uint32_t t = __umulhi(n, m);
+    return l ? (t + ((n - t) >> 1)) >> (l - 1) : n;
+}
+#endif
 
 // Arguments common to every plan-driven launch.
 struct LaunchGeom {
