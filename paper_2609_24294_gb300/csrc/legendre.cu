@@ -41,6 +41,7 @@
 // stops.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -57,10 +58,12 @@ struct zfpx_legendre_s {
     int nlat = 0, T = 0, nh = 0, nhs = 0, device = 0;
     int64_t table_rows = 0;
     float *d_table = nullptr;   // K-major: [table_rows][nhs] floats, columns >= nh zero
+    float *d_table_lo = nullptr;   // the table's TF32 low parts (tf32_lo), same layout
     LegItem *d_items = nullptr;
     int *d_status = nullptr;    // 0, or the code of a wait that ran out
     int nitems = 0;
     CUtensorMap tmap_table;     // TMA view of the table: {nh, table_rows}, boxes {32, 128}
+    CUtensorMap tmap_table_lo;  // the same view of its low parts
 };
 
 namespace zfpx {
@@ -155,8 +158,32 @@ __device__ __forceinline__ void mbar_expect(uint32_t mbar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(mbar), "r"(bytes) : "memory");
 }
 
-// lo = round_to_tf32(a - trunc_to_tf32(a)) over n 16-byte chunks, by the
-// `nthr` threads numbered t
+// The 3 x TF32 split of a float32 a: hi = a with its 13 low mantissa bits
+// cleared (what the tensor core reads of a), lo = a - hi (exact) rounded to
+// TF32, to nearest with ties away from zero, by adding half of the last kept
+// bit to the magnitude bits and clearing the rest (the rounding of PTX's
+// cvt.rna.tf32.f32, as integer operations).
+__host__ __device__ inline float tf32_lo(float a)
+{
+#ifdef __CUDA_ARCH__
+    const float l = a - __uint_as_float(__float_as_uint(a) & 0xffffe000u);
+    return __uint_as_float((__float_as_uint(l) + 0x1000u) & 0xffffe000u);
+#else
+    uint32_t u;
+    std::memcpy(&u, &a, 4);
+    u &= 0xffffe000u;
+    float h;
+    std::memcpy(&h, &u, 4);
+    const float l = a - h;
+    std::memcpy(&u, &l, 4);
+    u = (u + 0x1000u) & 0xffffe000u;
+    float r;
+    std::memcpy(&r, &u, 4);
+    return r;
+#endif
+}
+
+// lo = tf32_lo(a) over n 16-byte chunks, by the `nthr` threads numbered t
 __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nchunks, int t, int nthr)
 {
     for (int i = t; i < nchunks; i += nthr) {
@@ -164,10 +191,7 @@ __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nc
         float v[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const float h = __uint_as_float(__float_as_uint(v[q]) & 0xffffe000u);
-            uint32_t r;
-            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v[q] - h));
-            v[q] = __uint_as_float(r);
+            v[q] = tf32_lo(v[q]);
         }
         reinterpret_cast<float4 *>(lo)[i] = make_float4(v[0], v[1], v[2], v[3]);
     }
@@ -209,7 +233,8 @@ __device__ __forceinline__ bool role_wait(uint32_t mbar, uint32_t parity, volati
 }
 
 __global__ void __launch_bounds__(kMmaThreads, 1)
-legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_b,
+legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_constant__ CUtensorMap tmap_alo,
+                    const __grid_constant__ CUtensorMap tmap_b,
                     const LegItem *__restrict__ items, LegGeom g, int stages, int ntiles_total,
                     float *__restrict__ are, float *__restrict__ aim, int *__restrict__ status)
 {
@@ -245,6 +270,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_a) : "memory");
+        asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_alo) : "memory");
         asm volatile("prefetch.tensormap [%0];" :: "l"(&tmap_b) : "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -269,8 +295,9 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
                         break;
                     }
                     const uint32_t fb = smem_u32(&full_bar[s]);
-                    mbar_expect(fb, a_bytes + b_bytes);
+                    mbar_expect(fb, 2 * a_bytes + b_bytes);
                     tma_load_2d(smem_u32(a_raw(s)), &tmap_a, k * kBK, arow, fb);
+                    tma_load_2d(smem_u32(a_lo(s)), &tmap_alo, k * kBK, arow, fb);
                     tma_load_2d(smem_u32(b_raw(s)), &tmap_b, k * kBK, brow, fb);
                 }
             }
@@ -291,8 +318,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
             for (int k = 0; k < nk; k++, i++) {
                 const int s = i % stages;
                 if (!role_wait(smem_u32(&full_bar[s]), (uint32_t)(i / stages) & 1u, vfail)) *vfail = 1;
-                split_lo(a_raw(s), a_lo(s), (int)(a_bytes / 16), c, kConsumers);
-                split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), c, kConsumers);
+                split_lo(b_raw(s), b_lo(s), (int)(b_bytes / 16), c, kConsumers);   // the table's come with it
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 // the named barrier, reducing every consumer's view of the failure
                 // flag so that all of them take the same branch
@@ -524,14 +550,20 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
         }
     }
     p->nitems = (int)items.size();
+    std::vector<float> tab_lo(tab.size());
+    for (size_t i = 0; i < tab.size(); i++) tab_lo[i] = tf32_lo(tab[i]);
     if (cudaMalloc(&p->d_table, tab.size() * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&p->d_table_lo, tab.size() * sizeof(float)) != cudaSuccess ||
         cudaMalloc(&p->d_items, std::max<size_t>(items.size(), 1) * sizeof(LegItem)) != cudaSuccess ||
         cudaMalloc(&p->d_status, sizeof(int)) != cudaSuccess ||
         cudaMemcpy(p->d_table, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(p->d_table_lo, tab_lo.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(p->d_items, items.data(), items.size() * sizeof(LegItem), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(p->d_status, 0, sizeof(int)) != cudaSuccess ||
-        make_tmap(&p->tmap_table, p->d_table, nh, std::max<int64_t>(rows, 1), nhs, kBM) != ZFPX_OK) {
+        make_tmap(&p->tmap_table, p->d_table, nh, std::max<int64_t>(rows, 1), nhs, kBM) != ZFPX_OK ||
+        make_tmap(&p->tmap_table_lo, p->d_table_lo, nh, std::max<int64_t>(rows, 1), nhs, kBM) != ZFPX_OK) {
         cudaFree(p->d_table);
+        cudaFree(p->d_table_lo);
         cudaFree(p->d_items);
         cudaFree(p->d_status);
         delete p;
@@ -554,6 +586,7 @@ void zfpx_legendre_destroy(zfpx_legendre p)
 {
     if (!p) return;
     cudaFree(p->d_table);
+    cudaFree(p->d_table_lo);
     cudaFree(p->d_items);
     cudaFree(p->d_status);
     delete p;
@@ -616,7 +649,8 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
     if (cudaFuncSetAttribute(legendre_mma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return ZFPX_ECUDA;
     const int grid = (int)std::min<int64_t>(nblk, num_sms());      // persistent: one CTA per SM
-    legendre_mma_kernel<<<grid, kMmaThreads, smem, st>>>(p->tmap_table, tmap_g, p->d_items, g, mma_stages(g.nt), (int)nblk,
+    legendre_mma_kernel<<<grid, kMmaThreads, smem, st>>>(p->tmap_table, p->tmap_table_lo, tmap_g, p->d_items, g,
+                                                          mma_stages(g.nt), (int)nblk,
                                                           d_are, d_aim, p->d_status);
     count_launch();
     return check_launch();
