@@ -203,11 +203,11 @@ __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nc
 //   warp 0 (one lane)  TMA producer: the K slices of every tile in turn, up to
 //                      `stages` ahead, a stage refilled once the MMAs that read
 //                      it have completed (mma_bar);
-//   warps 1-7          wait for a slice (full_bar), derive the data tile's lo part (the table's comes by TMA), meet at
+//   warps 1-11         wait for a slice (full_bar), derive the data tile's lo part (the table's comes by TMA), meet at
 //                      a named barrier; one of their threads issues the slice's
 //                      MMAs into the tile's accumulator and commits them to the
 //                      stage, and after a tile's last slice to acc_full;
-//   warps 8-11         epilogue: once a tile's accumulator is complete, each
+//   warps 12-15        epilogue: once a tile's accumulator is complete, each
 //                      reads the 32 rows of its TMEM lane quadrant, scatters
 //                      them into the triangular output and frees the
 //                      accumulator (acc_empty).
@@ -215,8 +215,8 @@ __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nc
 // between tiles, so a tile's epilogue overlaps the next tile's MMAs.
 // Dynamic shared memory: `stages` x {A raw, A lo, B raw, B lo}, 1024-aligned.
 constexpr int kMaxStages = 4;
-constexpr int kConsumers = 224;                 // warps 1-7
-constexpr int kMmaThreads = 384;                // 12 warps
+constexpr int kConsumers = 352;                 // warps 1-11
+constexpr int kMmaThreads = 512;                // 16 warps
 constexpr int kAccCols = 256;
 
 // A bounded wait that also gives up once another role has failed.
@@ -302,7 +302,7 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
                 }
             }
         }
-    } else if (warp <= 7) {
+    } else if (warp <= 11) {
         // ---- lo tiles and MMAs
         const int c = tid - 32;
         const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(nt >> 3) << 17) |
@@ -353,9 +353,9 @@ legendre_mma_kernel(const __grid_constant__ CUtensorMap tmap_a, const __grid_con
             }
         }
     } else {
-        // ---- epilogue: warp 8 + q reads TMEM lanes 32 q .. 32 q + 31 (its warp
+        // ---- epilogue: warp 12 + q reads TMEM lanes 32 q .. 32 q + 31 (its warp
         // index mod 4 is q, the lane quadrant tcgen05.ld lets it reach)
-        const int q = warp - 8, lane = tid & 31;
+        const int q = warp - 12, lane = tid & 31;
         int j = 0;
         for (int t = blockIdx.x; t < ntiles_total; t += gridDim.x, j++) {
             const int acc = j & 1;
