@@ -203,8 +203,9 @@ __device__ __forceinline__ void split_lo(const uint8_t *raw, uint8_t *lo, int nc
 //   warp 0 (one lane)  TMA producer: the K slices of every tile in turn, up to
 //                      `stages` ahead, a stage refilled once the MMAs that read
 //                      it have completed (mma_bar);
-//   warps 1-11         wait for a slice (full_bar), derive the data tile's lo part (the table's comes by TMA), meet at
-//                      a named barrier; one of their threads issues the slice's
+//   warps 1-11         wait for a slice (full_bar), derive the data tile's lo
+//                      part (the table's comes by TMA), meet at a named
+//                      barrier; one of their threads issues the slice's
 //                      MMAs into the tile's accumulator and commits them to the
 //                      stage, and after a tile's last slice to acc_full;
 //   warps 12-15        epilogue: once a tile's accumulator is complete, each
