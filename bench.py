@@ -393,7 +393,7 @@ def extra_serving(z, peak, lens, fields, n=2000, rate_hz=50e3, arena=40 << 30):
     """Request loop: n messages (row x level slabs of the resident O1280
     fields, sizes lognormal around 1 MiB clipped to 16 KiB..64 MiB), Poisson
     arrivals at rate_hz, rates 8 / 16, admitted into a 40 GB arena, batched
-    continuously over 4 streams; p50 / p99 latency from arrival to completion
+    continuously over 8 streams; p50 / p99 latency from arrival to completion
     seen by the host, sustained GB/s; beside float32 / float16 pack+unpack of
     the same slabs."""
     import torch
@@ -407,13 +407,16 @@ def extra_serving(z, peak, lens, fields, n=2000, rate_hz=50e3, arena=40 << 30):
         ptr = f.data_ptr() + 4 * (r["z0"] * f.stride(0) + int(offs[r["row0"]]))
         calls.append(dict(src=ptr, lev_stride=f.stride(0), nlev=r["nz"], dims=r["dims"], rate=r["rate"],
                           row0=r["row0"], row1=r["row1"]))
-    srv = serve.Server(lens, arena_bytes=arena, nstreams=4, max_batch=64)
+    # engine settings from a sweep on these slabs (max batch 32 .. 2048, 1 .. 8 streams, 1-D unit
+    # sizes 4 .. 16): 512 requests per batch at most, 8 streams, 8 1-D blocks per lane
+    srv = serve.Server(lens, arena_bytes=arena, nstreams=8, max_batch=512)
+    srv.set_unit_blocks(8)
     serve.run_requests_native(srv, calls[:50])                            # warm-up
     arrivals = np.cumsum(np.random.default_rng(5).exponential(1.0 / rate_hz, n))
     lat, wall, busy_max, nbatch = serve.run_requests_native(srv, calls, arrivals=arrivals)
     total = float(sum(r["bytes"] for r in reqs))
     res = {"workload": "%d O1280 slabs, lognormal sizes (median %.2f MB, max %.1f MB), Poisson %.0f/s, rates 8/16, "
-                       "40 GB arena, 4 streams, request loop in the library" % (
+                       "40 GB arena, 8 streams, at most 512 requests per batch, request loop in the library" % (
                            n, np.median([r["bytes"] for r in reqs]) / 1e6, max(r["bytes"] for r in reqs) / 1e6,
                            rate_hz),
            "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
