@@ -882,12 +882,65 @@ ZFPX_HD void decode_block2_tile(const Tile &tile, float (&x)[16], Planes &pl)
         return;
     }
     const int e = (int)((head >> 1) & 0xffu);
-    TileReader<Tile> rd{tile, 9};
-    int n = 0, R = 16 * RATE - 9, kmin = 32;
+    // Plane by plane from one 64-bit window: n verbatim bits, the first group
+    // bit, and a group-tested part of at most 16 - n value bits and 15 group
+    // bits, 48 bits in all.  The tile is zero past the budget, so a part the
+    // budget cuts reads on as zeros: no one and no closing 0 appear there,
+    // and only the implied one of coefficient 15 needs the check that its
+    // bits fit (the 3-D decoder's reading, with 16 coefficients).
+    constexpr int END = 16 * RATE;
+    int pos = 9, n = 0, kmin = 32;
+    uint32_t lm = 0;                                             // low n bits
 #pragma unroll 1
-    for (int k = 31; k >= 0 && R > 0; k--) {
-        pl.store_half(k, 0, (uint32_t)decode_plane<16>(rd, n, R));
+    for (int k = 31; k >= 0 && pos < END; k--) {
         kmin = k;
+        const int rem = END - pos;
+        const uint64_t w = tile_peek(tile, pos);
+        if (n >= 16) {                                           // verbatim plane
+            pl.store_half(k, 0, (uint32_t)w & (rem < 16 ? (1u << rem) - 1u : 0xffffu));
+            pos += 16;
+            continue;
+        }
+        uint32_t X = (uint32_t)w & lm;
+        if (rem <= n) { pl.store_half(k, 0, (uint32_t)w & ((1u << rem) - 1u)); break; }   // cut in the verbatim bits
+        pos += n + 1;
+        if (!(w & (uint64_t)(lm + 1u))) { pl.store_half(k, 0, X); continue; }           // group empty
+        uint64_t term;
+        uint64_t V = group_values(w >> (n + 1), term);
+        const uint64_t below = term ? (term & (0ull - term)) - 1ull : ~0ull;   // bits before the closing 0
+        const int T = popc64(below);
+        // the t-th one, at offset p, is coefficient n + p - t: take the ones
+        // lowest first, shifting the rest down by one after each
+        int t = 0;
+        uint64_t nw = 0;
+        V &= below;
+        while (V) {
+            const uint64_t b = V & (0ull - V);
+            nw |= b;
+            V = (V ^ b) >> 1;
+            t++;
+        }
+        // ones past coefficient 14 lie beyond a part that ends at the implied one
+        const uint64_t keep = (1ull << (15 - n)) - 1ull;
+        const bool over = (nw & ~keep) != 0ull;
+        if (over) {
+            nw &= keep;
+            t = popc64(nw);
+        }
+        X |= (uint32_t)nw << n;
+        if (!over && term) {                                     // closed by a 0 below coefficient 15
+            pl.store_half(k, 0, X);
+            n += T - t + 1;
+            lm = (1u << n) - 1u;
+            pos += T + 1;
+            continue;
+        }
+        const int E = 15 - n + t;                                // the part ends at the implied one
+        if (E > END - pos) { pl.store_half(k, 0, X); break; }
+        pl.store_half(k, 0, X | 0x8000u);
+        pos += E;
+        n = 16;
+        lm = 0xffffu;
     }
     // Planes below kmin are zero; when planes 0..15 are zero in every lane of
     // the warp, the transpose stages below 16 skip them.
