@@ -83,6 +83,8 @@ struct Geom64 {
     int64_t n[3], s[3];
     int64_t bx, by, nblocks, nunits;
     int rate;
+    int vec;        // unit x stride, even y and z strides, 16-byte aligned base: rows of a block are
+                    // two 16-byte moves each
 };
 
 __device__ __forceinline__ void block_origin(const Geom64 &g, int64_t b, int64_t &x0, int64_t &y0, int64_t &z0)
@@ -174,16 +176,40 @@ __global__ void __launch_bounds__(32, kF64MinCtas) encode_f64_kernel(const doubl
             int64_t x0, y0, z0;
             block_origin(g, b0 + lane, x0, y0, z0);
             int64_t v[64];
+            if (g.vec && x0 + 4 <= g.n[0] && y0 + 4 <= g.n[1] && z0 + 4 <= g.n[2]) {
+                // an interior block: two 16-byte loads per row
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+#pragma unroll
+                    for (int j = 0; j < 4; j++) {
+                        const double2 *row = reinterpret_cast<const double2 *>(src + (z0 + k) * g.s[2] +
+                                                                               (y0 + j) * g.s[1] + x0);
+                        const double2 a = __ldg(row), b = __ldg(row + 1);
+                        v[16 * k + 4 * j] = __double_as_longlong(a.x);
+                        v[16 * k + 4 * j + 1] = __double_as_longlong(a.y);
+                        v[16 * k + 4 * j + 2] = __double_as_longlong(b.x);
+                        v[16 * k + 4 * j + 3] = __double_as_longlong(b.y);
+                    }
+            } else {
+                // edge blocks and other layouts: element loads, the last row, level
+                // and point repeated past the array's end, through a local array
+                // kept rolled so the hot path's code stays compact
+                int64_t t[64];
+#pragma unroll 1
+                for (int r = 0; r < 64; r++) {
+                    const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                    t[r] = __double_as_longlong(__ldg(src + min(z0 + k, g.n[2] - 1) * g.s[2] +
+                                                      min(y0 + j, g.n[1] - 1) * g.s[1] +
+                                                      min(x0 + i, g.n[0] - 1) * g.s[0]));
+                }
+#pragma unroll
+                for (int r = 0; r < 64; r++) v[r] = t[r];
+            }
             uint64_t amax = 0;
 #pragma unroll
             for (int r = 0; r < 64; r++) {
-                const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
-                const double x = __ldg(src + min(z0 + k, g.n[2] - 1) * g.s[2] + min(y0 + j, g.n[1] - 1) * g.s[1] +
-                                       min(x0 + i, g.n[0] - 1) * g.s[0]);
-                const uint64_t bits = (uint64_t)__double_as_longlong(x);
-                const uint64_t a = bits & 0x7fffffffffffffffull;
+                const uint64_t a = (uint64_t)v[r] & 0x7fffffffffffffffull;
                 amax = a > amax ? a : amax;
-                v[r] = (int64_t)bits;
             }
             const int e = block_exponent(amax);
             VarWriter wr{stile, 0ull, 0, 0, lane, g.rate};
@@ -342,18 +368,36 @@ __global__ void __launch_bounds__(32, kF64MinCtas) decode_f64_kernel(const uint8
                 for (int r = 0; r < 64; r++) x[r] = __longlong_as_double(t[r]);
             }
         }
+        if (g.vec && x0 + 4 <= g.n[0] && y0 + 4 <= g.n[1] && z0 + 4 <= g.n[2]) {
+            // an interior block: two 16-byte stores per row
 #pragma unroll
-        for (int r = 0; r < 64; r++) {
-            const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
-            if (x0 + i < g.n[0] && y0 + j < g.n[1] && z0 + k < g.n[2])
-                dst[(z0 + k) * g.s[2] + (y0 + j) * g.s[1] + (x0 + i) * g.s[0]] = x[r];
+            for (int k = 0; k < 4; k++)
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    double2 *row = reinterpret_cast<double2 *>(dst + (z0 + k) * g.s[2] + (y0 + j) * g.s[1] + x0);
+                    row[0] = make_double2(x[16 * k + 4 * j], x[16 * k + 4 * j + 1]);
+                    row[1] = make_double2(x[16 * k + 4 * j + 2], x[16 * k + 4 * j + 3]);
+                }
+        } else {
+            // edge blocks and other layouts: element stores inside the array,
+            // through a local array kept rolled
+            double t[64];
+#pragma unroll
+            for (int r = 0; r < 64; r++) t[r] = x[r];
+#pragma unroll 1
+            for (int r = 0; r < 64; r++) {
+                const int i = r & 3, j = (r >> 2) & 3, k = r >> 4;
+                if (x0 + i < g.n[0] && y0 + j < g.n[1] && z0 + k < g.n[2])
+                    dst[(z0 + k) * g.s[2] + (y0 + j) * g.s[1] + (x0 + i) * g.s[0]] = t[r];
+            }
         }
     }
 }
 
-Geom64 make_geom(const int64_t n[3], const int64_t s[3], int rate)
+Geom64 make_geom(const int64_t n[3], const int64_t s[3], int rate, const void *base)
 {
     Geom64 g;
+    g.vec = s[0] == 1 && s[1] % 2 == 0 && s[2] % 2 == 0 && !((uintptr_t)base & 15u);
     for (int a = 0; a < 3; a++) { g.n[a] = n[a]; g.s[a] = s[a]; }
     g.bx = (n[0] + 3) / 4; g.by = (n[1] + 3) / 4;
     g.nblocks = g.bx * g.by * ((n[2] + 3) / 4);
@@ -405,7 +449,7 @@ int zfpx_encode_f64(int rate, const double *d_in, const int64_t n[3], const int6
     if (!d_in || !d_out || !valid_f64_args(rate, n, stride)) return ZFPX_EINVAL;
     if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
     if (cap < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
-    const Geom64 g = make_geom(n, stride, rate);
+    const Geom64 g = make_geom(n, stride, rate, d_in);
     const size_t smem = f64_smem_bytes(rate);
     const int rc = f64_prepare((const void *)encode_f64_kernel, smem);
     if (rc) return rc;
@@ -421,7 +465,7 @@ int zfpx_decode_f64(int rate, const uint8_t *d_in, size_t len, const int64_t n[3
     if (!d_in || !d_out || !valid_f64_args(rate, n, stride)) return ZFPX_EINVAL;
     if (((uintptr_t)d_out & 7u) || ((uintptr_t)d_in & 7u)) return ZFPX_EINVAL;
     if (len < zfpx_stream_bytes_f64(rate, n)) return ZFPX_ESIZE;
-    const Geom64 g = make_geom(n, stride, rate);
+    const Geom64 g = make_geom(n, stride, rate, d_out);
     const size_t smem = f64_smem_bytes(rate);
     const int rc = f64_prepare((const void *)decode_f64_kernel, smem);
     if (rc) return rc;
