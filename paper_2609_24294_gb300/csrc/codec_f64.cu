@@ -72,11 +72,13 @@ struct Tile64 {
     }
 };
 
-struct TileReader64 {
-    const Tile64 &t;
-    int pos;
-    __device__ __forceinline__ uint64_t peek() const { return t.peek(pos); }
-    __device__ __forceinline__ void skip(int k) { pos += k; }
+// The same stream as 32-bit words (word i is the low half of 64-bit word
+// i / 2 for even i, the high half for odd i), for the float32 path's plane
+// parser.
+struct Tile64As32 {
+    const uint32_t *sm;
+    int lane;
+    __device__ __forceinline__ uint32_t get(int i) const { return sm[2 * ((i >> 1) * 32 + lane) + (i & 1)]; }
 };
 
 struct Geom64 {
@@ -321,13 +323,10 @@ __global__ void __launch_bounds__(32, kF64MinCtas) decode_f64_kernel(const uint8
             for (int r = 0; r < 64; r++) x[r] = 0.0;
         } else {
             const int e = (int)((head >> 1) & 0x7ffu);
-            TileReader64 rd{st, 12};
-            int n = 0, R = 64 * g.rate - 12, kmin = 64;
-#pragma unroll 1
-            for (int k = 63; k >= 0 && R > 0; k--) {
-                pl.store(k, decode_plane<64>(rd, n, R));
-                kmin = k;
-            }
+            // the planes from bit 12 on; the tile's two zero 64-bit words let the
+            // parser read past the budget without a test
+            const Tile64As32 t32{reinterpret_cast<const uint32_t *>(tile), lane};
+            const int kmin = parse_planes64<true>(t32, 12, 64 * g.rate, 63, pl);
 #pragma unroll 1
             for (int k = 0; k < kmin; k++) pl.store(k, 0ull);
             int64_t v[64];

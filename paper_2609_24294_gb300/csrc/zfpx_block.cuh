@@ -573,26 +573,21 @@ ZFPX_HD uint64_t group_values(uint64_t W, uint64_t &term)
     return val;
 }
 
-// Decodes one block from this lane's stream tile: plane by plane, each
+// The bit planes of a 64-coefficient block, planes ktop, ktop - 1, ... from
+// stream bit pos on, with the budget ending at bit END: plane by plane, each
 // plane's group-tested part in one step when it closes inside a 64-bit
 // window, below coefficient 63 and inside the budget; otherwise (rare) one
-// newly significant coefficient per step.
-template <int RATE, class Tile, class Planes>
-ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
+// newly significant coefficient per step.  SAFE: the tile holds at least
+// three zero words after the budget, so a window may be read at any position
+// before END + 32 without a test.  Stores every plane it reaches (pl.store)
+// and returns the lowest; the planes below stay for the caller to clear.
+template <bool SAFE, class Tile, class Planes>
+ZFPX_HD int parse_planes64(const Tile &tile, int pos, const int END, const int ktop, Planes &pl)
 {
-    constexpr int kSeq[64] = ZFPX_SEQ3;
-    constexpr int END = 64 * RATE;
-    const uint64_t head = tile_peek(tile, 0);
-    if (!(head & 1ull)) {
-#pragma unroll
-        for (int i = 0; i < 64; i++) x[i] = 0.0f;
-        return;
-    }
-    const int e = (int)((head >> 1) & 0xffu);
-    int pos = 9, n = 0, kmin = 32;                               // planes below kmin stay zero
+    int n = 0, kmin = ktop + 1;
     uint64_t lm = 0;                                             // low_mask(n)
 #pragma unroll 1
-    for (int k = 31; k >= 0 && pos < END; k--) {
+    for (int k = ktop; k >= 0 && pos < END; k--) {
         kmin = k;                                                // every pass stores plane k
         const int rem = END - pos;
         const uint64_t w = tile_peek(tile, pos);
@@ -611,7 +606,7 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
             // cut by the budget shows as one that runs on, and only the
             // implied one needs the check that its zeros fit (B bits left).
             uint64_t term;
-            uint64_t V = group_values(kTileZeroRows<RATE> >= 3 || pos < END ? tile_peek(tile, pos) : 0ull, term);
+            uint64_t V = group_values(SAFE || pos < END ? tile_peek(tile, pos) : 0ull, term);
             const uint64_t below = term ? (term & (0ull - term)) - 1ull : ~0ull;   // bits before the closing 0
             const int T = popc64(below);                         // offset of the closing 0 (64: none)
             const int lim = 62 - n;                              // offset - rank of coefficient 62
@@ -661,7 +656,7 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
 #pragma unroll 1
         for (;;) {
             const int r = END - pos;
-            const uint64_t v = kTileZeroRows<RATE> >= 3 || pos < END ? tile_peek(tile, pos) : 0ull;
+            const uint64_t v = SAFE || pos < END ? tile_peek(tile, pos) : 0ull;
             const int lim = 63 - n;
             const int tz = v ? lowest_set(v) : 64;
             if (tz >= lim) {                                     // only the implied one is left
@@ -682,6 +677,26 @@ ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
         if (cut) break;
         lm = low_mask(n);
     }
+    return kmin;
+}
+
+// Decodes one block from this lane's stream tile: its planes by
+// parse_planes64, then the transposes, the inverse transform and the
+// dequantisation.
+template <int RATE, class Tile, class Planes>
+ZFPX_HD void decode_block3_tile(const Tile &tile, float (&x)[64], Planes &pl)
+{
+    constexpr int kSeq[64] = ZFPX_SEQ3;
+    constexpr int END = 64 * RATE;
+    const uint64_t head = tile_peek(tile, 0);
+    if (!(head & 1ull)) {
+#pragma unroll
+        for (int i = 0; i < 64; i++) x[i] = 0.0f;
+        return;
+    }
+    const int e = (int)((head >> 1) & 0xffu);
+    // planes below kmin stay zero
+    const int kmin = parse_planes64<kTileZeroRows<RATE> >= 3>(tile, 9, END, 31, pl);
     uint32_t lo[32], hi[32];
     // Planes below kmin are zero; when that holds for planes 0..kLow-1 in
     // every lane of the warp, the stages smaller than kLow skip them.
