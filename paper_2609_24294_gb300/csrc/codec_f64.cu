@@ -105,6 +105,41 @@ __device__ __forceinline__ int block_exponent(uint64_t amax)
     return E == 0 ? 1 : E + 1;                                   // frexp exponent + 1023
 }
 
+// The quantisation and the dequantisation of the common case in integer
+// operations on the bits: on this GPU the float64 pipe runs at a small
+// fraction of the integer one, and these are the path's only float64
+// arithmetic.  Both give the bits of the float64 formulas exactly (the
+// products by powers of two there are exact, so only the truncation and the
+// one rounding of q to 53 bits remain).
+//
+// q = trunc(x 2^(62 - e_max)), e = e_max + 1023 the block's exponent: x =
+// +-M 2^(E - 1075) with E the biased exponent (taken as 1 for subnormals) and
+// M the significand (with the implicit bit for normals), so |q| is M shifted
+// left by E + 10 - e (at most 10 within the block whose maximum set e) or
+// right by its negative.
+__device__ __forceinline__ int64_t quantize64(uint64_t bits, int e)
+{
+    const int E = (int)((bits >> 52) & 0x7ffu);
+    const uint64_t M = (bits & 0x000fffffffffffffull) | (E ? 0x0010000000000000ull : 0ull);
+    const int t = (E ? E : 1) + 10 - e;
+    const uint64_t a = t >= 0 ? (M << t) : (t > -64 ? (M >> -t) : 0ull);
+    return (bits >> 63) ? (int64_t)(0ull - a) : (int64_t)a;
+}
+
+// x = q 2^(e - 1085) rounded once to nearest even, for e >= 63, where every
+// non-zero result is normal (or, past the largest double, infinite): the one
+// rounding is the conversion of q, and the power-of-two scaling an integer
+// add to the exponent field (infinity where it passes the largest exponent).
+__device__ __forceinline__ double dequantize64_normal(int64_t q, int e)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(__ll2double_rn(q));
+    const int E = (int)((b >> 52) & 0x7ffu);                     // 0 only for q = 0
+    const int ne = E + e - 1085;                                 // >= 1 for q != 0
+    const uint64_t r = ne >= 2047 ? (b & 0x8000000000000000ull) | 0x7ff0000000000000ull
+                                  : b + ((uint64_t)(int64_t)(e - 1085) << 52);
+    return __longlong_as_double((long long)(E ? r : b));
+}
+
 // The 3-D transform on a block held in registers (int64 v[i + 4j + 16k]).
 __device__ __forceinline__ void lift_fwd64r(int64_t &a, int64_t &b, int64_t &c, int64_t &d)
 {
@@ -218,14 +253,8 @@ __global__ void __launch_bounds__(32, kF64MinCtas) encode_f64_kernel(const doubl
             if (!e) {
                 wr.finish();
             } else {
-                // q = trunc(x 2^(62 - e_max)) with e_max = e - 1023, as two
-                // exact power-of-two products (each factor a normal double)
-                const int sh = 62 - (e - 1023);
-                const int s1 = sh > 600 ? 600 : sh;
-                const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
-                const double f2 = __longlong_as_double((long long)(sh - s1 + 1023) << 52);
 #pragma unroll
-                for (int r = 0; r < 64; r++) v[r] = __double2ll_rz((__longlong_as_double(v[r]) * f1) * f2);
+                for (int r = 0; r < 64; r++) v[r] = quantize64((uint64_t)v[r], e);
                 xform3_fwd64(v);
 #pragma unroll
                 for (int r = 0; r < 64; r++) v[r] = (int64_t)(((uint64_t)v[r] + kNega64) ^ kNega64);
@@ -256,7 +285,8 @@ __global__ void __launch_bounds__(32, kF64MinCtas) encode_f64_kernel(const doubl
     }
 }
 
-// x = q 2^(e_max - 62) rounded once to nearest even, e_max = e - 1023.
+// x = q 2^(e_max - 62) rounded once to nearest even, e_max = e - 1023 (every
+// exponent; the kernels take dequantize64_normal where it applies).
 __device__ __forceinline__ double dequantize64(int64_t q, int e)
 {
     const int s = e - 1023 - 62;                                 // x = q 2^s
@@ -349,13 +379,8 @@ __global__ void __launch_bounds__(32, kF64MinCtas) decode_f64_kernel(const uint8
             for (int r = 0; r < 64; r++) v[r] = sub64((int64_t)((uint64_t)v[r] ^ kNega64), (int64_t)kNega64);
             xform3_inv64(v);
             if (e >= 63) {
-                // every non-zero result is normal: (double)q rounds once and
-                // the two power-of-two scalings are exact
-                const int s = e - 1023 - 62, s1 = s < -600 ? -600 : s;
-                const double f1 = __longlong_as_double((long long)(s1 + 1023) << 52);
-                const double f2 = __longlong_as_double((long long)(s - s1 + 1023) << 52);
 #pragma unroll
-                for (int r = 0; r < 64; r++) x[r] = (__ll2double_rn(v[r]) * f1) * f2;
+                for (int r = 0; r < 64; r++) x[r] = dequantize64_normal(v[r], e);
             } else {
                 // tiny exponents (rare): a rolled loop over a local copy
                 int64_t t[64];
