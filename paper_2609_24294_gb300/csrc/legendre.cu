@@ -121,6 +121,60 @@ __global__ void __launch_bounds__(256) legendre_fold_kernel(const float *__restr
     }
 }
 
+// The same fold for fields whose rows start on 16 bytes (latitude and level
+// strides multiples of 4, 16-byte aligned bases): tiles of 128 orders x 32
+// latitudes, every load and store a 16-byte vector (four orders in, four
+// latitudes out).  Block (32, 8).
+__global__ void __launch_bounds__(256) legendre_fold4_kernel(const float *__restrict__ re,
+                                                             const float *__restrict__ im, float *__restrict__ G,
+                                                             LegGeom g)
+{
+    __shared__ float sS[32][129], sA[32][129];          // [latitude][order]
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 32 + tx;
+    const int m0 = blockIdx.x * 128, j0 = blockIdx.y * 32;
+    const int lev = blockIdx.z >> 1, part = blockIdx.z & 1;
+    const float *F = (part ? im : re) + lev * g.is2;
+    const int m = m0 + 4 * tx;
+    for (int i = ty; i < 32; i += 8) {
+        const int j = j0 + i;
+        float a[4] = {0.f, 0.f, 0.f, 0.f}, b[4] = {0.f, 0.f, 0.f, 0.f};
+        if (j < g.nh) {
+            const float *rn = F + (int64_t)j * g.is1, *rs = F + (int64_t)(g.nlat - 1 - j) * g.is1;
+            if (m + 3 <= g.T) {
+                const float4 u = __ldg(reinterpret_cast<const float4 *>(rn + m));
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(rs + m));
+                a[0] = u.x; a[1] = u.y; a[2] = u.z; a[3] = u.w;
+                b[0] = v.x; b[1] = v.y; b[2] = v.z; b[3] = v.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; q++)
+                    if (m + q <= g.T) {
+                        a[q] = __ldg(rn + m + q);
+                        b[q] = __ldg(rs + m + q);
+                    }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            sS[i][4 * tx + q] = a[q] + b[q];
+            sA[i][4 * tx + q] = a[q] - b[q];
+        }
+    }
+    __syncthreads();
+    const int c = part * g.nlev + lev;
+    const int jj = 4 * (t & 7), j = j0 + jj;              // latitudes j .. j + 3 (nhs is a multiple of 4)
+    if (j >= g.nhs) return;
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int k = (t >> 3) + 32 * r, mm = m0 + k;
+        if (mm > g.T) break;
+        const int64_t row = ((int64_t)mm * 2 * g.ncp + c) * g.nhs + j;
+        *reinterpret_cast<float4 *>(G + row) = make_float4(sS[jj][k], sS[jj + 1][k], sS[jj + 2][k], sS[jj + 3][k]);
+        *reinterpret_cast<float4 *>(G + row + (int64_t)g.ncp * g.nhs) =
+            make_float4(sA[jj][k], sA[jj + 1][k], sA[jj + 2][k], sA[jj + 3][k]);
+    }
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // tcgen05 shared-memory descriptor of a K-major, 128-byte-swizzled operand
@@ -638,9 +692,15 @@ int zfpx_legendre_forward(zfpx_legendre p, const float *d_re, const float *d_im,
     int rc = make_tmap(&tmap_g, G, p->nh, grows, p->nhs, g.nt);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    const dim3 fgrid((p->T + 1 + 31) / 32, (p->nhs + 31) / 32, 2 * g.nlev);
-    if (fgrid.z > 65535) return ZFPX_EINVAL;
-    legendre_fold_kernel<<<fgrid, dim3(32, 8), 0, st>>>(d_re, d_im, G, g);
+    if (2 * g.nlev > 65535) return ZFPX_EINVAL;
+    const bool vec4 = stride[1] % 4 == 0 && stride[2] % 4 == 0 && !((uintptr_t)d_re & 15u) && !((uintptr_t)d_im & 15u);
+    if (vec4) {
+        const dim3 fgrid((p->T + 1 + 127) / 128, (p->nhs + 31) / 32, 2 * g.nlev);
+        legendre_fold4_kernel<<<fgrid, dim3(32, 8), 0, st>>>(d_re, d_im, G, g);
+    } else {
+        const dim3 fgrid((p->T + 1 + 31) / 32, (p->nhs + 31) / 32, 2 * g.nlev);
+        legendre_fold_kernel<<<fgrid, dim3(32, 8), 0, st>>>(d_re, d_im, G, g);
+    }
     count_launch();
     rc = check_launch();
     if (rc) return rc;
