@@ -379,7 +379,7 @@ def extra_batched(z, reps, peak, lens, fields):
         del bufs
     res = {"workload": "O1280 octahedral, 10 fields, 868 levels, 5.73e9 values (22.9 GB), rates 8/16, dims 1/3",
            "launch": {"warps_per_cta": choice[0], "ctas_per_sm": choice[1], "blocks_per_lane_1d": choice[2],
-                      "tuned_ms": timings},
+                      "units_per_claim": choice[3], "tuned_ms": timings},
            "encode_ms": enc_ms, "decode_ms": dec_ms,
            "encode_f32_GBps": f32_bytes / (enc_ms / 1e3) / 1e9, "decode_f32_GBps": f32_bytes / (dec_ms / 1e3) / 1e9,
            "encode_frac_of_measured_hbm": moved / (enc_ms / 1e3) / 1e9 / peak,

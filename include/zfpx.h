@@ -403,6 +403,11 @@ ZFPX_API int zfpx_batch_set_launch(zfpx_batch batch, int warps_per_cta, int ctas
  * waiting for the device to go idle.  Picked by the autotuner; results never
  * depend on it.  Errors: ZFPX_EINVAL, ZFPX_ECUDA, ZFPX_ENOMEM. */
 ZFPX_API int zfpx_batch_set_unit_blocks(zfpx_batch batch, int blocks_per_lane_1d);
+/* Work units a warp claims at a time from its kind's queue (1..64, default
+ * 4): one atomic add per claim.  More units per claim spend fewer atomics,
+ * fewer balance the end of a launch better.  Picked by the autotuner; results
+ * never depend on it.  Errors: ZFPX_EINVAL. */
+ZFPX_API int zfpx_batch_set_claim_units(zfpx_batch batch, int units_per_claim);
 ZFPX_API int zfpx_batch_encode(zfpx_batch batch, uint8_t *d_out, size_t cap, void *stream);
 ZFPX_API int zfpx_batch_decode(zfpx_batch batch, const uint8_t *d_in, size_t len, void *stream);
 
@@ -432,6 +437,9 @@ ZFPX_API int zfpx_server_set_launch(zfpx_server server, int warps_per_cta, int c
 /* The 1-D work-unit size of zfpx_batch_set_unit_blocks, for batches launched
  * from then on.  Errors: ZFPX_EINVAL. */
 ZFPX_API int zfpx_server_set_unit_blocks(zfpx_server server, int blocks_per_lane_1d);
+/* The units per claim of zfpx_batch_set_claim_units, for batches launched from
+ * then on.  Errors: ZFPX_EINVAL. */
+ZFPX_API int zfpx_server_set_claim_units(zfpx_server server, int units_per_claim);
 ZFPX_API int zfpx_server_submit(zfpx_server server, const zfpx_field *request, int64_t *id);
 ZFPX_API int zfpx_server_pump(zfpx_server server, int *launched);
 ZFPX_API int zfpx_server_poll(zfpx_server server, int64_t *done, int max, int *ndone);

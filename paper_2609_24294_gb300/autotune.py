@@ -12,7 +12,8 @@ Candidates:
   shared-memory tiles and the scheduling granularity) x CTAs per SM (1..as many as fit: fewer
   CTAs leave more L1 per block, more CTAs hide latency); then, for batches
   with 1-D fields, the 1-D blocks each lane codes per work unit (fewer claims
-  and searches per block against balance on short batches);
+  and searches per block against balance on short batches); then the work
+  units a warp claims at a time (fewer atomics against a shorter tail);
 * plan codec kernels (3-D blocks): consecutive 32-block units per warp (the
   blocks-per-warp knob; each CTA of the grid codes units-per-warp x warps
   units, so it also sets the grid size), per direction and rate.
@@ -29,6 +30,8 @@ CACHE = os.environ.get("ZFPX_TUNE_CACHE", os.path.join(os.path.expanduser("~"), 
 BATCH_CANDIDATES = [(3, 0), (2, 0), (4, 0), (3, 3), (8, 0)]
 LB1_DEFAULT = 16
 LB1_CANDIDATES = (2, 4, 8, 16, 32)
+UPC_DEFAULT = 4
+UPC_CANDIDATES = (1, 2, 4, 8)
 UPW_CANDIDATES = (1, 2, 3, 4, 8)
 
 
@@ -80,18 +83,21 @@ def time_call(fn, reps=3, warmup=1, stream=None):
 
 def tune_batch(batch, specs, out, candidates=None, lb1_candidates=None, reps=3, use_cache=True):
     """Picks (warps per CTA, CTAs per SM) for batch encode + decode, then the
-    1-D blocks per lane if any spec (nlev, dims, rate) has dims 1; returns
-    ((warps, ctas, blocks_per_lane_1d), {candidate: ms})."""
+    1-D blocks per lane if any spec (nlev, dims, rate) has dims 1, then the
+    units per claim; returns ((warps, ctas, blocks_per_lane_1d,
+    units_per_claim), {candidate: ms})."""
     key = batch_signature(batch, specs) + "@" + _device_key()
     cache = _load() if use_cache else {}
-    if use_cache and key in cache and len(cache[key]["choice"]) == 3:
-        w, c, l1 = cache[key]["choice"]
+    if use_cache and key in cache and len(cache[key]["choice"]) == 4:
+        w, c, l1, uc = cache[key]["choice"]
         batch.set_launch(w, c)
         batch.set_unit_blocks(l1)
-        return (w, c, l1), cache[key].get("timings", {})
+        batch.set_claim_units(uc)
+        return (w, c, l1, uc), cache[key].get("timings", {})
     timings = {}
     both = lambda: (batch.encode(out), batch.decode(out))
     batch.set_unit_blocks(LB1_DEFAULT)
+    batch.set_claim_units(UPC_DEFAULT)
     for (w, c) in (candidates or BATCH_CANDIDATES):
         batch.set_launch(w, c)
         timings["%d,%d" % (w, c)] = time_call(both, reps=reps)
@@ -109,10 +115,20 @@ def tune_batch(batch, specs, out, candidates=None, lb1_candidates=None, reps=3, 
             if ms < best_ms:
                 l1, best_ms = cand, ms
         batch.set_unit_blocks(l1)
+    uc = UPC_DEFAULT
+    for cand in UPC_CANDIDATES:
+        if cand == UPC_DEFAULT:
+            continue
+        batch.set_claim_units(cand)
+        ms = time_call(both, reps=reps)
+        timings["%d,%d,lb%d,upc%d" % (w, c, l1, cand)] = ms
+        if ms < best_ms:
+            uc, best_ms = cand, ms
+    batch.set_claim_units(uc)
     if use_cache:
-        cache[key] = {"choice": [w, c, l1], "timings": timings}
+        cache[key] = {"choice": [w, c, l1, uc], "timings": timings}
         _store(cache)
-    return (w, c, l1), timings
+    return (w, c, l1, uc), timings
 
 
 def plan_signature(plan, rate):

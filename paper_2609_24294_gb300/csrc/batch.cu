@@ -83,6 +83,7 @@ struct BatchGeom {
     GroupDev groups[kMaxGroups];
     int ngroups;
     int lb1;              // 1-D units: 32 lb1 blocks, lb1 per lane
+    int upc;              // units a warp claims at a time (one atomic per claim)
     uint32_t *ctr;        // ngroups work counters, zero at launch
 };
 
@@ -109,7 +110,8 @@ __device__ __forceinline__ void fill_plane4(const BatchGeom &bg, Tab &tab)
 
 // Work distribution of the batch kernels.  A batch with no more units than
 // the grid has warps gives each warp one unit.  Otherwise each (dims, rate)
-// group is a queue of 32-block units claimed one at a time by whole warps.  A CTA starts on
+// group is a queue of units claimed upc at a time (one atomic add per claim)
+// by whole warps.  A CTA starts on
 // its home group -- the SMs are split between groups in proportion to their
 // work, so an SM mostly runs one kind's code and keeps it in its instruction
 // cache -- and then helps the other groups until every queue is empty.
@@ -136,16 +138,22 @@ __device__ __forceinline__ void for_each_unit(const BatchGeom &bg, int lane, Fn 
         const int gi = (home + t) % bg.ngroups;
         const GroupDev G = bg.groups[gi];
         uint32_t *ctr = bg.ctr + gi;
+        const uint32_t C = (uint32_t)bg.upc;
         uint32_t u = 0;
-        if (lane == 0) u = atomicAdd(ctr, 1u);
+        if (lane == 0) u = atomicAdd(ctr, C);
         u = __shfl_sync(0xffffffffu, u, 0);
         while ((int64_t)u < G.n) {
             uint32_t next = 0;                                   // claimed ahead: its latency hides behind fn
-            if (lane == 0) next = atomicAdd(ctr, 1u);
+            if (lane == 0) next = atomicAdd(ctr, C);
             next = __shfl_sync(0xffffffffu, next, 0);
-            const int64_t c = G.u0 + u;
-            const int ii = item_of_unit(bg.items, bg.nitems, c);
-            fn(G, c, ii);
+            // the claim's units in order; a unit's item is the last one starting at or before it
+            const uint32_t ue = (uint32_t)min((int64_t)u + C, G.n);
+            int ii = item_of_unit(bg.items, bg.nitems, G.u0 + u);
+            for (uint32_t v = u; v < ue; v++) {
+                const int64_t c = G.u0 + v;
+                while (ii + 1 < bg.nitems && __ldg(&bg.items[ii + 1].unit0) <= c) ii++;
+                fn(G, c, ii);
+            }
             u = next;
         }
     }
@@ -512,6 +520,8 @@ int64_t field_stream_bytes(const GridHost &g, const zfpx_field &F, int r0, int r
 // Blocks of one work unit: 32 for 3-D items (one per lane), 32 lb1 for 1-D.
 constexpr int kDefaultLb1 = 16;
 constexpr int kMaxLb1 = 64;
+constexpr int kDefaultUpc = 4;
+constexpr int kMaxUpc = 64;
 inline int64_t unit_blocks(int dims, int lb1) { return dims == 3 ? 32 : 32 * (int64_t)lb1; }
 
 // Field and item descriptors of a set of fields whose streams start at the
@@ -593,10 +603,11 @@ void build_work(const GridHost &g, const zfpx_field *fields, const int64_t *stre
 }
 
 BatchGeom make_geom(const FieldDevB *d_fields, const ItemDevB *d_items, const GridDev &grid, int nitems,
-                    int64_t nunits, const std::vector<GroupDev> &groups, int lb1, uint32_t *d_ctr)
+                    int64_t nunits, const std::vector<GroupDev> &groups, int lb1, int upc, uint32_t *d_ctr)
 {
     BatchGeom g;
     g.lb1 = lb1;
+    g.upc = upc;
     g.items = d_items;
     g.fields = d_fields;
     g.grid = grid;
@@ -657,6 +668,7 @@ struct zfpx_batch_s {
     int64_t nunits = 0;
     int warps = 3, ctas_per_sm = 0;     // 0 = as many as fit
     int lb1 = zfpx::kDefaultLb1;        // 1-D blocks per lane of a unit
+    int upc = zfpx::kDefaultUpc;        // units per work claim
     zfpx::FieldDevB *d_fields = nullptr;
     zfpx::ItemDevB *d_items = nullptr;
     std::vector<zfpx::GroupDev> groups;
@@ -746,6 +758,13 @@ int zfpx_batch_set_launch(zfpx_batch b, int warps_per_cta, int ctas_per_sm)
     return ZFPX_OK;
 }
 
+int zfpx_batch_set_claim_units(zfpx_batch b, int units_per_claim)
+{
+    if (!b || units_per_claim < 1 || units_per_claim > kMaxUpc) return ZFPX_EINVAL;
+    b->upc = units_per_claim;
+    return ZFPX_OK;
+}
+
 int zfpx_batch_set_unit_blocks(zfpx_batch b, int blocks_per_lane_1d)
 {
     if (!b || blocks_per_lane_1d < 1 || blocks_per_lane_1d > kMaxLb1) return ZFPX_EINVAL;
@@ -761,7 +780,7 @@ static int batch_geom(zfpx_batch b, bool encode, cudaStream_t st, BatchGeom &g)
 {
     uint32_t *ctr = b->d_ctr + (encode ? 0 : kMaxGroups);
     if (cudaMemsetAsync(ctr, 0, kMaxGroups * sizeof(uint32_t), st) != cudaSuccess) return ZFPX_ECUDA;
-    g = make_geom(b->d_fields, b->d_items, b->grid.dev(), b->nitems, b->nunits, b->groups, b->lb1, ctr);
+    g = make_geom(b->d_fields, b->d_items, b->grid.dev(), b->nitems, b->nunits, b->groups, b->lb1, b->upc, ctr);
     return ZFPX_OK;
 }
 
@@ -876,6 +895,7 @@ struct zfpx_server_s {
     int max_batch = 64;
     int warps = 3, ctas_per_sm = 0;
     int lb1 = zfpx::kDefaultLb1;
+    int upc = zfpx::kDefaultUpc;
     std::deque<int64_t> completed;
     int64_t batches = 0;
 };
@@ -933,6 +953,13 @@ int zfpx_server_set_launch(zfpx_server s, int warps_per_cta, int ctas_per_sm)
     if (!s || !batch_warps_ok(warps_per_cta) || ctas_per_sm < 0) return ZFPX_EINVAL;
     s->warps = warps_per_cta;
     s->ctas_per_sm = ctas_per_sm;
+    return ZFPX_OK;
+}
+
+int zfpx_server_set_claim_units(zfpx_server s, int units_per_claim)
+{
+    if (!s || units_per_claim < 1 || units_per_claim > kMaxUpc) return ZFPX_EINVAL;
+    s->upc = units_per_claim;                 // applies to batches launched from now on
     return ZFPX_OK;
 }
 
@@ -1033,8 +1060,8 @@ int zfpx_server_pump(zfpx_server s, int *launched)
     uint32_t *ctr = reinterpret_cast<uint32_t *>(sl.d_desc + coff);
     const FieldDevB *dfd = reinterpret_cast<const FieldDevB *>(sl.d_desc);
     const ItemDevB *dit = reinterpret_cast<const ItemDevB *>(sl.d_desc + ioff);
-    const BatchGeom ge = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1, ctr);
-    const BatchGeom gd = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1,
+    const BatchGeom ge = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1, s->upc, ctr);
+    const BatchGeom gd = make_geom(dfd, dit, s->grid.dev(), (int)items.size(), units, groups, s->lb1, s->upc,
                                    ctr + kMaxGroups);
     int rc = launch_batch(ge, s->warps, s->ctas_per_sm, true, nullptr, s->d_arena, sl.stream);
     if (!rc) rc = launch_batch(gd, s->warps, s->ctas_per_sm, false, s->d_arena, nullptr, sl.stream);

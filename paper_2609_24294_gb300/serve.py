@@ -31,6 +31,9 @@ class Server:
     def set_unit_blocks(self, blocks_per_lane_1d):
         z._check(z.lib().zfpx_server_set_unit_blocks(self._h, blocks_per_lane_1d), "zfpx_server_set_unit_blocks")
 
+    def set_claim_units(self, units_per_claim):
+        z._check(z.lib().zfpx_server_set_claim_units(self._h, units_per_claim), "zfpx_server_set_claim_units")
+
     def submit(self, src, lev_stride, nlev, dims, rate, row0, row1):
         """src: device pointer (int) of level 0, first point of row row0."""
         f = z.Field()

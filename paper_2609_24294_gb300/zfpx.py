@@ -95,6 +95,7 @@ def lib():
         "zfpx_server_destroy": ([vp], None),
         "zfpx_server_set_launch": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_server_set_unit_blocks": ([vp, ctypes.c_int], ctypes.c_int),
+        "zfpx_server_set_claim_units": ([vp, ctypes.c_int], ctypes.c_int),
         "zfpx_server_submit": ([vp, ctypes.POINTER(Field), i64p], ctypes.c_int),
         "zfpx_server_pump": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "zfpx_server_poll": ([vp, i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -114,6 +115,7 @@ def lib():
         "zfpx_batch_field_bytes": ([vp, ctypes.c_int], sz),
         "zfpx_batch_set_launch": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_batch_set_unit_blocks": ([vp, ctypes.c_int], ctypes.c_int),
+        "zfpx_batch_set_claim_units": ([vp, ctypes.c_int], ctypes.c_int),
         "zfpx_batch_encode": ([vp, vp, sz, vp], ctypes.c_int),
         "zfpx_batch_decode": ([vp, vp, sz, vp], ctypes.c_int),
         "zfpx_graph_num_kernels": ([vp], ctypes.c_int),
@@ -651,6 +653,9 @@ class Batch:
 
     def set_unit_blocks(self, blocks_per_lane_1d):
         _check(lib().zfpx_batch_set_unit_blocks(self._h, blocks_per_lane_1d), "zfpx_batch_set_unit_blocks")
+
+    def set_claim_units(self, units_per_claim):
+        _check(lib().zfpx_batch_set_claim_units(self._h, units_per_claim), "zfpx_batch_set_claim_units")
 
     def encode(self, out, stream=None):
         _check(lib().zfpx_batch_encode(self._h, _dev(out, "out"), _nbytes(out), _stream(stream)), "zfpx_batch_encode")

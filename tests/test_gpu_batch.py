@@ -22,8 +22,12 @@ SPECS = [(9, "temperature", 3, 8), (6, "power", 3, 16), (1, "humidity", 1, 8), (
          (2, "power", 1, 16), (3, "temperature", 3, 16)]
 
 
-@pytest.mark.parametrize("N,warps,lb1", [(6, 4, 8), (13, 8, 8), (13, 4, 1), (13, 4, 3), (6, 8, 64)])
-def test_batch_matches_oracle(z, N, warps, lb1):
+# (grid N, warps per CTA, CTAs per SM, 1-D blocks per lane, units per claim); one CTA per SM on the
+# N = 96 grid gives fewer warps than work units, so warps claim their units from the queues
+@pytest.mark.parametrize("N,warps,ctas,lb1,upc", [(6, 4, 0, 8, 4), (13, 8, 0, 8, 1), (13, 4, 0, 1, 3),
+                                                  (13, 4, 0, 3, 64), (6, 8, 0, 64, 2), (13, 2, 0, 16, 4),
+                                                  (96, 2, 1, 4, 3), (96, 3, 1, 1, 1), (96, 2, 1, 2, 8)])
+def test_batch_matches_oracle(z, N, warps, ctas, lb1, upc):
     lens = og.row_lengths(N)
     if N == 13:
         lens = lens[:-2]                         # a partial last row-quad
@@ -37,8 +41,9 @@ def test_batch_matches_oracle(z, N, warps, lb1):
         dsts.append(torch.full_like(srcs[-1], float("nan")))
         specs.append((nlev, dims, rate))
     b = z.Batch(lens, [(s, d, dims, rate) for s, d, (_, dims, rate) in zip(srcs, dsts, specs)])
-    b.set_launch(warps, 0)
+    b.set_launch(warps, ctas)
     b.set_unit_blocks(lb1)                      # 1-D blocks per lane of a work unit
+    b.set_claim_units(upc)                      # work units per claim
     ref = ob.encode_batch(host, lens, specs)
     assert b.nbytes() == ref.size
     out = torch.zeros(b.nbytes(), dtype=torch.uint8, device="cuda")
