@@ -307,8 +307,9 @@ ZFPX_API int zfpx_decompress_rfft(zfpx_plan plan, int rate, const uint8_t *d_rec
  * out_stride floats apart (>= (T+1)(T+2)/2).
  * zfpx_legendre_create builds the plan on the current device: the Gauss
  * nodes and weights and the table w_j Pbar_l^m(mu_j) over the northern half
- * (computed in double, rounded once; about (T+1)(T+2) nlat bytes of device
- * memory, a synchronous upload); nlat even, at most 32768, T + 1 <= nlat.
+ * (computed in double, rounded once) with its TF32 low parts for the tensor
+ * cores (about 2 (T+1)(T+2) nlat bytes of device memory in all, a
+ * synchronous upload); nlat even, at most 32768, T + 1 <= nlat.
  * zfpx_legendre_forward takes n[1] equal to the plan's nlat and 1 .. 2^20
  * levels, and needs caller-owned device scratch d_work (16-byte aligned) of
  * zfpx_legendre_workspace_bytes(plan, levels) bytes; calls that share d_work
