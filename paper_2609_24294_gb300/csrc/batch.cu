@@ -12,10 +12,11 @@
 // in level order, inside an item the blocks in row (row-quad) order then along
 // x; fields at 256-byte aligned offsets.
 //
-// Work list: every (field, item) is split into chunks of 32 consecutive blocks
-// (one per lane); chunks are sorted so that fields of one (dims, rate) class
-// are contiguous, and each warp of the persistent grid takes a contiguous
-// range of chunks.  The class is uniform across a warp.
+// Work list: every (field, item) is split into work units of consecutive
+// blocks (3-D: 32, one per lane; 1-D: 32 lb1, lb1 per lane); units are sorted
+// so that fields of one (dims, rate) class are contiguous, each class a queue
+// that warps of the persistent grid claim units from (for_each_unit below).
+// The class is uniform across a warp.
 #include <algorithm>
 #include <chrono>
 #include <climits>
