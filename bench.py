@@ -423,6 +423,14 @@ def extra_serving(z, peak, lens, fields, n=2000, rate_hz=50e3, arena=40 << 30):
            "mean_ms": float(lat.mean() * 1e3), "wall_ms": wall * 1e3, "f32_GBps_sustained": total / wall / 1e9,
            "offered_GBps": total * rate_hz / n / 1e9, "batches": nbatch, "requests_per_batch": n / max(nbatch, 1),
            "max_streams_busy": busy_max}
+    # the same arrivals with a batching window (launch at 8 waiting requests or after 200 us)
+    srv.set_batching(8, 200.0)
+    lat_w, wall_w, _, nb_w = serve.run_requests_native(srv, calls, arrivals=arrivals)
+    srv.set_batching(1, 0.0)
+    res["window_8_or_200us"] = {"p50_ms": float(np.percentile(lat_w, 50) * 1e3),
+                                "p99_ms": float(np.percentile(lat_w, 99) * 1e3),
+                                "f32_GBps_sustained": total / wall_w / 1e9, "batches": nb_w,
+                                "requests_per_batch": n / max(nb_w, 1)}
     # capacity: every request submitted at once, the engine batching as fast as it can
     _, wall_cap, _, nb_cap = serve.run_requests_native(srv, calls)
     res["capacity_f32_GBps"] = total / wall_cap / 1e9

@@ -438,6 +438,13 @@ ZFPX_API int zfpx_server_set_launch(zfpx_server server, int warps_per_cta, int c
 /* The 1-D work-unit size of zfpx_batch_set_unit_blocks, for batches launched
  * from then on.  Errors: ZFPX_EINVAL. */
 ZFPX_API int zfpx_server_set_unit_blocks(zfpx_server server, int blocks_per_lane_1d);
+/* A batching window for zfpx_server_pump: a batch is launched once at least
+ * min_requests requests wait, or once the oldest waiting one has waited
+ * max_wait_us microseconds (1 and 0, the defaults, launch whatever waits as
+ * soon as a stream is free).  A window trades latency for larger batches
+ * when requests arrive slower than the device codes them.  min_requests <=
+ * max_batch, 0 <= max_wait_us <= 1e7.  Errors: ZFPX_EINVAL. */
+ZFPX_API int zfpx_server_set_batching(zfpx_server server, int min_requests, double max_wait_us);
 /* The units per claim of zfpx_batch_set_claim_units, for batches launched from
  * then on.  Errors: ZFPX_EINVAL. */
 ZFPX_API int zfpx_server_set_claim_units(zfpx_server server, int units_per_claim);

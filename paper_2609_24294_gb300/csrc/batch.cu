@@ -836,6 +836,7 @@ struct ServerReq {
     int64_t stream_bytes, values_bytes, mem_bytes;
     int64_t mem_off = -1;    // arena offset (stream, then values)
     int state = 0;           // 0 queued, 1 in flight, 2 done
+    std::chrono::steady_clock::time_point t_submit;
 };
 
 struct ServerSlot {
@@ -897,6 +898,8 @@ struct zfpx_server_s {
     int warps = 3, ctas_per_sm = 0;
     int lb1 = zfpx::kDefaultLb1;
     int upc = zfpx::kDefaultUpc;
+    int min_batch = 1;                  // batching window: launch at min_batch waiting requests
+    double max_wait_s = 0.0;            // ... or once the oldest has waited this long
     std::deque<int64_t> completed;
     int64_t batches = 0;
 };
@@ -957,6 +960,15 @@ int zfpx_server_set_launch(zfpx_server s, int warps_per_cta, int ctas_per_sm)
     return ZFPX_OK;
 }
 
+int zfpx_server_set_batching(zfpx_server s, int min_requests, double max_wait_us)
+{
+    if (!s || min_requests < 1 || min_requests > s->max_batch || !(max_wait_us >= 0.0) || max_wait_us > 1e7)
+        return ZFPX_EINVAL;
+    s->min_batch = min_requests;
+    s->max_wait_s = max_wait_us * 1e-6;
+    return ZFPX_OK;
+}
+
 int zfpx_server_set_claim_units(zfpx_server s, int units_per_claim)
 {
     if (!s || units_per_claim < 1 || units_per_claim > kMaxUpc) return ZFPX_EINVAL;
@@ -987,6 +999,7 @@ int zfpx_server_submit(zfpx_server s, const zfpx_field *req, int64_t *id)
     r.mem_bytes = (r.stream_bytes + 255) / 256 * 256 + (r.values_bytes + 255) / 256 * 256;
     if (r.mem_bytes > s->arena.total) return ZFPX_ENOMEM_BUDGET;
     const int64_t rid = s->next_id++;
+    r.t_submit = std::chrono::steady_clock::now();
     s->reqs.emplace(rid, r);
     s->queue.push_back(rid);
     *id = rid;
@@ -1013,6 +1026,12 @@ int zfpx_server_pump(zfpx_server s, int *launched)
     if (launched) *launched = 0;
     server_reap(s);
     if (s->queue.empty()) return ZFPX_OK;
+    // the batching window: wait for min_batch requests unless the oldest has waited max_wait
+    if ((int)s->queue.size() < s->min_batch) {
+        const double waited = std::chrono::duration<double>(std::chrono::steady_clock::now() -
+                                                            s->reqs[s->queue.front()].t_submit).count();
+        if (waited < s->max_wait_s) return ZFPX_OK;
+    }
     // the next stream whose previous batch has finished
     int si = -1;
     for (int t = 0; t < (int)s->slots.size(); t++) {

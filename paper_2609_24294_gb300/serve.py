@@ -31,6 +31,11 @@ class Server:
     def set_unit_blocks(self, blocks_per_lane_1d):
         z._check(z.lib().zfpx_server_set_unit_blocks(self._h, blocks_per_lane_1d), "zfpx_server_set_unit_blocks")
 
+    def set_batching(self, min_requests=1, max_wait_us=0.0):
+        """Batching window: launch once min_requests wait or the oldest has waited max_wait_us."""
+        z._check(z.lib().zfpx_server_set_batching(self._h, int(min_requests), float(max_wait_us)),
+                 "zfpx_server_set_batching")
+
     def set_claim_units(self, units_per_claim):
         z._check(z.lib().zfpx_server_set_claim_units(self._h, units_per_claim), "zfpx_server_set_claim_units")
 

@@ -96,6 +96,7 @@ def lib():
         "zfpx_server_set_launch": ([vp, ctypes.c_int, ctypes.c_int], ctypes.c_int),
         "zfpx_server_set_unit_blocks": ([vp, ctypes.c_int], ctypes.c_int),
         "zfpx_server_set_claim_units": ([vp, ctypes.c_int], ctypes.c_int),
+        "zfpx_server_set_batching": ([vp, ctypes.c_int, ctypes.c_double], ctypes.c_int),
         "zfpx_server_submit": ([vp, ctypes.POINTER(Field), i64p], ctypes.c_int),
         "zfpx_server_pump": ([vp, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "zfpx_server_poll": ([vp, i64p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),

@@ -124,3 +124,29 @@ def test_native_loop_matches_python_loop(z):
     lat3, _, _, _ = serve.run_requests_native(small, [big])
     assert np.isnan(lat3).all()
     small.close()
+
+
+def test_batching_window(z):
+    """With a batching window (launch at 6 waiting requests or after 300 us)
+    requests share batches at an arrival rate the device outpaces, every one
+    finishes, and each result is the one the default mode gives."""
+    from paper_2609_24294_gb300 import serve
+    lens, specs, fields, reqs, calls = _setup()
+    srv = serve.Server(lens, arena_bytes=64 << 20, nstreams=4, max_batch=16)
+    _, _, _, plain = serve.run_requests(srv, calls, keep_results=True)
+    b0 = srv.stats()["batches"]
+    srv.set_batching(6, 300.0)
+    arrivals = np.cumsum(np.full(len(calls), 20e-6))                # 50k requests/s
+    lat, wall, busy, nb = serve.run_requests_native(srv, calls, arrivals=arrivals)
+    assert np.all(np.isfinite(lat)) and nb >= 1
+    assert len(calls) / nb >= 3                                      # batches are shared
+    _, _, _, windowed = serve.run_requests(srv, calls, keep_results=True)
+    for (sa, va), (sb, vb) in zip(plain, windowed):
+        assert sa.tobytes() == sb.tobytes() and np.array_equal(va.view(np.uint32), vb.view(np.uint32))
+    with pytest.raises(z.ZfpxError):
+        srv.set_batching(17, 0.0)                                    # above max_batch
+    with pytest.raises(z.ZfpxError):
+        srv.set_batching(1, -1.0)
+    srv.set_batching(1, 0.0)
+    assert srv.stats()["batches"] > b0
+    srv.close()
