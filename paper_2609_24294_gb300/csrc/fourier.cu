@@ -42,15 +42,15 @@ __global__ void __launch_bounds__(32 * kMaxWarps, 3) rfft_lon_kernel(const float
                                                                 float *__restrict__ im, const float2 *__restrict__ tw,
                                                                 FftGeom g)
 {
-    extern __shared__ float2 fsm[];
+    extern __shared__ __align__(16) float2 fsm[];
     const int H = g.H, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     float2 *const buf = fsm + (size_t)wid * 2 * H;
     for (int64_t gr = (int64_t)blockIdx.x * nw + wid; gr < g.nrows; gr += (int64_t)gridDim.x * nw) {
         const int64_t y = gr % g.ny, z = gr / g.ny;
         // the row in, as H complex values (8-byte aligned pairs)
         const float2 *src = reinterpret_cast<const float2 *>(in + z * g.is2 + y * g.is1);
-#pragma unroll 4
-        for (int k = lane; k < H; k += 32) buf[k] = __ldg(src + k);
+        load_row_async(buf, src, H, lane);
+        wait_rows();
         __syncwarp();
         rfft_row(buf, buf + H, tw, g, lane, re + z * g.os2 + y * g.os1, im + z * g.os2 + y * g.os1);
     }

@@ -114,7 +114,8 @@ decode_rfft_kernel(const uint8_t *__restrict__ in, const FusedMsg *__restrict__ 
             const int k = r >> 2, j = r & 3;
             if (k >= U.nzr || j >= U.nyr) continue;
             const float2 *src = reinterpret_cast<const float2 *>(rows + (size_t)r * NP);
-            for (int q = lane; q < fg.H; q += 32) X[q] = src[q];
+            fft::load_row_async(X, src, fg.H, lane);
+            fft::wait_rows();
             __syncwarp();
             const int64_t o = (int64_t)(U.z0 + k) * os2 + (int64_t)(U.y0 + j) * os1;
             fft::rfft_row(X, Y, tw, fg, lane, re + o, im + o);

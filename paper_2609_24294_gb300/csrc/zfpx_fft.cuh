@@ -120,6 +120,26 @@ __device__ __forceinline__ void fft_stage(const float2 *x, float2 *y, const floa
 }
 
 
+// A row of H complex values (8-byte aligned) into shared memory by
+// asynchronous copies, every copy of the lane in flight at once (16 bytes each
+// when both addresses are on 16 bytes and H is even, else 8), as one commit
+// group; wait_rows() waits for the lane's groups.
+__device__ __forceinline__ void load_row_async(float2 *dst, const float2 *src, int H, int lane)
+{
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(dst);
+    if (((((uint32_t)(uintptr_t)src) | s) & 15u) == 0 && (H & 1) == 0) {
+        for (int k = lane; k < H / 2; k += 32)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s + 16u * (uint32_t)k), "l"(src + 2 * k)
+                         : "memory");
+    } else {
+        for (int k = lane; k < H; k += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s + 8u * (uint32_t)k), "l"(src + k)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void wait_rows() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // One row: X holds the H complex values z_k = x_2k + i x_2k+1 on entry; Y is
 // scratch of H values; writes X_m / N, m < K, to ore / oim.  One warp.
 __device__ __forceinline__ void rfft_row(float2 *X, float2 *Y, const float2 *__restrict__ tw, const FftGeom &g,
