@@ -259,14 +259,18 @@ __global__ void __launch_bounds__(32, kF64MinCtas) encode_f64_kernel(const doubl
 #pragma unroll
                 for (int r = 0; r < 64; r++) v[r] = (int64_t)(((uint64_t)v[r] + kNega64) ^ kNega64);
                 // the 64 planes by quadrant: bits 32 hb .. 32 hb + 31 of the
-                // coefficients 32 ch .. 32 ch + 31 in coding order
+                // coefficients 32 ch .. 32 ch + 31 in coding order.  The loop over
+                // ch stays rolled (a select picks the coefficient): half the code
+                // of four unrolled quadrants, which the instruction cache holds
+                // better beside the unrolled lifting
 #pragma unroll
                 for (int hb = 0; hb < 2; hb++)
-#pragma unroll
+#pragma unroll 1
                     for (int ch = 0; ch < 2; ch++) {
                         uint32_t w[32];
 #pragma unroll
-                        for (int t = 0; t < 32; t++) w[t] = (uint32_t)((uint64_t)v[kSeq[32 * ch + t]] >> (32 * hb));
+                        for (int t = 0; t < 32; t++)
+                            w[t] = (uint32_t)((uint64_t)(ch ? v[kSeq[32 + t]] : v[kSeq[t]]) >> (32 * hb));
                         transpose32(w);
 #pragma unroll
                         for (int k = 0; k < 32; k++) pl.store_half(32 * hb + k, ch, w[k]);
