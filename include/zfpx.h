@@ -196,6 +196,21 @@ ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[
 ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                 const int64_t stride[3], float *d_out, void *stream);
 
+/* ---- debug report of non-finite inputs -------------------------------------
+ * The paper leaves infinities and NaNs in the input unspecified.  The codec
+ * codes a block whose largest magnitude is not finite as a zero block (a single
+ * 0 bit; it decodes to zeros) and never faults on one; this call reports such
+ * inputs.  It adds to *d_count (a device counter that the caller owns, zeroes
+ * and reads) the number of elements of the view (extents n[], element strides
+ * stride[] >= 0, axis 0 fastest) whose exponent field is all ones, i.e. the
+ * infinities and NaNs.  elem_bytes: 4 for float32, 8 for float64; d_src
+ * aligned to it, d_count to 8 bytes.  Asynchronous on `stream`; it is a call
+ * of its own, so the codec calls pay nothing for it.  An empty view adds 0 and
+ * launches nothing.  Errors: ZFPX_EINVAL (NULL, a negative extent or stride,
+ * elem_bytes not 4 or 8, misaligned pointers), ZFPX_ECUDA. */
+ZFPX_API int zfpx_count_nonfinite(const void *d_src, int elem_bytes, const int64_t n[3], const int64_t stride[3],
+                                  unsigned long long *d_count, void *stream);
+
 /* ---- accuracy and precision modes: variable rate (3-D blocks) --------------
  * The ZFP mode the paper names and leaves for future work (Sec. II-C).  Every
  * 4x4x4 block (raster order, partial blocks edge-replicated as in the raw

@@ -5,6 +5,8 @@
 // cast comparator (Sec. I; Sec. IV-D counts its cost as nil; Sec. IV-F
 // measures its error by a round trip through float16).  zfpx_permute: the all-to-all of
 // Sec. II-B on one device, recv[dst][src] <- send[src][dst].
+// zfpx_count_nonfinite: the debug report of non-finite inputs, which the
+// codec codes as zero blocks (the paper leaves such inputs unspecified).
 //
 // All three are pure data movement, bound by HBM bandwidth: every lane moves
 // one 16-byte quad (4 values, or 16 stream bytes) per step, warps take
@@ -231,6 +233,27 @@ int run_quads(zfpx_plan p, int mode, int rate, const void *in, void *out, int la
     return check_launch();
 }
 
+// Number of elements of a strided view whose exponent field is all ones (the
+// infinities and NaNs; U = uint32_t for float32, uint64_t for float64): a
+// grid-stride loop over the view's elements in raster order, a warp sum,
+// one atomic add per warp into *out.
+template <class U>
+__global__ void __launch_bounds__(kThreads) count_nonfinite_kernel(const U *__restrict__ src, int64_t n0, int64_t n1,
+                                                                   int64_t total, int64_t s0, int64_t s1, int64_t s2,
+                                                                   U emask, unsigned long long *out)
+{
+    unsigned long long c = 0;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += step) {
+        const int64_t t = i / n0, x = i - t * n0;
+        const int64_t z = t / n1, y = t - z * n1;
+        c += (__ldg(src + x * s0 + y * s1 + z * s2) & emask) == emask ? 1ull : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
 }  // namespace
 
 int launch_permute(const uint8_t *send, uint8_t *recv, const LaunchGeom &g, int rate, int dims, cudaStream_t st)
@@ -289,6 +312,35 @@ int zfpx_permute(zfpx_plan p, int rate, const void *d_send, void *d_recv, size_t
     LaunchGeom g{};
     g.msgs = t->d_msgs; g.nmsg = (int)p->msgs.size(); g.nunits = t->nunits;
     return launch_permute(a, (uint8_t *)d_recv, g, rate, p->dims, (cudaStream_t)stream);
+}
+
+int zfpx_count_nonfinite(const void *d_src, int elem_bytes, const int64_t n[3], const int64_t stride[3],
+                         unsigned long long *d_count, void *stream)
+{
+    if (!d_src || !n || !stride || !d_count) return ZFPX_EINVAL;
+    if (elem_bytes != 4 && elem_bytes != 8) return ZFPX_EINVAL;
+    if (((uintptr_t)d_src % (uintptr_t)elem_bytes) || ((uintptr_t)d_count & 7u)) return ZFPX_EINVAL;
+    for (int a = 0; a < 3; a++)
+        if (n[a] < 0 || stride[a] < 0) return ZFPX_EINVAL;
+    if (n[0] == 0 || n[1] == 0 || n[2] == 0) return ZFPX_OK;
+    if (n[0] > INT64_MAX / n[1] || n[0] * n[1] > INT64_MAX / n[2]) return ZFPX_EINVAL;
+    const int64_t total = n[0] * n[1] * n[2];
+    const cudaStream_t st = (cudaStream_t)stream;
+    const int64_t want = (total + kThreads - 1) / kThreads;
+    if (elem_bytes == 4) {
+        const int occ = occupancy((const void *)count_nonfinite_kernel<uint32_t>, kThreads);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * occ));
+        count_nonfinite_kernel<uint32_t><<<grid, kThreads, 0, st>>>(
+            (const uint32_t *)d_src, n[0], n[1], total, stride[0], stride[1], stride[2], 0x7f800000u, d_count);
+    } else {
+        const int occ = occupancy((const void *)count_nonfinite_kernel<uint64_t>, kThreads);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)num_sms() * occ));
+        count_nonfinite_kernel<uint64_t><<<grid, kThreads, 0, st>>>((const uint64_t *)d_src, n[0], n[1], total,
+                                                                    stride[0], stride[1], stride[2],
+                                                                    0x7ff0000000000000ull, d_count);
+    }
+    count_launch();
+    return check_launch();
 }
 
 }  // extern "C"

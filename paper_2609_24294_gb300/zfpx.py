@@ -135,6 +135,7 @@ def lib():
         "zfpx_encode_f64": ([ctypes.c_int, vp, i64p, i64p, vp, sz, vp], ctypes.c_int),
         "zfpx_decode_f64": ([ctypes.c_int, vp, sz, i64p, i64p, vp, vp], ctypes.c_int),
         "zfpx_rfft_lon": ([vp, i64p, i64p, ctypes.c_int, vp, vp, i64p, vp], ctypes.c_int),
+        "zfpx_count_nonfinite": ([vp, ctypes.c_int, i64p, i64p, vp, vp], ctypes.c_int),
         "zfpx_gauss_legendre": ([ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
                                 ctypes.c_int),
         "zfpx_legendre_create": ([ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int], ctypes.c_int),
@@ -417,6 +418,23 @@ def zfpx_rfft_lon(src, re, im, stream=None):
     _, os_ = field_view(re)
     _check(lib().zfpx_rfft_lon(_dev(src, "src"), _i64x3(n), _i64x3(s), int(re.shape[-1]), _dev(re, "re"),
                                _dev(im, "im"), _i64x3(os_), _stream(stream)), "zfpx_rfft_lon")
+
+
+def zfpx_count_nonfinite(src, count, stream=None):
+    """Adds to count (a one-element int64 CUDA tensor) the number of infinities
+    and NaNs in the float32 or float64 CUDA tensor src (1 to 3 dimensions, the
+    last one fastest; any non-negative strides).  The codec codes a block
+    holding one as a zero block; this is the debug report of such inputs."""
+    if src.dtype not in (torch.float32, torch.float64) or not 1 <= src.dim() <= 3:
+        raise ValueError("src must be a 1-D to 3-D float32 or float64 tensor")
+    if count.dtype != torch.int64 or count.numel() != 1:
+        raise ValueError("count must be a one-element int64 tensor")
+    if src.numel() == 0:
+        return
+    n = tuple(reversed(src.shape)) + (1,) * (3 - src.dim())
+    s = tuple(reversed(src.stride())) + (0,) * (3 - src.dim())
+    _check(lib().zfpx_count_nonfinite(_dev(src, "src"), src.element_size(), _i64x3(n), _i64x3(s),
+                                      _dev(count, "count"), _stream(stream)), "zfpx_count_nonfinite")
 
 
 def zfpx_gauss_legendre(n):

@@ -136,6 +136,28 @@ def test_float64_and_spectral_calls_reject_bad_arguments_before_any_launch(zfpx)
     assert zfpx.zfpx_launch_count() == before
 
 
+def test_count_nonfinite_rejects_bad_arguments_before_any_launch(zfpx):
+    """The debug report of non-finite inputs checks its arguments on the host
+    and launches nothing for an empty view."""
+    L = zfpx.lib()
+    before = zfpx.zfpx_launch_count()
+    n = (ctypes.c_int64 * 3)(8, 8, 8)
+    s = (ctypes.c_int64 * 3)(1, 8, 64)
+    p, c = ctypes.c_void_p(256), ctypes.c_void_p(4096)
+    assert L.zfpx_count_nonfinite(None, 4, n, s, c, None) == -1
+    assert L.zfpx_count_nonfinite(p, 4, n, s, None, None) == -1
+    for eb in (0, 2, 3, 16):
+        assert L.zfpx_count_nonfinite(p, eb, n, s, c, None) == -1, eb
+    assert L.zfpx_count_nonfinite(ctypes.c_void_p(258), 4, n, s, c, None) == -1      # src off 4 bytes
+    assert L.zfpx_count_nonfinite(ctypes.c_void_p(260), 8, n, s, c, None) == -1      # src off 8 bytes
+    assert L.zfpx_count_nonfinite(p, 4, n, s, ctypes.c_void_p(4100), None) == -1     # counter off 8 bytes
+    assert L.zfpx_count_nonfinite(p, 4, (ctypes.c_int64 * 3)(8, -1, 8), s, c, None) == -1
+    assert L.zfpx_count_nonfinite(p, 4, n, (ctypes.c_int64 * 3)(1, -8, 64), c, None) == -1
+    for empty in ((0, 8, 8), (8, 0, 8), (8, 8, 0)):
+        assert L.zfpx_count_nonfinite(p, 8, (ctypes.c_int64 * 3)(*empty), s, c, None) == 0
+    assert zfpx.zfpx_launch_count() == before
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 32, 640, 1280, 2560])
 def test_gauss_legendre_nodes_of_the_library(zfpx, n):
     """The nodes and weights behind the Legendre plan's table (host code, no GPU)
