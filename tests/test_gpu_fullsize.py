@@ -5,11 +5,13 @@ times:
   one CUDA graph, rates 8 and 16: every value of the final field against the
   oracle chained through both transpositions (Sec. II-B, II-C), run over all
   host cores;
-* the ten-field O1280 batch (22.9 GB, one launch each way): sampled blocks'
-  bytes and decoded values, 3-D row-quads and 1-D rows, at both launch
-  shapes the tuner picks between;
-* the serving loop on 2000 requests over the same fields: sampled requests
-  against the oracle, and alone against in the mix.
+* the ten-field O1280 batch (22.9 GB, one launch each way): every byte of
+  every field's stream and every decoded value against the oracle, 3-D
+  row-quads and 1-D rows, and the other launch shape the tuner picks between
+  giving the same bytes and values;
+* the serving loop on 2000 requests over the same fields: every request's
+  stream and values against the oracle, and a sample of requests run alone
+  against the same requests in the mix.
 """
 import numpy as np
 import pytest
