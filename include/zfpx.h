@@ -118,7 +118,11 @@ ZFPX_API uint64_t zfpx_launch_count(void);
  * bytes in both layouts.  The plan is host-side; device tables are built on
  * first use per rate (or by zfpx_plan_prepare, which should precede any
  * stream capture).  *out receives a plan owned by the caller, freed with
- * zfpx_plan_destroy.  Errors: ZFPX_EINVAL, ZFPX_ENOMEM. */
+ * zfpx_plan_destroy.  Size limits (the kernels' block and row indices are
+ * 32-bit): every extent at most 2^31 - 8, and in every message
+ * ceil(nx / 4) * ny * nz < 2^31 (nx, ny, nz the message box); a larger field
+ * goes through more ranks or several calls.  Errors: ZFPX_EINVAL (bad
+ * argument or a size limit), ZFPX_ENOMEM. */
 ZFPX_API int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *dst,
                      int pr, int pc, int transposition, int dims, int split_mode);
 ZFPX_API void zfpx_plan_destroy(zfpx_plan plan);
@@ -188,8 +192,10 @@ ZFPX_API int zfpx_permute(zfpx_plan plan, int rate, const void *d_send, void *d_
  * Encodes the array of extents n[] read through element strides stride[]
  * into d_out (cap bytes, at least zfpx_stream_bytes).  dims 1, 2 or 3,
  * rate 8 or 16; blocks back to back in raster order of block indices (axis 0
- * fastest; for dims 2 each level's blocks in turn).  Errors: ZFPX_EINVAL,
- * ZFPX_ESIZE, ZFPX_ECUDA. */
+ * fastest; for dims 2 each level's blocks in turn).  The array is one message
+ * of a one-rank plan, so the plan's size limits hold: ceil(n[0] / 4) * n[1] *
+ * n[2] < 2^31 (about 8.6e9 values).  Errors: ZFPX_EINVAL, ZFPX_ESIZE,
+ * ZFPX_ECUDA. */
 ZFPX_API size_t zfpx_stream_bytes(int dims, int rate, const int64_t n[3]);
 ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[3],
                 const int64_t stride[3], uint8_t *d_out, size_t cap, void *stream);

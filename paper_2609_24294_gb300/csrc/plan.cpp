@@ -2,6 +2,7 @@
 // and the device tables the kernels read (paper Sec. II-B; Table 1).
 #include <algorithm>
 #include <atomic>
+#include <cstdint>
 #include <cstring>
 #include <new>
 
@@ -48,6 +49,10 @@ int check_launch()
 static const int64_t kAlign = 256;
 static int64_t align_up(int64_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 static int64_t ceil4(int64_t v) { return (v + 3) / 4; }
+
+// Largest extent per axis: a block's origin plus 4 (the kernels test x0 + 4 <=
+// n in 32-bit arithmetic) stays below 2^31.
+constexpr int64_t kMaxExtent = ((int64_t)1 << 31) - 8;
 
 static void block_counts(int dims, const HostMsg &m, int64_t b[3])
 {
@@ -210,7 +215,7 @@ int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *ds
     if (dims < 1 || dims > 3) return ZFPX_EINVAL;
     if (split_mode != ZFPX_SPLIT_BALANCED && split_mode != ZFPX_SPLIT_TABLE1) return ZFPX_EINVAL;
     for (int a = 0; a < 3; a++) {
-        if (src->n[a] < 1 || src->n[a] != dst->n[a] || src->n[a] > (int64_t)1 << 31) return ZFPX_EINVAL;
+        if (src->n[a] < 1 || src->n[a] != dst->n[a] || src->n[a] > kMaxExtent) return ZFPX_EINVAL;
         if (src->stride[a] < 0 || dst->stride[a] < 0) return ZFPX_EINVAL;
     }
     zfpx_plan_s *p = new (std::nothrow) zfpx_plan_s;
@@ -239,6 +244,16 @@ int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *ds
                 for (int l = 0; l < pr; l++)
                     p->msgs.push_back(HostMsg{j * pc + k, l * pc + k, j, l,
                                               xs[l], xl[l], ys[j], yl[j], zs[k], zl[k]});
+    }
+    // The kernels index a message's 4-value groups along x (1-D blocks, the
+    // packs' quads; every coarser block count and row count is at most this)
+    // with 32-bit integers.
+    for (const HostMsg &m : p->msgs) {
+        const int64_t g = ceil4(m.nx) * m.ny;                     // <= 2^29 * 2^31: no overflow
+        if (g > INT32_MAX || g * m.nz > INT32_MAX) {
+            delete p;
+            return ZFPX_EINVAL;
+        }
     }
     *out = p;
     return ZFPX_OK;

@@ -136,6 +136,35 @@ def test_float64_and_spectral_calls_reject_bad_arguments_before_any_launch(zfpx)
     assert zfpx.zfpx_launch_count() == before
 
 
+def test_plan_size_limits(zfpx):
+    """The kernels index a message's 4-value groups along x, rows and blocks
+    with 32-bit integers: a plan whose message holds 2^31 or more groups, or
+    whose extent passes 2^31 - 8, is refused; the same field split over more
+    ranks, or just inside the limits, is accepted.  Host-only: no launch."""
+    L = zfpx.lib()
+    before = zfpx.zfpx_launch_count()
+
+    def create(n, pr, pc, dims):
+        v = zfpx.View3((ctypes.c_int64 * 3)(*n), (ctypes.c_int64 * 3)(0, 0, 0))
+        h = ctypes.c_void_p()
+        rc = L.zfpx_plan_create(ctypes.byref(h), ctypes.byref(v), ctypes.byref(v), pr, pc, 0, dims, 0)
+        if rc == 0:
+            L.zfpx_plan_destroy(h)
+        return rc
+
+    big = (1 << 31) - 8
+    assert create((big, 1, 1), 1, 1, 1) == 0
+    assert create((big + 1, 1, 1), 1, 1, 1) == -1
+    assert create((1, big, 1), 1, 1, 3) == 0
+    assert create((1, 1, big + 1), 1, 1, 3) == -1
+    for dims in (1, 2, 3):
+        assert create((4, 1 << 16, (1 << 15) - 1), 1, 1, dims) == 0          # 2^31 - 2^16 groups
+        assert create((4, 1 << 16, 1 << 15), 1, 1, dims) == -1               # 2^31 groups
+        assert create((8, 1 << 20, 1 << 12), 1, 1, dims) == -1               # 2^33 groups in one message
+        assert create((8, 1 << 20, 1 << 12), 4, 4, dims) == 0                # 2^28 in each of 64
+    assert zfpx.zfpx_launch_count() == before
+
+
 def test_count_nonfinite_rejects_bad_arguments_before_any_launch(zfpx):
     """The debug report of non-finite inputs checks its arguments on the host
     and launches nothing for an empty view."""
