@@ -4,6 +4,8 @@
 // produce with the oracle.  Test infrastructure only.
 //
 //   block_codec_host MODE RATE < input > output      (RATE 8 or 16)
+//     enc3: N x 64 float32             -> N streams of 8 RATE bytes (the scalar two-pass 3-D
+//                                         encoder, the statement the GPU's warp-uniform coder follows)
 //     dec3: N streams of 8 RATE bytes  -> N x 64 float32 (the GPU decoders' 3-D block decoder)
 //     enc2: N x 16 float32             -> N streams of 2 RATE bytes
 //     dec2: N streams of 2 RATE bytes  -> N x 16 float32
@@ -111,6 +113,23 @@ void store_le(uint64_t v, int nbytes, uint8_t *dst)
 }
 
 template <int RATE>
+int enc3(const std::vector<uint8_t> &in)
+{
+    if (in.size() % 256) return 2;
+    for (size_t o = 0; o < in.size(); o += 256) {
+        float x[64];
+        std::memcpy(x, &in[o], sizeof x);
+        Writer<RATE> wr{};
+        Planes64 pl{};
+        encode_block3<RATE>(x, wr, pl);
+        uint8_t out[8 * RATE];
+        for (int i = 0; i < RATE; i++) store_le(wr.wd[i], 8, out + 8 * i);
+        write_all(out, sizeof out);
+    }
+    return 0;
+}
+
+template <int RATE>
 int dec3(const std::vector<uint8_t> &in)
 {
     constexpr int B = 8 * RATE;
@@ -215,6 +234,7 @@ int dec1(const std::vector<uint8_t> &in)
 template <int RATE>
 int run(const char *mode, const std::vector<uint8_t> &in)
 {
+    if (!std::strcmp(mode, "enc3")) return enc3<RATE>(in);
     if (!std::strcmp(mode, "dec3")) return dec3<RATE>(in);
     if (!std::strcmp(mode, "enc2")) return enc2<RATE>(in);
     if (!std::strcmp(mode, "dec2")) return dec2<RATE>(in);

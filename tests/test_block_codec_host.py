@@ -4,15 +4,16 @@ by block and bit for bit (paper Sec. II-C; the readings of the oracle).
 `tests/block_codec_host.cpp` compiles the __host__ __device__ functions of
 `csrc/zfpx_block.cuh` with a C++ compiler: the 3-D block decoder that the
 GPU's decode kernels run (windowed plane parse, transposes, inverse
-transform, dequantisation), and the 2-D and 1-D encoders and decoders (the
-1-D ones with four blocks in lockstep, checked against one block at a time).
+transform, dequantisation), the scalar two-pass 3-D encoder (the statement
+the GPU's warp-uniform encoder follows), and the 2-D and 1-D encoders and
+decoders (the 1-D ones with four blocks in lockstep, checked against one
+block at a time).
 Streams must equal the oracle's byte for byte and decoded floats its bit
 patterns, on graded spectra, random blocks over many scales, special values
 (zero, signed zero, subnormals, the largest floats, inf and NaN) and, for the
 decoders, arbitrary byte streams.  No GPU: a regression in the coding logic
-shows here before any GPU run.  (The 3-D encoder of the GPU path is the
-warp-uniform coder of `csrc/zfpx_enc3.cuh`, device code; its parity is in the
-GPU tests.)"""
+shows here before any GPU run.  (The warp-uniform 3-D encoder the GPU runs,
+`csrc/zfpx_enc3.cuh`, is device code; its parity is in the GPU tests.)"""
 import shutil
 import subprocess
 from pathlib import Path
@@ -96,9 +97,11 @@ def bits(a):
 
 
 @pytest.mark.parametrize("rate", [8, 16])
-def test_3d_decoder_equals_the_oracle(host, rate):
+def test_3d_coders_equal_the_oracle(host, rate):
     x = blocks(3, 1200, seed=rate)
-    streams = oracle_encode(3, rate, x).tobytes() + random_streams(3, rate, 400, seed=100 + rate)
+    want_s = oracle_encode(3, rate, x)
+    assert run(host, "enc3", rate, x.tobytes()) == want_s.tobytes()
+    streams = want_s.tobytes() + random_streams(3, rate, 400, seed=100 + rate)
     got = np.frombuffer(run(host, "dec3", rate, streams), np.float32).reshape(-1, 64)
     want = oracle_decode(3, rate, streams)
     assert got.shape == want.shape
@@ -122,6 +125,6 @@ def test_2d_and_1d_coders_equal_the_oracle(host, dims, rate):
 
 def test_host_program_rejects_bad_input(host):
     for mode, rate, data in [("dec3", 8, b"\0" * 63), ("enc2", 16, b"\0" * 60), ("dec1", 8, b"\0" * 5),
-                             ("enc3", 8, b""), ("dec3", 12, b"")]:
+                             ("enc3", 8, b"\0" * 255), ("enc4", 8, b""), ("dec3", 12, b"")]:
         r = subprocess.run([str(host), mode, str(rate)], input=data, capture_output=True)
         assert r.returncode == 2, (mode, rate)
