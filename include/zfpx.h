@@ -121,8 +121,9 @@ ZFPX_API uint64_t zfpx_launch_count(void);
  * zfpx_plan_destroy.  Size limits (the kernels' block and row indices are
  * 32-bit): every extent at most 2^31 - 8, and in every message
  * ceil(nx / 4) * ny * nz < 2^31 (nx, ny, nz the message box); a larger field
- * goes through more ranks or several calls.  Errors: ZFPX_EINVAL (bad
- * argument or a size limit), ZFPX_ENOMEM. */
+ * goes through more ranks or several calls.  At most 2^24 messages
+ * (p_r p_c p_c for transposition 0, p_r p_c p_r for 1).  Errors: ZFPX_EINVAL
+ * (bad argument or a size limit), ZFPX_ENOMEM (host tables). */
 ZFPX_API int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *dst,
                      int pr, int pc, int transposition, int dims, int split_mode);
 ZFPX_API void zfpx_plan_destroy(zfpx_plan plan);

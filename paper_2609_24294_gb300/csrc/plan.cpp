@@ -53,6 +53,9 @@ static int64_t ceil4(int64_t v) { return (v + 3) / 4; }
 // Largest extent per axis: a block's origin plus 4 (the kernels test x0 + 4 <=
 // n in 32-bit arithmetic) stays below 2^31.
 constexpr int64_t kMaxExtent = ((int64_t)1 << 31) - 8;
+// Most messages a plan may hold (P p_c for z -> lambda, P p_r for lambda ->
+// theta): 2^24 descriptors, about 1.3 GB of host tables.
+constexpr int64_t kMaxMessages = (int64_t)1 << 24;
 
 static void block_counts(int dims, const HostMsg &m, int64_t b[3])
 {
@@ -218,6 +221,7 @@ int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *ds
         if (src->n[a] < 1 || src->n[a] != dst->n[a] || src->n[a] > kMaxExtent) return ZFPX_EINVAL;
         if (src->stride[a] < 0 || dst->stride[a] < 0) return ZFPX_EINVAL;
     }
+    if ((int64_t)pr * pc * (transposition == 0 ? pc : pr) > kMaxMessages) return ZFPX_EINVAL;
     zfpx_plan_s *p = new (std::nothrow) zfpx_plan_s;
     if (!p) return ZFPX_ENOMEM;
     for (int a = 0; a < 3; a++) { p->n[a] = src->n[a]; p->ss[a] = src->stride[a]; p->ds[a] = dst->stride[a]; }
@@ -225,25 +229,30 @@ int zfpx_plan_create(zfpx_plan *out, const zfpx_view3 *src, const zfpx_view3 *ds
     p->transposition = transposition; p->dims = dims; p->split_mode = split_mode;
 
     std::vector<int64_t> xs, xl, ys, yl, zs, zl;
-    if (transposition == 0) {
-        split(p->n[0], pc, split_mode, xs, xl);
-        split(p->n[1], pr, split_mode, ys, yl);
-        split(p->n[2], pc, split_mode, zs, zl);
-        // source rank j*pc+i, in send order: by source, then destination peer k
-        for (int j = 0; j < pr; j++)
-            for (int i = 0; i < pc; i++)
+    try {
+        if (transposition == 0) {
+            split(p->n[0], pc, split_mode, xs, xl);
+            split(p->n[1], pr, split_mode, ys, yl);
+            split(p->n[2], pc, split_mode, zs, zl);
+            // source rank j*pc+i, in send order: by source, then destination peer k
+            for (int j = 0; j < pr; j++)
+                for (int i = 0; i < pc; i++)
+                    for (int k = 0; k < pc; k++)
+                        p->msgs.push_back(HostMsg{j * pc + i, j * pc + k, i, k,
+                                                  xs[i], xl[i], ys[j], yl[j], zs[k], zl[k]});
+        } else {
+            split(p->n[0], pr, split_mode, xs, xl);
+            split(p->n[1], pr, split_mode, ys, yl);
+            split(p->n[2], pc, split_mode, zs, zl);
+            for (int j = 0; j < pr; j++)
                 for (int k = 0; k < pc; k++)
-                    p->msgs.push_back(HostMsg{j * pc + i, j * pc + k, i, k,
-                                              xs[i], xl[i], ys[j], yl[j], zs[k], zl[k]});
-    } else {
-        split(p->n[0], pr, split_mode, xs, xl);
-        split(p->n[1], pr, split_mode, ys, yl);
-        split(p->n[2], pc, split_mode, zs, zl);
-        for (int j = 0; j < pr; j++)
-            for (int k = 0; k < pc; k++)
-                for (int l = 0; l < pr; l++)
-                    p->msgs.push_back(HostMsg{j * pc + k, l * pc + k, j, l,
-                                              xs[l], xl[l], ys[j], yl[j], zs[k], zl[k]});
+                    for (int l = 0; l < pr; l++)
+                        p->msgs.push_back(HostMsg{j * pc + k, l * pc + k, j, l,
+                                                  xs[l], xl[l], ys[j], yl[j], zs[k], zl[k]});
+        }
+    } catch (const std::bad_alloc &) {
+        delete p;
+        return ZFPX_ENOMEM;
     }
     // The kernels index a message's 4-value groups along x (1-D blocks, the
     // packs' quads; every coarser block count and row count is at most this)

@@ -140,7 +140,9 @@ def test_plan_size_limits(zfpx):
     """The kernels index a message's 4-value groups along x, rows and blocks
     with 32-bit integers: a plan whose message holds 2^31 or more groups, or
     whose extent passes 2^31 - 8, is refused; the same field split over more
-    ranks, or just inside the limits, is accepted.  Host-only: no launch."""
+    ranks, or just inside the limits, is accepted.  A rank grid that would
+    need more than 2^24 messages is refused before any table is built.
+    Host-only: no launch."""
     L = zfpx.lib()
     before = zfpx.zfpx_launch_count()
 
@@ -153,6 +155,9 @@ def test_plan_size_limits(zfpx):
         return rc
 
     big = (1 << 31) - 8
+    # at most 2^24 messages: p_r p_c p_c (z -> lambda) or p_r p_c p_r (lambda -> theta)
+    assert create((64, 64, 64), 1, 8192, 3) == -1
+    assert create((64, 64, 64), 64, 64, 3) == 0                              # 2^18 messages
     assert create((big, 1, 1), 1, 1, 1) == 0
     assert create((big + 1, 1, 1), 1, 1, 1) == -1
     assert create((1, big, 1), 1, 1, 3) == 0
