@@ -42,6 +42,8 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <memory>
+#include <new>
 #include <vector>
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -554,27 +556,29 @@ void gauss_legendre(int n, std::vector<double> &mu, std::vector<double> &w)
 
 using namespace zfpx;
 
-extern "C" {
+namespace {
 
-int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
+int legendre_create(zfpx_legendre *out, int nlat, int T)
 {
-    if (!out) return ZFPX_EINVAL;
-    *out = nullptr;
-    if (nlat < 2 || nlat % 2 || nlat > 1 << 15 || T < 0 || T + 1 > nlat) return ZFPX_EINVAL;   // grid z = nlat
-    auto *p = new zfpx_legendre_s();
+    std::unique_ptr<zfpx_legendre_s> hold(new zfpx_legendre_s());
+    zfpx_legendre_s *p = hold.get();
     p->nlat = nlat; p->T = T; p->nh = nlat / 2;
     p->nhs = (p->nh + 3) / 4 * 4;                        // row pitch: a multiple of 16 bytes
-    if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return ZFPX_ECUDA; }
-    std::vector<double> mu, w;
-    gauss_legendre(nlat, mu, w);
+    if (cudaGetDevice(&p->device) != cudaSuccess) return ZFPX_ECUDA;
     const int nh = p->nh, nhs = p->nhs;
-    std::vector<double> s(nh);
-    for (int j = 0; j < nh; j++) s[j] = std::sqrt(std::max(0.0, 1.0 - mu[j] * mu[j]));
     // rows: for m = 0..T, parity 0 then 1, one row per l = m + p + 2 i, K-major
     int64_t rows = 0;
     for (int m = 0; m <= T; m++)
         for (int par = 0; par < 2; par++) rows += (T - m - par) >= 0 ? (T - m - par) / 2 + 1 : 0;
     p->table_rows = rows;
+    // the two tables (high and low TF32 parts) must fit on the device
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return ZFPX_ECUDA;
+    if ((double)std::max<int64_t>(rows, 1) * nhs * 2 * sizeof(float) > (double)total_b) return ZFPX_ENOMEM;
+    std::vector<double> mu, w;
+    gauss_legendre(nlat, mu, w);
+    std::vector<double> s(nh);
+    for (int j = 0; j < nh; j++) s[j] = std::sqrt(std::max(0.0, 1.0 - mu[j] * mu[j]));
     std::vector<float> tab((size_t)std::max<int64_t>(rows, 1) * nhs, 0.0f);
     std::vector<LegItem> items;
     std::vector<double> pmm(nh, std::sqrt(0.5));
@@ -622,11 +626,28 @@ int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
         cudaFree(p->d_table_lo);
         cudaFree(p->d_items);
         cudaFree(p->d_status);
-        delete p;
         return ZFPX_ECUDA;
     }
-    *out = p;
+    *out = hold.release();
     return ZFPX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int zfpx_legendre_create(zfpx_legendre *out, int nlat, int T)
+{
+    if (!out) return ZFPX_EINVAL;
+    *out = nullptr;
+    if (nlat < 2 || nlat % 2 || nlat > 1 << 15 || T < 0 || T + 1 > nlat) return ZFPX_EINVAL;   // grid z = nlat
+    // the host tables are built before any device memory is taken: a failed
+    // host allocation leaves nothing behind
+    try {
+        return legendre_create(out, nlat, T);
+    } catch (const std::bad_alloc &) {
+        return ZFPX_ENOMEM;
+    }
 }
 
 int zfpx_gauss_legendre(int n, double *mu, double *w)

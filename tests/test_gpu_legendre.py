@@ -110,6 +110,11 @@ def test_errors(z):
     for nlat, T in [(3, 1), (8, 8), (0, 0), (8, -1)]:
         with pytest.raises(z.ZfpxError):
             z.Legendre(nlat, T)
+    # tables larger than the device (T = 32767: about 70 TB) are refused before
+    # any of them is built
+    with pytest.raises(z.ZfpxError) as e:
+        z.Legendre(1 << 15, (1 << 15) - 1)
+    assert e.value.code == -6                                                    # ZFPX_ENOMEM
     plan = z.Legendre(8, 5)
     re = torch.zeros((2, 8, 6), device="cuda")
     a = torch.zeros((2, plan.ncoeffs), device="cuda")
