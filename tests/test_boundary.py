@@ -25,6 +25,21 @@ def test_exports_every_declared_symbol(zfpx):
         assert hasattr(L, n), n
 
 
+def test_exports_nothing_undeclared(zfpx):
+    """The library's dynamic symbol table holds exactly the calls the header
+    declares: nothing outside the documented C ABI is reachable."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("no nm")
+    out = subprocess.run([nm, "-D", "--defined-only", zfpx.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = {f[-1] for f in (ln.split() for ln in out.splitlines()) if len(f) >= 3 and f[1] in "TW"}
+    exported = {n for n in exported if not n.startswith("_")}
+    assert exported == set(zfpx.declared_symbols())
+
+
 def test_strerror_and_counter(zfpx):
     L = zfpx.lib()
     for code in (0, -1, -2, -3, -4, -5, -6):
