@@ -203,8 +203,9 @@ ZFPX_API int zfpx_encode(int dims, int rate, const float *d_in, const int64_t n[
 ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, const int64_t n[3],
                 const int64_t stride[3], float *d_out, void *stream);
 
-/* ---- debug report of non-finite inputs -------------------------------------
- * The paper leaves infinities and NaNs in the input unspecified.  The codec
+/* ---- debug report of non-finite inputs (Sec. II-C) ------------------------
+ * The paper's codec outline leaves infinities and NaNs in the input
+ * unspecified.  The codec
  * codes a block whose largest magnitude is not finite as a zero block (a single
  * 0 bit; it decodes to zeros) and never faults on one; this call reports such
  * inputs.  It adds to *d_count (a device counter that the caller owns, zeroes
