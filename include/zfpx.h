@@ -205,10 +205,9 @@ ZFPX_API int zfpx_decode(int dims, int rate, const uint8_t *d_in, size_t len, co
 
 /* ---- debug report of non-finite inputs (Sec. II-C) ------------------------
  * The paper's codec outline leaves infinities and NaNs in the input
- * unspecified.  The codec
- * codes a block whose largest magnitude is not finite as a zero block (a single
- * 0 bit; it decodes to zeros) and never faults on one; this call reports such
- * inputs.  It adds to *d_count (a device counter that the caller owns, zeroes
+ * unspecified.  The codec codes a block whose largest magnitude is not finite
+ * as a zero block (a single 0 bit; it decodes to zeros) and never faults on
+ * one; this call reports such inputs.  It adds to *d_count (a device counter that the caller owns, zeroes
  * and reads) the number of elements of the view (extents n[], element strides
  * stride[] >= 0, axis 0 fastest) whose exponent field is all ones, i.e. the
  * infinities and NaNs.  elem_bytes: 4 for float32, 8 for float64; d_src
